@@ -1,0 +1,18 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a B300 and the built CUDA library")
+    config.addinivalue_line("markers", "slow: minutes of CPU work")
+
+
+@pytest.fixture(scope="session")
+def root():
+    return ROOT
