@@ -1,0 +1,258 @@
+/*
+ * egt.h -- C-ABI of the B300 Excessive Gap Technique library (libegt.so).
+ *
+ * Solves the sequence-form bilinear saddle point of a two-player zero-sum
+ * poker river endgame,  min_{x in X} max_{y in Y} <x, A y>  (Eq. 1 / Eq. 2),
+ * with EGT and the dilated entropy distance (Sec. 3, Sec. 5, Algorithms 1-4).
+ * x is player 1 (moves first, minimises), y is player 2 (maximises); A holds
+ * the expected payoff to player 2, chance-normalised per hand dealt.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every function returns an egt_status and never aborts; on failure a
+ *   thread-local message is available from egt_last_error().
+ * - The caller owns every pointer it passes; the library never frees caller
+ *   memory.  An egt_game owns its device tables and solver state and frees
+ *   them in egt_destroy_game.
+ * - "device" pointers are CUDA global memory on the game's device; "host"
+ *   pointers are ordinary CPU memory.
+ * - Strategy and gradient vectors are laid out [seq][hand] with a leading
+ *   dimension ld (egt_dims.ld, a multiple of 32 >= H): element (s, h) is at
+ *   s * ld + h.  Hands are in ascending strength order (ties by input index),
+ *   see egt_hand_order.  Columns h >= H are ignored on input and written as
+ *   0 on output.  Vector base pointers must be 16-byte aligned.
+ * - stream: a cudaStream_t (NULL = legacy default stream).  Kernels run on it;
+ *   calls that return host values synchronise it.  Calls on one game share
+ *   its scratch memory: issue them on one stream (or otherwise serialise).
+ *
+ * Game model (Sec. 7, subgame description) and the betting reading used here
+ * --------------------------------------------------------------------------
+ * Chance deals each player a private hand from that player's range (hands
+ * sharing a card are never dealt together); player 1 acts first; fold ends
+ * the game, call or two opening checks go to showdown (stronger hand wins the
+ * stake, ties pay 0).  Each player has pot/2 in; the loser pays pot/2 plus
+ * their river chips.  Not facing a bet: check, or bet f * pot_total for each
+ * menu fraction f.  Facing a bet: fold, call, or raise by call + f *
+ * (pot_total + call).  Sizes that reach the remaining stack are dropped;
+ * all-in is offered (if enabled) while the number of bets is below raise_cap
+ * and chips remain after calling; raise_cap counts the opening bet and the
+ * raises; there is no fold when not facing a bet.
+ *
+ * Canonical numbering: the public tree is walked depth first with actions in
+ * the order fold, check/call, menu sizes, all-in; a player's information sets
+ * (simplexes) are sorted by (level b_Q^j, preorder index of the public node);
+ * sequences are numbered simplex by simplex in action order; terminals in
+ * preorder.  The empty sequence is not stored.
+ */
+#ifndef EGT_H_
+#define EGT_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define EGT_API __attribute__((visibility("default")))
+#else
+#define EGT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct egt_game egt_game;
+
+typedef enum {
+  EGT_OK = 0,
+  EGT_ERR_INVALID_ARG = 1,     /* bad pointer, size, player, range, card id, ... */
+  EGT_ERR_OOM = 2,             /* device or host allocation failed */
+  EGT_ERR_CUDA = 3,            /* a CUDA runtime call or kernel launch failed */
+  EGT_ERR_NUMERIC = 4,         /* a NaN / Inf appeared in a value */
+  EGT_ERR_TAU_UNDERFLOW = 5,   /* Alg. 4 halved tau below 2^-30 */
+  EGT_ERR_NOT_CONVERGED = 6,   /* egt_solve hit max_iters above its gap target */
+  EGT_ERR_TIMEOUT = 7          /* reserved: a bounded device wait gave up */
+} egt_status;
+
+/* One river endgame (all pointers host, read during egt_create_game only).
+ * hand_cards: [n_hands][hand_size] card ids in [0, n_cards), distinct within a
+ *   hand, no two hands equal; hand_size is 1 or 2.
+ * strength: [n_hands], higher wins, equal = tie.
+ * range[p]: [n_hands] >= 0 finite, not all zero; normalised internally.
+ * pot, stack: chips (stack = remaining chips of each player, equal stacks).
+ * bb: chips per big blind; gaps are reported in mbb = bb / 1000 per hand.
+ * bet_fracs: [n_bets] pot fractions > 0 in menu order. */
+typedef struct {
+  int32_t n_cards;
+  int32_t hand_size;
+  int32_t n_hands;
+  const int32_t* hand_cards;
+  const int32_t* strength;
+  const double* range[2];
+  double pot;
+  double stack;
+  double bb;
+  int32_t n_bets;
+  const double* bet_fracs;
+  int32_t allin;
+  int32_t raise_cap;
+} egt_game_desc;
+
+/* Sizes and constants of a compiled game.
+ * S[p] sequences, J[p] simplexes (information sets per hand), L[p] levels of
+ * player p's per-hand treeplex; T terminals (n_fold of them folds); H hands;
+ * ld leading dimension; Z chance normaliser (sum over compatible hand pairs
+ * of r1 r2); normA = max |A_ij| (the l1 operator norm, Sec. 3); M[p] = max l1
+ * norm of player p's strategy space (DGF modulus 1/M, Sec. 5); Omega[p] = max
+ * minus min of the dilated entropy over it (Sec. 3). */
+typedef struct {
+  int32_t H, ld;
+  int32_t S[2], J[2], L[2];
+  int32_t T, n_fold;
+  double Z, normA, M[2], Omega[2];
+} egt_dims;
+
+/* Compile the game (betting tree, treeplex tables, hand/card tables) and
+ * upload it to `device`; allocates the game's device memory (tables, solver
+ * state, scratch).  *out receives the handle.  device = -1 compiles the host
+ * tables only: the query calls work, every compute call returns INVALID_ARG,
+ * and no CUDA call is made.  Errors: INVALID_ARG on an invalid description,
+ * OOM, CUDA. */
+EGT_API egt_status egt_create_game(const egt_game_desc* desc, int32_t device, void* stream, egt_game** out);
+
+/* Free everything the game owns (synchronises its device).  NULL is a no-op. */
+EGT_API egt_status egt_destroy_game(egt_game* game);
+
+EGT_API egt_status egt_dims_query(const egt_game* game, egt_dims* out);
+
+/* order[k] (host, [H]) = input index of the hand at sorted position k. */
+EGT_API egt_status egt_hand_order(const egt_game* game, int32_t* order);
+
+/* Per-hand treeplex of player p (Sec. 4 notation), host arrays of length J[p]:
+ * parent sequence p_j (-1: q_{p_j} = 1), first sequence of I_j, n_j, level
+ * b_Q^j, and the DGF weight beta_j = 2 + sum over child simplexes 2 beta_k
+ * (Sec. 5).  Any pointer may be NULL. */
+EGT_API egt_status egt_treeplex_query(const egt_game* game, int32_t player, int32_t* parent,
+                              int32_t* first_seq, int32_t* n_actions, int32_t* level,
+                              double* beta);
+
+/* Terminals in preorder, host arrays of length T: sigma_1(b), sigma_2(b),
+ * kind (0 fold, 1 showdown), coef (fold: payoff to player 2; showdown: stake
+ * paid by the weaker hand).  Any pointer may be NULL. */
+EGT_API egt_status egt_terminal_query(const egt_game* game, int32_t* seq1, int32_t* seq2,
+                              int32_t* kind, double* coef);
+
+/* Gradient product (Sec. 3: grad f = A y, grad phi = A^T x).
+ * player 0: out[S0][ld] = A in, in = y [S1][ld];
+ * player 1: out[S1][ld] = A^T in, in = x [S0][ld].  Device pointers, in != out.
+ * Computed per terminal with card-removal inclusion-exclusion (folds) and
+ * strength-sorted prefix sums with per-card corrections (showdowns), FP32
+ * with compensated (float-float) sums. */
+EGT_API egt_status egt_grad(egt_game* game, int32_t player, const float* in, float* out, void* stream);
+
+/* Same product in FP64 throughout (used by the stopping gap). */
+EGT_API egt_status egt_grad_f64(egt_game* game, int32_t player, const double* in, double* out,
+                        void* stream);
+
+/* Smoothed best response with the dilated entropy DGF (Sec. 5).
+ * player 0: q = argmin_{x in X} <x, g> + mu d_X(x), value = that minimum
+ *           (phi_mu(y) when g = A y);
+ * player 1: q = argmax_{y in Y} <y, g> - mu d_Y(y), value = that maximum
+ *           (f_mu(x) when g = A^T x).
+ * g, q_out: device [S_p][ld] (q_out may be NULL to get the value only).
+ * value_out: host, may be NULL (then no synchronisation).  mu > 0. */
+EGT_API egt_status egt_smoothed_br(egt_game* game, int32_t player, const float* g, double mu,
+                           float* q_out, double* value_out, void* stream);
+
+/* Plain best-response value in FP64 (the mu -> 0 limit; Sec. 3 residual):
+ * player 0: min_x <x, g>; player 1: max_y <y, g>.  g device [S_p][ld] FP64,
+ * value_out host. */
+EGT_API egt_status egt_best_response_f64(egt_game* game, int32_t player, const double* g,
+                                 double* value_out, void* stream);
+
+/* Saddle-point residual eps_sad(x, y) = max_y' x^T A y' - min_x' x'^T A y (Sec. 3),
+ * products and best responses in FP64, in mbb per hand (host out).  x, y device. */
+EGT_API egt_status egt_gap(egt_game* game, const float* x, const float* y, double* gap_mbb,
+                   void* stream);
+
+/* ---- solver (Algorithms 1-4) ---------------------------------------------- */
+
+typedef enum {
+  EGT_THEORY = 0,     /* Alg. 1: mu = ||A|| sqrt(M_X M_Y), tau_t = 2/(t+3), alternate by parity */
+  EGT_PRACTICAL = 1,  /* "EGT": tuned mu (alpha), tau_t = 2/(t+3), step the player with larger mu */
+  EGT_AS = 2          /* "EGT/as": Alg. 3 + 4, aggressive tau with backtracking on EGV < 0 */
+} egt_variant;
+
+typedef struct {
+  int32_t t, player, backoffs;
+  double tau, mu[2], egv, gap_mbb;
+} egt_iter_log;
+
+/* alpha: practical variants start from mu = alpha ||A|| sqrt(M_X M_Y) and
+ *   double both mu while EGV < 0 at the initial point.
+ * mu0: if both > 0, the initial mu as given (no guard).
+ * eps_mbb: stop once eps_sad <= eps_mbb (checked every gap_every iterations,
+ *   FP64); <= 0 runs max_iters.
+ * replay: if replay_n > 0, iteration t steps player replay_player[t] with
+ *   tau = replay_tau[t] (no EGV check) for replay_n iterations (host arrays).
+ * log: optional host array of log_cap entries filled per iteration. */
+typedef struct {
+  int32_t variant;
+  double alpha;
+  double mu0[2];
+  double eps_mbb;
+  int32_t max_iters;
+  int32_t gap_every;
+  int32_t replay_n;
+  const int32_t* replay_player;
+  const double* replay_tau;
+  int32_t log_cap;
+  egt_iter_log* log;
+} egt_solve_opts;
+
+typedef struct {
+  int32_t iters, products, backoffs, gap_checks;
+  double gap_mbb, mu[2], tau, seconds;
+} egt_solve_report;
+
+/* Initial point of Alg. 1 / 3: x_omega = uniform behavioural strategy,
+ * y^0 = y_{mu_y}(x_omega), x^0 = x_{mu_x}(y^0) (grad d* with the minus sign
+ * restored), mu from opts (variant, alpha, mu0, guard). */
+EGT_API egt_status egt_solver_init(egt_game* game, const egt_solve_opts* opts, void* stream);
+
+typedef enum {
+  EGT_STEP_PLAIN = 0,   /* one Step (Alg. 2) at tau, always kept */
+  EGT_STEP_CHECK = 1,   /* one Step at tau, EGV evaluated, kept iff EGV >= 0 */
+  EGT_STEP_DECR = 2     /* Alg. 4: halve tau until EGV >= 0, then keep */
+} egt_step_mode;
+
+typedef struct {
+  int32_t player, accepted, backoffs, products;
+  double tau, egv, mu[2];
+} egt_step_info;
+
+/* One Step (Alg. 2) from the solver state; player 0 = x-focused, 1 =
+ * y-focused, -1 = the player with the larger mu (tie: y).  *tau_inout is the
+ * step size (Decr writes back the accepted one).  info (host) may be NULL. */
+EGT_API egt_status egt_step(egt_game* game, int32_t player, double* tau_inout, int32_t mode,
+                    egt_step_info* info, void* stream);
+
+/* Copy the current iterates (device [S_p][ld], NULL to skip) and mu (host [2]). */
+EGT_API egt_status egt_state_get(egt_game* game, float* x, float* y, double* mu, void* stream);
+
+/* Replace the iterates and mu (checkpoint resume); cached products are recomputed. */
+EGT_API egt_status egt_state_set(egt_game* game, const float* x, const float* y, const double* mu,
+                         void* stream);
+
+/* Run Alg. 1 / practical EGT / Alg. 3 from egt_solver_init to the gap target.
+ * x_out, y_out: device, may be NULL.  rep: host, may be NULL.
+ * Returns NOT_CONVERGED if eps_mbb > 0 was not reached within max_iters. */
+EGT_API egt_status egt_solve(egt_game* game, const egt_solve_opts* opts, float* x_out, float* y_out,
+                     egt_solve_report* rep, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+EGT_API const char* egt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EGT_H_ */

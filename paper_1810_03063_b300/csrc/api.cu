@@ -1,0 +1,926 @@
+// C-ABI of libegt (include/egt.h): game compilation and upload, the gradient /
+// smoothed-best-response / gap entry points, and the EGT drivers (Alg. 1-4).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/egt.h"
+#include "egt_internal.cuh"
+#include "tree.hpp"
+
+using namespace egt;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+egt_status fail(egt_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                 \
+  do {                                                                                 \
+    cudaError_t e__ = (expr);                                                          \
+    if (e__ != cudaSuccess)                                                            \
+      return fail(e__ == cudaErrorMemoryAllocation ? EGT_ERR_OOM : EGT_ERR_CUDA,       \
+                  std::string(#expr) + ": " + cudaGetErrorString(e__));                \
+  } while (0)
+
+#define EGT_TRY(expr)                  \
+  do {                                 \
+    egt_status s__ = (expr);           \
+    if (s__ != EGT_OK) return s__;     \
+  } while (0)
+
+// Restores the caller's current device when it goes out of scope.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (dev < 0) return;   // host-only game: no CUDA calls
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+constexpr int kMaxLd = 2048;
+constexpr double kTauMin = 1.0 / (1u << 30);
+
+}  // namespace
+
+struct egt_game {
+  int device = 0;
+  Compiled comp;
+  // host copies
+  int H = 0, ld = 0, hand_size = 2, n_slots = 0, lmax = 0;
+  double Z = 0, normA = 0, M[2] = {0, 0}, Omega[2] = {0, 0}, bb = 1, pot = 1;
+  std::vector<int32_t> order;
+  // device arena of tables
+  void* arena = nullptr;
+  DevGame dg{};
+  // solver state and scratch (device)
+  float* vec = nullptr;          // all float vectors
+  float *x[2], *y[2], *gx[2], *gy[2], *tx, *ty;   // [S0|S1][ld]
+  int cur = 0;                   // index of the current iterate / cached products
+  double* g64[2] = {nullptr, nullptr};   // FP64 products for the gap
+  double* partials = nullptr;    // per-CTA value partials
+  unsigned int* counter = nullptr;
+  double* vals = nullptr;        // device value slots
+  int* status = nullptr;         // device NaN flag
+  double* pinned = nullptr;      // host readback of value slots
+  double mu[2] = {0, 0};
+  bool initialised = false;
+  bool host_only = false;        // compiled tables only (device = -1): queries work, kernels do not
+  long long products = 0;
+};
+
+namespace {
+
+size_t vec_elems(const egt_game* G, int p) { return (size_t)G->comp.tpx[p].S * G->ld; }
+
+egt_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(EGT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return EGT_OK;
+}
+
+egt_status validate(const egt_game_desc* d) {
+  if (!d) return fail(EGT_ERR_INVALID_ARG, "desc is NULL");
+  if (d->hand_size != 1 && d->hand_size != 2) return fail(EGT_ERR_INVALID_ARG, "hand_size must be 1 or 2");
+  if (d->n_cards < 1 || d->n_cards > 254) return fail(EGT_ERR_INVALID_ARG, "n_cards out of range [1, 254]");
+  if (d->n_hands < 1) return fail(EGT_ERR_INVALID_ARG, "n_hands < 1");
+  if (!d->hand_cards || !d->strength || !d->range[0] || !d->range[1])
+    return fail(EGT_ERR_INVALID_ARG, "NULL hand_cards / strength / range");
+  if (!(d->pot > 0) || !(d->stack >= 0) || !(d->bb > 0) || !std::isfinite(d->pot) ||
+      !std::isfinite(d->stack) || !std::isfinite(d->bb))
+    return fail(EGT_ERR_INVALID_ARG, "pot, bb must be > 0 and stack >= 0, finite");
+  if (d->n_bets < 0 || (d->n_bets > 0 && !d->bet_fracs)) return fail(EGT_ERR_INVALID_ARG, "bad bet menu");
+  for (int i = 0; i < d->n_bets; ++i)
+    if (!(d->bet_fracs[i] > 0) || !std::isfinite(d->bet_fracs[i]))
+      return fail(EGT_ERR_INVALID_ARG, "bet fractions must be > 0 and finite");
+  if (d->raise_cap < 0) return fail(EGT_ERR_INVALID_ARG, "raise_cap < 0");
+  const int H = d->n_hands, k = d->hand_size;
+  std::vector<std::pair<int, int>> seen;
+  seen.reserve(H);
+  for (int h = 0; h < H; ++h) {
+    int a = d->hand_cards[h * k], b = k == 2 ? d->hand_cards[h * k + 1] : -1;
+    if (a < 0 || a >= d->n_cards || (k == 2 && (b < 0 || b >= d->n_cards)))
+      return fail(EGT_ERR_INVALID_ARG, "card id out of range at hand " + std::to_string(h));
+    if (k == 2 && a == b) return fail(EGT_ERR_INVALID_ARG, "repeated card in hand " + std::to_string(h));
+    if (k == 2 && a > b) std::swap(a, b);
+    seen.push_back({a, b});
+  }
+  std::sort(seen.begin(), seen.end());
+  if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+    return fail(EGT_ERR_INVALID_ARG, "two hands hold the same cards");
+  for (int p = 0; p < 2; ++p) {
+    double tot = 0;
+    for (int h = 0; h < H; ++h) {
+      double r = d->range[p][h];
+      if (!(r >= 0) || !std::isfinite(r)) return fail(EGT_ERR_INVALID_ARG, "range entries must be finite and >= 0");
+      tot += r;
+    }
+    if (!(tot > 0)) return fail(EGT_ERR_INVALID_ARG, "a range is all zero");
+  }
+  return EGT_OK;
+}
+
+template <typename T>
+T* carve(char*& p, size_t n) {
+  p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 255) & ~uintptr_t(255));
+  T* out = reinterpret_cast<T*>(p);
+  p += n * sizeof(T);
+  return out;
+}
+
+// Host tables (card slots, tie groups, ranges, Z, ||A||, M, Omega, terminal CSR); with
+// to_device, uploaded as one device arena that G->dg points into.
+egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStream_t st) {
+  const int H = G->H, ld = G->ld, k = d->hand_size;
+  Compiled& C = G->comp;
+
+  // card slots: live cards in ascending id, plus an empty slot (padding, 1-card hands)
+  std::vector<int> slot_of(d->n_cards, -1);
+  for (int h = 0; h < H; ++h)
+    for (int c = 0; c < k; ++c) slot_of[d->hand_cards[h * k + c]] = 1;
+  int ns = 0;
+  for (int c = 0; c < d->n_cards; ++c)
+    if (slot_of[c] > 0) slot_of[c] = ns++;
+  const int empty = ns;
+  G->n_slots = ns + 1;
+  if (G->n_slots > 255) return fail(EGT_ERR_INVALID_ARG, "more than 254 live cards");
+
+  std::vector<uchar2> hcard(ld);
+  std::vector<std::vector<int>> lists(G->n_slots);
+  for (int s = 0; s < ld; ++s) {
+    if (s < H) {
+      const int h = G->order[s];
+      const int a = slot_of[d->hand_cards[h * k]];
+      const int b = k == 2 ? slot_of[d->hand_cards[h * k + 1]] : empty;
+      hcard[s] = make_uchar2((unsigned char)a, (unsigned char)b);
+      lists[a].push_back(s);
+      if (k == 2) lists[b].push_back(s);
+    } else {
+      hcard[s] = make_uchar2((unsigned char)empty, (unsigned char)empty);
+    }
+  }
+  G->lmax = 1;
+  for (auto& l : lists) G->lmax = std::max<int>(G->lmax, (int)l.size());
+  if (G->lmax > kMaxListLen) return fail(EGT_ERR_INVALID_ARG, "a card is held by more than 64 hands");
+
+  // tie groups in sorted order; padding forms one group at the end
+  std::vector<ushort2> grp(ld);
+  for (int s = 0; s < H;) {
+    int e = s;
+    const int str = d->strength[G->order[s]];
+    while (e < H && d->strength[G->order[e]] == str) ++e;
+    for (int i = s; i < e; ++i) grp[i] = make_ushort2((unsigned short)s, (unsigned short)e);
+    s = e;
+  }
+  for (int s = H; s < ld; ++s) grp[s] = make_ushort2((unsigned short)H, (unsigned short)ld);
+
+  std::vector<uchar4> cpos(ld, make_uchar4(0, 0, 0, 0));
+  auto count_below = [&](int slot, int bound) {
+    const auto& l = lists[slot];
+    return (unsigned char)(std::lower_bound(l.begin(), l.end(), bound) - l.begin());
+  };
+  for (int s = 0; s < H; ++s) {
+    cpos[s] = make_uchar4(count_below(hcard[s].x, grp[s].x), count_below(hcard[s].x, grp[s].y),
+                          count_below(hcard[s].y, grp[s].x), count_below(hcard[s].y, grp[s].y));
+  }
+  std::vector<uint16_t> card_hands((size_t)G->n_slots * G->lmax, 0);
+  std::vector<int> card_len(G->n_slots);
+  for (int c = 0; c < G->n_slots; ++c) {
+    card_len[c] = (int)lists[c].size();
+    for (size_t i = 0; i < lists[c].size(); ++i) card_hands[(size_t)c * G->lmax + i] = (uint16_t)lists[c][i];
+  }
+
+  // ranges: normalised, Z by inclusion-exclusion over shared cards
+  std::vector<double> r[2];
+  std::vector<double> per_card[2];
+  double R[2];
+  for (int p = 0; p < 2; ++p) {
+    r[p].assign(ld, 0.0);
+    double tot = 0;
+    for (int h = 0; h < H; ++h) tot += d->range[p][h];
+    for (int s = 0; s < H; ++s) r[p][s] = d->range[p][G->order[s]] / tot;
+    R[p] = 0;
+    for (int s = 0; s < H; ++s) R[p] += r[p][s];
+    per_card[p].assign(G->n_slots, 0.0);
+    for (int s = 0; s < H; ++s) {
+      per_card[p][hcard[s].x] += r[p][s];
+      if (k == 2) per_card[p][hcard[s].y] += r[p][s];
+    }
+  }
+  double Z = R[0] * R[1];
+  for (int c = 0; c < ns; ++c) Z -= per_card[0][c] * per_card[1][c];
+  if (k == 2)
+    for (int s = 0; s < H; ++s) Z += r[0][s] * r[1][s];
+  if (!(Z > 0)) return fail(EGT_ERR_INVALID_ARG, "no compatible hand pair has positive probability (Z = 0)");
+  G->Z = Z;
+
+  // ||A|| = max_ij |A_ij|: largest |coef| of each terminal kind times the largest chance weight
+  double max_any = 0, max_diff = 0;
+  for (int a = 0; a < H; ++a)
+    for (int b = 0; b < H; ++b) {
+      const bool share = hcard[a].x == hcard[b].x || (k == 2 && (hcard[a].x == hcard[b].y ||
+                                                                 hcard[a].y == hcard[b].x ||
+                                                                 hcard[a].y == hcard[b].y));
+      if (share) continue;
+      const double w = r[0][a] * r[1][b];
+      max_any = std::max(max_any, w);
+      if (d->strength[G->order[a]] != d->strength[G->order[b]]) max_diff = std::max(max_diff, w);
+    }
+  double na = 0;
+  for (auto& t : C.term) na = std::max(na, std::fabs(t.coef) * (t.kind == 0 ? max_any : max_diff));
+  G->normA = na / Z;
+  for (int p = 0; p < 2; ++p) {
+    G->M[p] = H * C.tpx[p].m_root;
+    G->Omega[p] = H * C.tpx[p].omega_root;
+  }
+
+  // terminals grouped by each player's own sequence
+  std::vector<int> tptr[2], topp[2], tkind[2];
+  std::vector<float> tcoef[2];
+  std::vector<double> tcoef64[2];
+  for (int p = 0; p < 2; ++p) {
+    const int S = C.tpx[p].S;
+    tptr[p].assign(S + 1, 0);
+    for (auto& t : C.term) tptr[p][t.seq[p] + 1]++;
+    for (int s = 0; s < S; ++s) tptr[p][s + 1] += tptr[p][s];
+    std::vector<int> fill(tptr[p].begin(), tptr[p].end() - 1);
+    const int n = (int)C.term.size();
+    topp[p].resize(n);
+    tkind[p].resize(n);
+    tcoef[p].resize(n);
+    tcoef64[p].resize(n);
+    for (auto& t : C.term) {
+      const int e = fill[t.seq[p]]++;
+      topp[p][e] = t.seq[1 - p];
+      tkind[p][e] = t.kind;
+      // showdown: payoff to player 2 is +stake when player 2 is stronger; the kernel forms
+      // (stronger - weaker) from the output hand's view, so player 2's rows flip the sign
+      const double c = t.kind == 0 ? t.coef : (p == 0 ? t.coef : -t.coef);
+      tcoef64[p][e] = c;
+      tcoef[p][e] = (float)c;
+    }
+  }
+
+  // sizes of the arena
+  std::vector<float> rf[2], rzf[2];
+  std::vector<double> rz64[2];
+  for (int p = 0; p < 2; ++p) {
+    rf[p].resize(ld);
+    rzf[p].resize(ld);
+    rz64[p].resize(ld);
+    for (int s = 0; s < ld; ++s) {
+      rf[p][s] = (float)r[p][s];
+      rz64[p][s] = r[p][s] / Z;
+      rzf[p][s] = (float)rz64[p][s];
+    }
+  }
+  struct TpxHost {
+    std::vector<float> log_n;
+  } th[2];
+  for (int p = 0; p < 2; ++p) {
+    th[p].log_n.resize(C.tpx[p].J);
+    for (int j = 0; j < C.tpx[p].J; ++j) th[p].log_n[j] = (float)std::log((double)C.tpx[p].inf_n[j]);
+  }
+
+  if (!to_device) return EGT_OK;
+  size_t bytes = 1 << 16;
+  bytes += ld * (sizeof(uchar2) + sizeof(ushort2) + sizeof(uchar4)) + card_hands.size() * 2 + card_len.size() * 4;
+  for (int p = 0; p < 2; ++p) {
+    bytes += ld * (2 * sizeof(float) + 2 * sizeof(double));
+    const Treeplex& T = C.tpx[p];
+    bytes += (4 * T.J + T.L + 1 + T.S + 1 + T.child_idx.size()) * sizeof(int) + T.J * (sizeof(double) + sizeof(float));
+    bytes += (tptr[p].size() + 2 * topp[p].size()) * sizeof(int) + tcoef[p].size() * (sizeof(float) + sizeof(double));
+  }
+  bytes += 64 * 256;   // alignment slack
+  std::vector<char> host(bytes, 0);
+  CUDA_TRY(cudaMalloc(&G->arena, bytes));
+  char* hp = host.data();
+  const uintptr_t base_h = reinterpret_cast<uintptr_t>(host.data());
+  const uintptr_t base_d = reinterpret_cast<uintptr_t>(G->arena);
+  bool overflow = false;
+  auto put = [&](const void* src, size_t nbytes) -> const void* {
+    hp = reinterpret_cast<char*>(base_h + ((reinterpret_cast<uintptr_t>(hp) - base_h + 255) & ~uintptr_t(255)));
+    if ((size_t)(reinterpret_cast<uintptr_t>(hp) - base_h) + nbytes > bytes) {
+      overflow = true;
+      return nullptr;
+    }
+    if (nbytes) std::memcpy(hp, src, nbytes);
+    const void* dev = reinterpret_cast<const void*>(base_d + (reinterpret_cast<uintptr_t>(hp) - base_h));
+    hp += nbytes;
+    return dev;
+  };
+  DevGame& g = G->dg;
+  g.H = H;
+  g.ld = ld;
+  g.hand_size = k;
+  g.n_slots = G->n_slots;
+  g.lmax = G->lmax;
+  g.hcard = (const uchar2*)put(hcard.data(), ld * sizeof(uchar2));
+  g.grp = (const ushort2*)put(grp.data(), ld * sizeof(ushort2));
+  g.cpos = (const uchar4*)put(cpos.data(), ld * sizeof(uchar4));
+  g.card_hands = (const uint16_t*)put(card_hands.data(), card_hands.size() * 2);
+  g.card_len = (const int*)put(card_len.data(), card_len.size() * 4);
+  for (int p = 0; p < 2; ++p) {
+    g.r[p] = (const float*)put(rf[p].data(), ld * 4);
+    g.rz[p] = (const float*)put(rzf[p].data(), ld * 4);
+    g.r64[p] = (const double*)put(r[p].data(), ld * 8);
+    g.rz64[p] = (const double*)put(rz64[p].data(), ld * 8);
+    const Treeplex& T = C.tpx[p];
+    DevTpx& dt = g.tpx[p];
+    dt.S = T.S;
+    dt.J = T.J;
+    dt.L = T.L;
+    dt.inf_parent = (const int*)put(T.inf_parent.data(), T.J * 4);
+    dt.inf_first = (const int*)put(T.inf_first.data(), T.J * 4);
+    dt.inf_n = (const int*)put(T.inf_n.data(), T.J * 4);
+    dt.level_ptr = (const int*)put(T.level_ptr.data(), (T.L + 1) * 4);
+    dt.child_ptr = (const int*)put(T.child_ptr.data(), (T.S + 1) * 4);
+    dt.child_idx = (const int*)put(T.child_idx.data(), T.child_idx.size() * 4);
+    dt.beta = (const double*)put(T.beta.data(), T.J * 8);
+    dt.log_n = (const float*)put(th[p].log_n.data(), T.J * 4);
+    DevTerms& tm = g.terms[p];
+    tm.ptr = (const int*)put(tptr[p].data(), tptr[p].size() * 4);
+    tm.opp_seq = (const int*)put(topp[p].data(), topp[p].size() * 4);
+    tm.kind = (const int*)put(tkind[p].data(), tkind[p].size() * 4);
+    tm.coef = (const float*)put(tcoef[p].data(), tcoef[p].size() * 4);
+    tm.coef64 = (const double*)put(tcoef64[p].data(), tcoef64[p].size() * 8);
+  }
+  const size_t used = reinterpret_cast<uintptr_t>(hp) - base_h;
+  if (overflow || used > bytes) return fail(EGT_ERR_INVALID_ARG, "internal: table arena overflow");
+  CUDA_TRY(cudaMemcpyAsync(G->arena, host.data(), used, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return EGT_OK;
+}
+
+egt_status alloc_state(egt_game* G) {
+  const size_t n0 = vec_elems(G, 0), n1 = vec_elems(G, 1);
+  // x[2], gy[2]... sized by their player: x, gx, tx are player 0; y, gy, ty are player 1
+  const size_t total = 5 * (n0 + 64) + 5 * (n1 + 64);   // each vector rounded up to 64 floats
+  CUDA_TRY(cudaMalloc(&G->vec, total * sizeof(float)));
+  CUDA_TRY(cudaMemset(G->vec, 0, total * sizeof(float)));
+  float* p = G->vec;
+  auto take = [&](size_t n) {
+    float* q = p;
+    p += (n + 63) / 64 * 64;
+    return q;
+  };
+  for (int i = 0; i < 2; ++i) {
+    G->x[i] = take(n0);
+    G->gx[i] = take(n0);
+    G->y[i] = take(n1);
+    G->gy[i] = take(n1);
+  }
+  G->tx = take(n0);
+  G->ty = take(n1);
+  CUDA_TRY(cudaMalloc(&G->g64[0], n0 * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&G->g64[1], n1 * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&G->partials, 1024 * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&G->counter, 16 * sizeof(unsigned int)));
+  CUDA_TRY(cudaMemset(G->counter, 0, 16 * sizeof(unsigned int)));
+  CUDA_TRY(cudaMalloc(&G->vals, 16 * sizeof(double)));
+  CUDA_TRY(cudaMemset(G->vals, 0, 16 * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&G->status, sizeof(int)));
+  CUDA_TRY(cudaMemset(G->status, 0, sizeof(int)));
+  CUDA_TRY(cudaHostAlloc(&G->pinned, 16 * sizeof(double), cudaHostAllocDefault));
+  return EGT_OK;
+}
+
+void free_game(egt_game* G) {
+  if (!G) return;
+  if (G->host_only) {
+    delete G;
+    return;
+  }
+  cudaFree(G->arena);
+  cudaFree(G->vec);
+  cudaFree(G->g64[0]);
+  cudaFree(G->g64[1]);
+  cudaFree(G->partials);
+  cudaFree(G->counter);
+  cudaFree(G->vals);
+  cudaFree(G->status);
+  if (G->pinned) cudaFreeHost(G->pinned);
+  delete G;
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+egt_status check_player(int p) {
+  if (p != 0 && p != 1) return fail(EGT_ERR_INVALID_ARG, "player must be 0 or 1");
+  return EGT_OK;
+}
+
+egt_status check_ptr(const void* p, const char* name) {
+  if (!p) return fail(EGT_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(p) & 15) return fail(EGT_ERR_INVALID_ARG, std::string(name) + " is not 16-byte aligned");
+  return EGT_OK;
+}
+
+// ---- internal launches (no argument checks) ----
+
+egt_status grad32(egt_game* G, int player, const float* in, float* out, cudaStream_t st) {
+  launch_grad<float, float>(G->dg, player, in, out, st);
+  G->products++;
+  return check_launch("grad kernel");
+}
+
+// SBR of player p with loss gradient sign * g (player 1 receives A^T x and negates).
+egt_status sbr(egt_game* G, int p, const float* g, double mu, const float* old, double tau,
+               float* out, int value_slot, cudaStream_t st) {
+  SbrArgs a{};
+  a.g = g;
+  a.sign = p == 0 ? 1.f : -1.f;
+  a.mu = mu;
+  a.old = old;
+  a.tau = (float)tau;
+  a.out = out;
+  a.value_dev = value_slot >= 0 ? G->vals + value_slot : nullptr;
+  a.partials = G->partials;
+  a.counter = G->counter;
+  a.status = G->status;
+  launch_sbr(G->dg, p, a, st);
+  return check_launch("sbr kernel");
+}
+
+// Copy value slots [first, first + n) to the pinned host buffer and check them.
+egt_status read_vals(egt_game* G, int first, int n, cudaStream_t st) {
+  CUDA_TRY(cudaMemcpyAsync(G->pinned + first, G->vals + first, n * sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = first; i < first + n; ++i)
+    if (!std::isfinite(G->pinned[i])) return fail(EGT_ERR_NUMERIC, "non-finite value in a best response");
+  return EGT_OK;
+}
+
+egt_status gap_internal(egt_game* G, const float* x, const float* y, double* gap_mbb, cudaStream_t st) {
+  launch_grad<float, double>(G->dg, 0, y, G->g64[0], st);   // A y
+  EGT_TRY(check_launch("grad f64 kernel"));
+  launch_grad<float, double>(G->dg, 1, x, G->g64[1], st);   // A^T x
+  EGT_TRY(check_launch("grad f64 kernel"));
+  launch_br64(G->dg, 0, G->g64[0], 1.0, G->vals + 8, G->partials, G->counter, st);    // min_x <x, Ay>
+  EGT_TRY(check_launch("br kernel"));
+  launch_br64(G->dg, 1, G->g64[1], -1.0, G->vals + 9, G->partials, G->counter, st);   // max_y <y, A^T x>
+  EGT_TRY(check_launch("br kernel"));
+  CUDA_TRY(cudaMemcpyAsync(G->pinned + 8, G->vals + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  const double eps = G->pinned[9] - G->pinned[8];
+  if (!std::isfinite(eps)) return fail(EGT_ERR_NUMERIC, "non-finite saddle-point residual");
+  *gap_mbb = eps / G->bb * 1000.0;
+  return EGT_OK;
+}
+
+// Initial point (Alg. 1 / 3 first lines) at the given mu; leaves x, y, Ay, A^T x in slot cur.
+egt_status init_point(egt_game* G, cudaStream_t st) {
+  const int c = G->cur;
+  EGT_TRY(sbr(G, 0, nullptr, 1.0, nullptr, 0, G->tx, -1, st));          // x_omega (uniform)
+  EGT_TRY(grad32(G, 1, G->tx, G->gy[c], st));                            // A^T x_omega
+  EGT_TRY(sbr(G, 1, G->gy[c], G->mu[1], nullptr, 0, G->y[c], -1, st));    // y0 = y_mu_y(x_omega)
+  EGT_TRY(grad32(G, 0, G->y[c], G->gx[c], st));                          // A y0
+  EGT_TRY(sbr(G, 0, G->gx[c], G->mu[0], nullptr, 0, G->x[c], 0, st));     // x0 = x_mu_x(y0), phi
+  EGT_TRY(grad32(G, 1, G->x[c], G->gy[c], st));                          // A^T x0
+  return EGT_OK;
+}
+
+// EGV(x, y) of the current state = phi_mu_x(y) - f_mu_y(x); slot 0 must hold phi already.
+egt_status current_egv(egt_game* G, double* egv, cudaStream_t st) {
+  const int c = G->cur;
+  EGT_TRY(sbr(G, 1, G->gy[c], G->mu[1], nullptr, 0, nullptr, 1, st));   // value of SBR_Y(-A^T x) = -f
+  EGT_TRY(read_vals(G, 0, 2, st));
+  *egv = G->pinned[0] + G->pinned[1];
+  return EGT_OK;
+}
+
+// One Step (Alg. 2) focused on `me` at tau, from state slot cur into slot 1 - cur.
+// Products are taken of the new iterates directly, so the cached A y / A^T x of the
+// state are always products of its own iterates.  With want_egv, the EGV of the
+// new point is left in value slots 2 (phi) and 3 (-f).
+egt_status step_once(egt_game* G, int me, double tau, bool want_egv, cudaStream_t st) {
+  const int c = G->cur, n = 1 - c;
+  const double mx = G->mu[0], my = G->mu[1];
+  if (me == 0) {
+    // x_hat = (1-tau) x + tau x_mu_x(y)
+    EGT_TRY(sbr(G, 0, G->gx[c], mx, G->x[c], tau, G->tx, -1, st));
+    EGT_TRY(grad32(G, 1, G->tx, G->ty, st));                               // A^T x_hat
+    // y_+ = (1-tau) y + tau y_mu_y(x_hat)
+    EGT_TRY(sbr(G, 1, G->ty, my, G->y[c], tau, G->y[n], -1, st));
+    EGT_TRY(grad32(G, 0, G->y[n], G->gx[n], st));                          // A y_+
+    // x_tilde = x_{(1-tau) mu_x}(y_+); x_+ = (1-tau) x + tau x_tilde; value = phi_{mu_x+}(y_+)
+    EGT_TRY(sbr(G, 0, G->gx[n], (1 - tau) * mx, G->x[c], tau, G->x[n], 2, st));
+    EGT_TRY(grad32(G, 1, G->x[n], G->gy[n], st));                          // A^T x_+
+    if (want_egv) EGT_TRY(sbr(G, 1, G->gy[n], my, nullptr, 0, nullptr, 3, st));   // -f_mu_y(x_+)
+  } else {
+    EGT_TRY(sbr(G, 1, G->gy[c], my, G->y[c], tau, G->ty, -1, st));        // y_hat
+    EGT_TRY(grad32(G, 0, G->ty, G->tx, st));                               // A y_hat
+    EGT_TRY(sbr(G, 0, G->tx, mx, G->x[c], tau, G->x[n], -1, st));          // x_+
+    EGT_TRY(grad32(G, 1, G->x[n], G->gy[n], st));                          // A^T x_+
+    // y_tilde = y_{(1-tau) mu_y}(x_+), y_+; value = -f_{mu_y+}(x_+)
+    EGT_TRY(sbr(G, 1, G->gy[n], (1 - tau) * my, G->y[c], tau, G->y[n], 3, st));
+    EGT_TRY(grad32(G, 0, G->y[n], G->gx[n], st));                          // A y_+
+    if (want_egv) EGT_TRY(sbr(G, 0, G->gx[n], mx, nullptr, 0, nullptr, 2, st));   // phi_mu_x(y_+)
+  }
+  return EGT_OK;
+}
+
+egt_status do_step(egt_game* G, int player, double* tau_io, int mode, egt_step_info* info,
+                   cudaStream_t st) {
+  if (!G->initialised) return fail(EGT_ERR_INVALID_ARG, "egt_solver_init has not been called");
+  if (!tau_io || !(*tau_io > 0) || !(*tau_io < 1)) return fail(EGT_ERR_INVALID_ARG, "tau must be in (0, 1)");
+  if (mode < 0 || mode > 2) return fail(EGT_ERR_INVALID_ARG, "unknown step mode");
+  const int me = player < 0 ? (G->mu[0] > G->mu[1] ? 0 : 1) : player;
+  if (me != 0 && me != 1) return fail(EGT_ERR_INVALID_ARG, "player must be -1, 0 or 1");
+  const long long p0 = G->products;
+  double tau = *tau_io, egv = NAN;
+  int backoffs = 0;
+  bool accepted = true;
+  for (;;) {
+    EGT_TRY(step_once(G, me, tau, mode != EGT_STEP_PLAIN, st));
+    if (mode == EGT_STEP_PLAIN) break;
+    EGT_TRY(read_vals(G, 2, 2, st));
+    egv = G->pinned[2] + G->pinned[3];
+    if (egv >= 0) break;
+    if (mode == EGT_STEP_CHECK) {
+      accepted = false;
+      break;
+    }
+    tau *= 0.5;
+    ++backoffs;
+    if (tau < kTauMin) return fail(EGT_ERR_TAU_UNDERFLOW, "Decr halved tau below 2^-30");
+  }
+  if (accepted) {
+    G->mu[me] *= (1.0 - tau);
+    G->cur = 1 - G->cur;
+  }
+  *tau_io = tau;
+  if (info) {
+    info->player = me;
+    info->accepted = accepted ? 1 : 0;
+    info->backoffs = backoffs;
+    info->products = (int32_t)(G->products - p0);
+    info->tau = tau;
+    info->egv = egv;
+    info->mu[0] = G->mu[0];
+    info->mu[1] = G->mu[1];
+  }
+  return EGT_OK;
+}
+
+egt_status solver_init(egt_game* G, const egt_solve_opts* o, cudaStream_t st) {
+  if (!o) return fail(EGT_ERR_INVALID_ARG, "opts is NULL");
+  if (o->variant < 0 || o->variant > 2) return fail(EGT_ERR_INVALID_ARG, "unknown variant");
+  const double theory = G->normA * std::sqrt(G->M[0] * G->M[1]);
+  const bool given = o->mu0[0] > 0 && o->mu0[1] > 0;
+  if (given) {
+    G->mu[0] = o->mu0[0];
+    G->mu[1] = o->mu0[1];
+  } else if (o->variant == EGT_THEORY) {
+    G->mu[0] = G->mu[1] = theory;
+  } else {
+    if (!(o->alpha > 0)) return fail(EGT_ERR_INVALID_ARG, "alpha must be > 0");
+    G->mu[0] = G->mu[1] = o->alpha * theory;
+  }
+  if (!(G->mu[0] > 0) || !(G->mu[1] > 0) || !std::isfinite(G->mu[0]) || !std::isfinite(G->mu[1]))
+    return fail(EGT_ERR_INVALID_ARG, "initial mu must be finite and > 0");
+  G->cur = 0;
+  EGT_TRY(init_point(G, st));
+  if (!given && o->variant != EGT_THEORY) {
+    for (int k = 0;; ++k) {
+      double egv;
+      EGT_TRY(current_egv(G, &egv, st));
+      if (egv >= 0) break;
+      if (k > 200) return fail(EGT_ERR_NUMERIC, "initial mu guard did not reach EGV >= 0");
+      G->mu[0] *= 2;
+      G->mu[1] *= 2;
+      EGT_TRY(init_point(G, st));
+    }
+  }
+  G->initialised = true;
+  return EGT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* egt_last_error(void) { return g_last_error.c_str(); }
+
+egt_status egt_create_game(const egt_game_desc* desc, int32_t device, void* stream, egt_game** out) {
+  if (!out) return fail(EGT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  EGT_TRY(validate(desc));
+  const bool host_only = device == -1;
+  if (!host_only) {
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(EGT_ERR_INVALID_ARG, "no such device");
+  }
+  DeviceGuard guard(host_only ? -1 : device);
+  if (!host_only && !guard.ok) return fail(EGT_ERR_CUDA, "cudaSetDevice failed");
+  egt_game* G = new (std::nothrow) egt_game();
+  if (!G) return fail(EGT_ERR_OOM, "host allocation failed");
+  G->device = device;
+  G->host_only = host_only;
+  G->H = desc->n_hands;
+  G->ld = (desc->n_hands + 31) / 32 * 32;
+  G->hand_size = desc->hand_size;
+  G->bb = desc->bb;
+  G->pot = desc->pot;
+  if (G->ld > kMaxLd) {
+    delete G;
+    return fail(EGT_ERR_INVALID_ARG, "n_hands above 2048");
+  }
+  std::string err = compile_betting(desc->pot, desc->stack, desc->bet_fracs, desc->n_bets,
+                                    desc->allin != 0, desc->raise_cap, G->comp);
+  if (!err.empty()) {
+    delete G;
+    return fail(EGT_ERR_INVALID_ARG, err);
+  }
+  G->order.resize(G->H);
+  std::iota(G->order.begin(), G->order.end(), 0);
+  std::stable_sort(G->order.begin(), G->order.end(),
+                   [&](int a, int b) { return desc->strength[a] < desc->strength[b]; });
+  egt_status st = upload(G, desc, !host_only, S(stream));
+  if (st == EGT_OK && !host_only) st = alloc_state(G);
+  if (st == EGT_OK && !host_only) {
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    for (int p = 0; p < 2 && st == EGT_OK; ++p)
+      if (sbr_smem_bytes(G->dg, p) > (size_t)dev_smem || br_smem_bytes(G->dg, p) > (size_t)dev_smem)
+        st = fail(EGT_ERR_INVALID_ARG, "betting tree too large for the shared-memory SBR tile");
+    if (st == EGT_OK && grad_smem_bytes(G->dg, true) > (size_t)std::min(dev_smem, 200 * 1024))
+      st = fail(EGT_ERR_INVALID_ARG, "hand count too large for the shared-memory gradient tile");
+  }
+  if (st != EGT_OK) {
+    std::string keep = g_last_error;
+    free_game(G);
+    g_last_error = keep;
+    return st;
+  }
+  *out = G;
+  return EGT_OK;
+}
+
+egt_status egt_destroy_game(egt_game* game) {
+  if (!game) return EGT_OK;
+  if (!game->host_only) {
+    DeviceGuard guard(game->device);
+    cudaDeviceSynchronize();
+    free_game(game);
+  } else {
+    free_game(game);
+  }
+  return EGT_OK;
+}
+
+egt_status egt_dims_query(const egt_game* G, egt_dims* o) {
+  if (!G || !o) return fail(EGT_ERR_INVALID_ARG, "NULL argument");
+  o->H = G->H;
+  o->ld = G->ld;
+  for (int p = 0; p < 2; ++p) {
+    o->S[p] = G->comp.tpx[p].S;
+    o->J[p] = G->comp.tpx[p].J;
+    o->L[p] = G->comp.tpx[p].L;
+    o->M[p] = G->M[p];
+    o->Omega[p] = G->Omega[p];
+  }
+  o->T = (int32_t)G->comp.term.size();
+  o->n_fold = 0;
+  for (auto& t : G->comp.term) o->n_fold += t.kind == 0;
+  o->Z = G->Z;
+  o->normA = G->normA;
+  return EGT_OK;
+}
+
+egt_status egt_hand_order(const egt_game* G, int32_t* order) {
+  if (!G || !order) return fail(EGT_ERR_INVALID_ARG, "NULL argument");
+  std::copy(G->order.begin(), G->order.end(), order);
+  return EGT_OK;
+}
+
+egt_status egt_treeplex_query(const egt_game* G, int32_t player, int32_t* parent, int32_t* first,
+                              int32_t* n_actions, int32_t* level, double* beta) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  EGT_TRY(check_player(player));
+  const Treeplex& T = G->comp.tpx[player];
+  for (int j = 0; j < T.J; ++j) {
+    if (parent) parent[j] = T.inf_parent[j];
+    if (first) first[j] = T.inf_first[j];
+    if (n_actions) n_actions[j] = T.inf_n[j];
+    if (level) level[j] = T.inf_level[j];
+    if (beta) beta[j] = T.beta[j];
+  }
+  return EGT_OK;
+}
+
+egt_status egt_terminal_query(const egt_game* G, int32_t* seq1, int32_t* seq2, int32_t* kind, double* coef) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  for (size_t b = 0; b < G->comp.term.size(); ++b) {
+    const Terminal& t = G->comp.term[b];
+    if (seq1) seq1[b] = t.seq[0];
+    if (seq2) seq2[b] = t.seq[1];
+    if (kind) kind[b] = t.kind;
+    if (coef) coef[b] = t.coef;
+  }
+  return EGT_OK;
+}
+
+egt_status egt_grad(egt_game* G, int32_t player, const float* in, float* out, void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  EGT_TRY(check_player(player));
+  EGT_TRY(check_ptr(in, "in"));
+  EGT_TRY(check_ptr(out, "out"));
+  if (in == out) return fail(EGT_ERR_INVALID_ARG, "in and out must differ");
+  DeviceGuard guard(G->device);
+  return grad32(G, player, in, out, S(stream));
+}
+
+egt_status egt_grad_f64(egt_game* G, int32_t player, const double* in, double* out, void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  EGT_TRY(check_player(player));
+  EGT_TRY(check_ptr(in, "in"));
+  EGT_TRY(check_ptr(out, "out"));
+  if ((const void*)in == (const void*)out) return fail(EGT_ERR_INVALID_ARG, "in and out must differ");
+  DeviceGuard guard(G->device);
+  launch_grad<double, double>(G->dg, player, in, out, S(stream));
+  return check_launch("grad f64 kernel");
+}
+
+egt_status egt_smoothed_br(egt_game* G, int32_t player, const float* g, double mu, float* q_out,
+                           double* value_out, void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  EGT_TRY(check_player(player));
+  EGT_TRY(check_ptr(g, "g"));
+  if (q_out) EGT_TRY(check_ptr(q_out, "q_out"));
+  if (!(mu > 0) || !std::isfinite(mu)) return fail(EGT_ERR_INVALID_ARG, "mu must be finite and > 0");
+  DeviceGuard guard(G->device);
+  EGT_TRY(sbr(G, player, g, mu, nullptr, 0, q_out, value_out ? 4 : -1, S(stream)));
+  if (value_out) {
+    EGT_TRY(read_vals(G, 4, 1, S(stream)));
+    // player 1's kernel solved min <y, -g> + mu d(y); its own maximum is the negation
+    *value_out = player == 0 ? G->pinned[4] : -G->pinned[4];
+  }
+  return EGT_OK;
+}
+
+egt_status egt_best_response_f64(egt_game* G, int32_t player, const double* g, double* value_out,
+                                 void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  EGT_TRY(check_player(player));
+  EGT_TRY(check_ptr(g, "g"));
+  if (!value_out) return fail(EGT_ERR_INVALID_ARG, "value_out is NULL");
+  DeviceGuard guard(G->device);
+  launch_br64(G->dg, player, g, player == 0 ? 1.0 : -1.0, G->vals + 10, G->partials, G->counter,
+              S(stream));
+  EGT_TRY(check_launch("br kernel"));
+  CUDA_TRY(cudaMemcpyAsync(G->pinned + 10, G->vals + 10, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
+  CUDA_TRY(cudaStreamSynchronize(S(stream)));
+  *value_out = G->pinned[10];
+  return EGT_OK;
+}
+
+egt_status egt_gap(egt_game* G, const float* x, const float* y, double* gap_mbb, void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  EGT_TRY(check_ptr(x, "x"));
+  EGT_TRY(check_ptr(y, "y"));
+  if (!gap_mbb) return fail(EGT_ERR_INVALID_ARG, "gap_mbb is NULL");
+  DeviceGuard guard(G->device);
+  return gap_internal(G, x, y, gap_mbb, S(stream));
+}
+
+egt_status egt_solver_init(egt_game* G, const egt_solve_opts* opts, void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  DeviceGuard guard(G->device);
+  return solver_init(G, opts, S(stream));
+}
+
+egt_status egt_step(egt_game* G, int32_t player, double* tau_inout, int32_t mode, egt_step_info* info,
+                    void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  DeviceGuard guard(G->device);
+  return do_step(G, player, tau_inout, mode, info, S(stream));
+}
+
+egt_status egt_state_get(egt_game* G, float* x, float* y, double* mu, void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  if (!G->initialised) return fail(EGT_ERR_INVALID_ARG, "egt_solver_init has not been called");
+  DeviceGuard guard(G->device);
+  const int c = G->cur;
+  if (x) CUDA_TRY(cudaMemcpyAsync(x, G->x[c], vec_elems(G, 0) * 4, cudaMemcpyDeviceToDevice, S(stream)));
+  if (y) CUDA_TRY(cudaMemcpyAsync(y, G->y[c], vec_elems(G, 1) * 4, cudaMemcpyDeviceToDevice, S(stream)));
+  if (mu) {
+    mu[0] = G->mu[0];
+    mu[1] = G->mu[1];
+  }
+  return EGT_OK;
+}
+
+egt_status egt_state_set(egt_game* G, const float* x, const float* y, const double* mu, void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  EGT_TRY(check_ptr(x, "x"));
+  EGT_TRY(check_ptr(y, "y"));
+  if (!mu || !(mu[0] > 0) || !(mu[1] > 0)) return fail(EGT_ERR_INVALID_ARG, "mu must be > 0");
+  DeviceGuard guard(G->device);
+  const int c = G->cur;
+  cudaStream_t st = S(stream);
+  CUDA_TRY(cudaMemcpyAsync(G->x[c], x, vec_elems(G, 0) * 4, cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(G->y[c], y, vec_elems(G, 1) * 4, cudaMemcpyDeviceToDevice, st));
+  G->mu[0] = mu[0];
+  G->mu[1] = mu[1];
+  EGT_TRY(grad32(G, 0, G->y[c], G->gx[c], st));
+  EGT_TRY(grad32(G, 1, G->x[c], G->gy[c], st));
+  G->initialised = true;
+  return EGT_OK;
+}
+
+egt_status egt_solve(egt_game* G, const egt_solve_opts* o, float* x_out, float* y_out,
+                     egt_solve_report* rep, void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  if (!o) return fail(EGT_ERR_INVALID_ARG, "opts is NULL");
+  if (o->max_iters < 0) return fail(EGT_ERR_INVALID_ARG, "max_iters < 0");
+  if (o->replay_n > 0 && (!o->replay_player || !o->replay_tau))
+    return fail(EGT_ERR_INVALID_ARG, "replay arrays are NULL");
+  if (x_out) EGT_TRY(check_ptr(x_out, "x_out"));
+  if (y_out) EGT_TRY(check_ptr(y_out, "y_out"));
+  DeviceGuard guard(G->device);
+  cudaStream_t st = S(stream);
+  const auto t0 = std::chrono::steady_clock::now();
+  G->products = 0;
+  EGT_TRY(solver_init(G, o, st));
+  const int gap_every = std::max(1, o->gap_every);
+  int t = 0, backoffs = 0, gap_checks = 0;
+  double tau = 0.5, gap = INFINITY;
+  for (;;) {
+    if (t % gap_every == 0 || t >= o->max_iters) {
+      EGT_TRY(gap_internal(G, G->x[G->cur], G->y[G->cur], &gap, st));
+      ++gap_checks;
+    }
+    if ((o->eps_mbb > 0 && gap <= o->eps_mbb) || t >= o->max_iters || (o->replay_n > 0 && t >= o->replay_n))
+      break;
+    egt_step_info info{};
+    if (o->replay_n > 0) {
+      double tt = o->replay_tau[t];
+      EGT_TRY(do_step(G, o->replay_player[t], &tt, EGT_STEP_PLAIN, &info, st));
+    } else if (o->variant == EGT_THEORY) {
+      double tt = 2.0 / (t + 3);
+      EGT_TRY(do_step(G, t % 2 == 0 ? 0 : 1, &tt, EGT_STEP_PLAIN, &info, st));
+    } else if (o->variant == EGT_PRACTICAL) {
+      double tt = 2.0 / (t + 3);
+      EGT_TRY(do_step(G, -1, &tt, EGT_STEP_PLAIN, &info, st));
+    } else {
+      EGT_TRY(do_step(G, -1, &tau, EGT_STEP_DECR, &info, st));
+      backoffs += info.backoffs;
+    }
+    if (o->log && t < o->log_cap) {
+      egt_iter_log& L = o->log[t];
+      L.t = t;
+      L.player = info.player;
+      L.backoffs = info.backoffs;
+      L.tau = info.tau;
+      L.mu[0] = G->mu[0];
+      L.mu[1] = G->mu[1];
+      L.egv = info.egv;
+      L.gap_mbb = gap;
+    }
+    ++t;
+  }
+  if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, G->x[G->cur], vec_elems(G, 0) * 4, cudaMemcpyDeviceToDevice, st));
+  if (y_out) CUDA_TRY(cudaMemcpyAsync(y_out, G->y[G->cur], vec_elems(G, 1) * 4, cudaMemcpyDeviceToDevice, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (rep) {
+    rep->iters = t;
+    rep->products = (int32_t)G->products;
+    rep->backoffs = backoffs;
+    rep->gap_checks = gap_checks;
+    rep->gap_mbb = gap;
+    rep->mu[0] = G->mu[0];
+    rep->mu[1] = G->mu[1];
+    rep->tau = tau;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (o->eps_mbb > 0 && !(gap <= o->eps_mbb))
+    return fail(EGT_ERR_NOT_CONVERGED, "gap target not reached within max_iters");
+  return EGT_OK;
+}
+
+}  // extern "C"

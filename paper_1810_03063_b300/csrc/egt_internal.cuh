@@ -1,0 +1,84 @@
+// Device-side game tables and kernel entry points (internal to libegt).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace egt {
+
+constexpr int kGradThreads = 256;   // threads of a gradient CTA
+constexpr int kSbrHands = 32;       // hands per SBR CTA (one per lane)
+constexpr int kSbrWarps = 8;        // warps per SBR CTA (simplexes of a level split over them)
+constexpr int kMaxListLen = 64;     // max hands holding one card (two per lane in a warp scan)
+
+// One player's per-hand treeplex on the device (Sec. 4 notation).
+struct DevTpx {
+  int S, J, L;
+  const int* inf_parent;   // [J] p_j, -1 for a root simplex
+  const int* inf_first;    // [J] first sequence of I_j
+  const int* inf_n;        // [J] n_j
+  const int* level_ptr;    // [L+1]
+  const int* child_ptr;    // [S+1] CSR of D_j^i
+  const int* child_idx;
+  const double* beta;      // [J]
+  const float* log_n;      // [J] log n_j
+};
+
+// Terminals grouped by the sequence of the output player (CSR over that player's sequences).
+struct DevTerms {
+  const int* ptr;          // [S_p + 1]
+  const int* opp_seq;      // [n] opponent sequence of the terminal
+  const int* kind;         // [n] 0 fold, 1 showdown
+  const float* coef;       // [n] signed: fold payoff to player 2, showdown +-stake
+  const double* coef64;
+};
+
+struct DevGame {
+  int H, ld;               // hands, leading dimension (multiple of 32)
+  int hand_size;           // 1 or 2
+  int n_slots;             // card slots (live cards + 1 empty slot used by padding / 1-card hands)
+  int lmax;                // longest card list
+  const uchar2* hcard;     // [ld] card slots of each (sorted) hand
+  const ushort2* grp;      // [ld] tie group [lo, hi) in sorted order
+  const uchar4* cpos;      // [ld] hands of card k before lo / hi: (lo0, hi0, lo1, hi1)
+  const uint16_t* card_hands;  // [n_slots][lmax] sorted hand indices holding the card
+  const int* card_len;     // [n_slots]
+  const float* r[2];       // [ld] normalised ranges (0 on padding)
+  const float* rz[2];      // [ld] r / Z
+  const double* r64[2];
+  const double* rz64[2];
+  DevTpx tpx[2];
+  DevTerms terms[2];       // terms[p]: grouped by player p's sequences (output of player p)
+};
+
+// ---- kernels ----
+template <typename TIn, typename T>
+void launch_grad(const DevGame& g, int player, const TIn* in, T* out, cudaStream_t st);
+
+size_t grad_smem_bytes(const DevGame& g, bool f64);
+
+// SBR of player p on g (sign: +1 player 0, -1 player 1), temperature mu * beta_j.
+// g may be NULL (treated as 0: the uniform behavioural strategy).  If out is
+// non-NULL writes q, or (1 - tau) old + tau q when old is non-NULL.  If
+// value_dev is non-NULL writes sum over hands and root simplexes of the value
+// (FP64) to *value_dev, reducing per-CTA partials (partials[grid], counter).
+struct SbrArgs {
+  const float* g;
+  float sign;
+  double mu;
+  const float* old;
+  float tau;
+  float* out;
+  double* value_dev;
+  double* partials;
+  unsigned int* counter;
+  int* status;             // set to 1 if a value turns NaN / Inf
+};
+void launch_sbr(const DevGame& g, int player, const SbrArgs& a, cudaStream_t st);
+size_t sbr_smem_bytes(const DevGame& g, int player);
+
+// Plain best response value in FP64: sign * (min over the treeplex of <q, sign * g>).
+void launch_br64(const DevGame& g, int player, const double* gv, double sign, double* value_dev,
+                 double* partials, unsigned int* counter, cudaStream_t st);
+size_t br_smem_bytes(const DevGame& g, int player);
+
+}  // namespace egt

@@ -1,0 +1,308 @@
+"""Thin ctypes binding of libegt (include/egt.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  Device buffers are anything
+with a ``data_ptr()`` (torch tensors) or a raw integer address; streams are a
+``torch.cuda.Stream`` or a raw ``cudaStream_t`` integer (None = the current
+torch stream when torch is loaded, else the legacy default stream).
+
+Importing this module loads ``libegt.so`` and raises ImportError if it has not
+been built (``python -m paper_1810_03063_b300.build``): there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libegt.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "egt.h")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1810_03063_b300.build`")
+lib = C.CDLL(LIB_PATH)
+
+STATUS = {0: "EGT_OK", 1: "EGT_ERR_INVALID_ARG", 2: "EGT_ERR_OOM", 3: "EGT_ERR_CUDA",
+          4: "EGT_ERR_NUMERIC", 5: "EGT_ERR_TAU_UNDERFLOW", 6: "EGT_ERR_NOT_CONVERGED",
+          7: "EGT_ERR_TIMEOUT"}
+THEORY, PRACTICAL, EGT_AS = 0, 1, 2
+STEP_PLAIN, STEP_CHECK, STEP_DECR = 0, 1, 2
+
+
+class EGTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GameDesc(C.Structure):
+    _fields_ = [("n_cards", C.c_int32), ("hand_size", C.c_int32), ("n_hands", C.c_int32),
+                ("hand_cards", C.POINTER(C.c_int32)), ("strength", C.POINTER(C.c_int32)),
+                ("range", C.POINTER(C.c_double) * 2), ("pot", C.c_double), ("stack", C.c_double),
+                ("bb", C.c_double), ("n_bets", C.c_int32), ("bet_fracs", C.POINTER(C.c_double)),
+                ("allin", C.c_int32), ("raise_cap", C.c_int32)]
+
+
+class Dims(C.Structure):
+    _fields_ = [("H", C.c_int32), ("ld", C.c_int32), ("S", C.c_int32 * 2), ("J", C.c_int32 * 2),
+                ("L", C.c_int32 * 2), ("T", C.c_int32), ("n_fold", C.c_int32), ("Z", C.c_double),
+                ("normA", C.c_double), ("M", C.c_double * 2), ("Omega", C.c_double * 2)]
+
+
+class IterLog(C.Structure):
+    _fields_ = [("t", C.c_int32), ("player", C.c_int32), ("backoffs", C.c_int32),
+                ("tau", C.c_double), ("mu", C.c_double * 2), ("egv", C.c_double),
+                ("gap_mbb", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("alpha", C.c_double), ("mu0", C.c_double * 2),
+                ("eps_mbb", C.c_double), ("max_iters", C.c_int32), ("gap_every", C.c_int32),
+                ("replay_n", C.c_int32), ("replay_player", C.POINTER(C.c_int32)),
+                ("replay_tau", C.POINTER(C.c_double)), ("log_cap", C.c_int32),
+                ("log", C.POINTER(IterLog))]
+
+
+class SolveReport(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("products", C.c_int32), ("backoffs", C.c_int32),
+                ("gap_checks", C.c_int32), ("gap_mbb", C.c_double), ("mu", C.c_double * 2),
+                ("tau", C.c_double), ("seconds", C.c_double)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("player", C.c_int32), ("accepted", C.c_int32), ("backoffs", C.c_int32),
+                ("products", C.c_int32), ("tau", C.c_double), ("egv", C.c_double),
+                ("mu", C.c_double * 2)]
+
+
+_vp, _i32, _f64 = C.c_void_p, C.c_int32, C.c_double
+_SIGS = {
+    "egt_create_game": [C.POINTER(GameDesc), _i32, _vp, C.POINTER(_vp)],
+    "egt_destroy_game": [_vp],
+    "egt_dims_query": [_vp, C.POINTER(Dims)],
+    "egt_hand_order": [_vp, _vp],
+    "egt_treeplex_query": [_vp, _i32, _vp, _vp, _vp, _vp, _vp],
+    "egt_terminal_query": [_vp, _vp, _vp, _vp, _vp],
+    "egt_grad": [_vp, _i32, _vp, _vp, _vp],
+    "egt_grad_f64": [_vp, _i32, _vp, _vp, _vp],
+    "egt_smoothed_br": [_vp, _i32, _vp, _f64, _vp, C.POINTER(_f64), _vp],
+    "egt_best_response_f64": [_vp, _i32, _vp, C.POINTER(_f64), _vp],
+    "egt_gap": [_vp, _vp, _vp, C.POINTER(_f64), _vp],
+    "egt_solver_init": [_vp, C.POINTER(SolveOpts), _vp],
+    "egt_step": [_vp, _i32, C.POINTER(_f64), _i32, C.POINTER(StepInfo), _vp],
+    "egt_state_get": [_vp, _vp, _vp, _vp, _vp],
+    "egt_state_set": [_vp, _vp, _vp, _vp, _vp],
+    "egt_solve": [_vp, C.POINTER(SolveOpts), _vp, _vp, C.POINTER(SolveReport), _vp],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = C.c_int
+lib.egt_last_error.argtypes = []
+lib.egt_last_error.restype = C.c_char_p
+
+
+def declared_symbols(header=HEADER):
+    """Names of the functions include/egt.h declares."""
+    text = open(header).read()
+    return sorted(set(re.findall(r"\b(egt_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(status):
+    if status != 0:
+        raise EGTError(status, lib.egt_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import sys
+        torch = sys.modules.get("torch")
+        if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _i32p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _f64p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Game:
+    """One compiled river endgame on a device (owns its device memory)."""
+
+    def __init__(self, spec, device=0, stream=None):
+        self._keep = dict(
+            cards=np.ascontiguousarray(spec.hands, dtype=np.int32),
+            strength=np.ascontiguousarray(spec.strength, dtype=np.int32),
+            r0=np.ascontiguousarray(spec.ranges[0], dtype=np.float64),
+            r1=np.ascontiguousarray(spec.ranges[1], dtype=np.float64),
+            bets=np.ascontiguousarray(spec.bet_fracs, dtype=np.float64),
+        )
+        k = self._keep
+        d = GameDesc()
+        d.n_cards = spec.n_cards
+        d.hand_size = spec.hand_size
+        d.n_hands = spec.n_hands
+        d.hand_cards = _i32p(k["cards"])
+        d.strength = _i32p(k["strength"])
+        d.range[0] = _f64p(k["r0"])
+        d.range[1] = _f64p(k["r1"])
+        d.pot, d.stack, d.bb = spec.pot, spec.stack, spec.bb
+        d.n_bets = len(spec.bet_fracs)
+        d.bet_fracs = _f64p(k["bets"])
+        d.allin = int(spec.allin)
+        d.raise_cap = spec.raise_cap
+        self._h = _vp()
+        _check(lib.egt_create_game(C.byref(d), device, _stream(stream), C.byref(self._h)))
+        self.spec = spec
+        self.device = device
+        dims = Dims()
+        _check(lib.egt_dims_query(self._h, C.byref(dims)))
+        self.H, self.ld = dims.H, dims.ld
+        self.S = (dims.S[0], dims.S[1])
+        self.J = (dims.J[0], dims.J[1])
+        self.L = (dims.L[0], dims.L[1])
+        self.T, self.n_fold = dims.T, dims.n_fold
+        self.Z, self.normA = dims.Z, dims.normA
+        self.M = (dims.M[0], dims.M[1])
+        self.Omega = (dims.Omega[0], dims.Omega[1])
+        order = np.empty(self.H, dtype=np.int32)
+        _check(lib.egt_hand_order(self._h, order.ctypes.data))
+        self.order = order
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib.egt_destroy_game(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- layout helpers (host-side marshalling between input hand order and [seq][ld]) ----
+    def pack(self, arr):
+        """[S][H] in input hand order -> [S][ld] numpy in sorted order (padding 0)."""
+        arr = np.asarray(arr)
+        out = np.zeros((arr.shape[0], self.ld), dtype=arr.dtype)
+        out[:, :self.H] = arr[:, self.order]
+        return out
+
+    def unpack(self, arr):
+        """[S][ld] in sorted order -> [S][H] in input hand order."""
+        arr = np.asarray(arr)
+        out = np.empty((arr.shape[0], self.H), dtype=arr.dtype)
+        out[:, self.order] = arr[:, :self.H]
+        return out
+
+    def treeplex(self, player):
+        J = self.J[player]
+        par, first, n, lev = (np.empty(J, np.int32) for _ in range(4))
+        beta = np.empty(J, np.float64)
+        _check(lib.egt_treeplex_query(self._h, player, par.ctypes.data, first.ctypes.data,
+                                      n.ctypes.data, lev.ctypes.data, beta.ctypes.data))
+        return dict(parent=par, first=first, n=n, level=lev, beta=beta)
+
+    def terminals(self):
+        T = self.T
+        s1, s2, kind = (np.empty(T, np.int32) for _ in range(3))
+        coef = np.empty(T, np.float64)
+        _check(lib.egt_terminal_query(self._h, s1.ctypes.data, s2.ctypes.data, kind.ctypes.data,
+                                      coef.ctypes.data))
+        return dict(seq1=s1, seq2=s2, kind=kind, coef=coef)
+
+    # ---- hot path ----
+    def grad(self, player, inp, out, stream=None):
+        _check(lib.egt_grad(self._h, player, _ptr(inp), _ptr(out), _stream(stream)))
+
+    def grad_f64(self, player, inp, out, stream=None):
+        _check(lib.egt_grad_f64(self._h, player, _ptr(inp), _ptr(out), _stream(stream)))
+
+    def smoothed_br(self, player, g, mu, q_out=None, value=True, stream=None):
+        v = C.c_double(float("nan"))
+        _check(lib.egt_smoothed_br(self._h, player, _ptr(g), float(mu), _ptr(q_out),
+                                   C.byref(v) if value else None, _stream(stream)))
+        return v.value if value else None
+
+    def best_response_f64(self, player, g, stream=None):
+        v = C.c_double()
+        _check(lib.egt_best_response_f64(self._h, player, _ptr(g), C.byref(v), _stream(stream)))
+        return v.value
+
+    def gap(self, x, y, stream=None):
+        v = C.c_double()
+        _check(lib.egt_gap(self._h, _ptr(x), _ptr(y), C.byref(v), _stream(stream)))
+        return v.value
+
+    # ---- solver ----
+    @staticmethod
+    def _opts(variant=EGT_AS, alpha=0.01, mu0=None, eps_mbb=1.0, max_iters=1000, gap_every=1,
+              replay=None, log_cap=0):
+        o = SolveOpts()
+        o.variant, o.alpha = variant, alpha
+        o.mu0[0], o.mu0[1] = (mu0 if mu0 is not None else (0.0, 0.0))
+        o.eps_mbb, o.max_iters, o.gap_every = eps_mbb, max_iters, gap_every
+        keep = []
+        if replay is not None and len(replay):
+            pl = np.ascontiguousarray([p for p, _ in replay], dtype=np.int32)
+            ta = np.ascontiguousarray([t for _, t in replay], dtype=np.float64)
+            keep += [pl, ta]
+            o.replay_n = len(replay)
+            o.replay_player, o.replay_tau = _i32p(pl), _f64p(ta)
+        log = None
+        if log_cap:
+            log = (IterLog * log_cap)()
+            o.log_cap, o.log = log_cap, C.cast(log, C.POINTER(IterLog))
+        return o, keep, log
+
+    def solver_init(self, stream=None, **kw):
+        o, keep, _ = self._opts(**kw)
+        _check(lib.egt_solver_init(self._h, C.byref(o), _stream(stream)))
+
+    def step(self, player=-1, tau=0.5, mode=STEP_DECR, stream=None):
+        t = C.c_double(tau)
+        info = StepInfo()
+        _check(lib.egt_step(self._h, player, C.byref(t), mode, C.byref(info), _stream(stream)))
+        return dict(player=info.player, accepted=bool(info.accepted), backoffs=info.backoffs,
+                    products=info.products, tau=info.tau, egv=info.egv, mu=(info.mu[0], info.mu[1]))
+
+    def state_get(self, x=None, y=None, stream=None):
+        mu = (C.c_double * 2)()
+        _check(lib.egt_state_get(self._h, _ptr(x), _ptr(y), C.cast(mu, C.c_void_p), _stream(stream)))
+        return (mu[0], mu[1])
+
+    def state_set(self, x, y, mu, stream=None):
+        m = (C.c_double * 2)(*mu)
+        _check(lib.egt_state_set(self._h, _ptr(x), _ptr(y), C.cast(m, C.c_void_p), _stream(stream)))
+
+    def solve(self, x_out=None, y_out=None, stream=None, raise_on_not_converged=False, **kw):
+        o, keep, log = self._opts(**kw)
+        rep = SolveReport()
+        st = lib.egt_solve(self._h, C.byref(o), _ptr(x_out), _ptr(y_out), C.byref(rep), _stream(stream))
+        if st != 0 and not (st == 6 and not raise_on_not_converged):
+            _check(st)
+        out = dict(status=STATUS[st], iters=rep.iters, products=rep.products, backoffs=rep.backoffs,
+                   gap_checks=rep.gap_checks, gap_mbb=rep.gap_mbb, mu=(rep.mu[0], rep.mu[1]),
+                   tau=rep.tau, seconds=rep.seconds)
+        if log is not None:
+            n = min(rep.iters, o.log_cap)
+            out["log"] = [dict(t=log[i].t, player=log[i].player, backoffs=log[i].backoffs,
+                               tau=log[i].tau, mu=(log[i].mu[0], log[i].mu[1]), egv=log[i].egv,
+                               gap_mbb=log[i].gap_mbb) for i in range(n)]
+        return out
