@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""EGT/as iterations per second on the full-deck river endgame (one B300 per rank).
+
+Workload: 52-card river endgame, fixed board, 1081 hands per player, bets
+{0.5, 1} x pot + all-in, raise cap 3, stack 10, pot 1, Dirichlet(0.5) ranges
+(seeded synthetic stand-in for the paper's Libratus endgames).  One step is one
+EGT/as iteration through the C-ABI: a Decr (Step = 3 FP32 products + 3 smoothed
+best responses, the EGV check, and any tau back-offs) plus the FP64 stopping gap
+of Alg. 3 (2 FP64 products + 2 best responses).  The game's state is ~1 MB, so
+L2 is flushed (256 MB write) before every timed iteration and each iteration is
+timed alone with CUDA events on the library's stream.
+
+Under torchrun (--gpus N > 1) every rank solves its own game (seed + rank) as an
+independent replica: the method has no exchange step, so no collective is used
+on the data path; a gloo barrier brackets the timed region and rank 0 reports
+the max time over ranks.
+
+--impl reference times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EGT iter/s"
+UNIT = "iter/s"
+WORKLOAD = "full-deck river endgame: 52 cards, 1081 hands/player, bets {0.5,1}xpot + all-in, raise cap 3, stack 10, pot 1, EGT/as"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample (cpu_baseline)")
+    ap.add_argument("--ttg-max-iters", type=int, default=20000)
+    ap.add_argument("--no-ttg", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return float(p["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def algorithmic_bytes(g):
+    """Bytes each kernel kind must move at least once per launch (averaged over both players).
+
+    grad f32: opponent columns referenced by a terminal (read) + own columns (write) + both
+              ranges + per-hand card / tie tables + card lists;
+    grad f64: same with FP32 input columns and FP64 output columns;
+    sbr:      gradient read + strategy write + previous iterate read (mixed output);
+    br f64:   FP64 gradient read.
+    """
+    term = g.terminals()
+    H = g.H
+    tables = 10 * H + 2 * 2 * H
+    out = {}
+    gf32, gf64, sbr, br = [], [], [], []
+    for p in range(2):
+        opp_cols = len(set((term["seq2"] if p == 0 else term["seq1"]).tolist()))
+        gf32.append(4 * H * (opp_cols + g.S[p]) + 8 * H + tables)
+        gf64.append(4 * H * opp_cols + 8 * H * g.S[p] + 16 * H + tables)
+        sbr.append(3 * 4 * H * g.S[p])
+        br.append(8 * H * g.S[p])
+    out["grad_f32"] = sum(gf32) / 2
+    out["grad_f64"] = sum(gf64) / 2
+    out["sbr"] = sum(sbr) / 2
+    out["br_f64"] = sum(br) / 2
+    return out
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1810_03063_b300 import egt, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    spec = synth.full_deck(seed=synth.BASE_SEED + rank)
+    g = egt.Game(spec, device=local)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_step(tau):
+        info = g.step(-1, tau, mode=egt.STEP_DECR)
+        return info, g.state_gap()
+
+    g.solver_init(variant=egt.EGT_AS, alpha=0.01)
+    tau = 0.5
+    for _ in range(args.warmup):
+        info, _ = one_step(tau)
+        tau = info["tau"]
+
+    def timed_pass(k, tau):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        backoffs = 0
+        gap = None
+        for i in range(k):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            info, gap = one_step(tau)
+            evs[i][1].record(stream)
+            tau = info["tau"]
+            backoffs += info["backoffs"]
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, tau, backoffs, gap
+
+    g.profile(0)                          # restart launch counts
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, tau, backoffs, gap = timed_pass(args.steps, tau)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = g.profile_read()
+    gpu_launches = sum(v["launches"] for v in launches.values())
+    ms_max = allreduce_max(world, ms)
+    total_iters = allreduce_sum(world, float(args.steps))
+
+    # per-kernel device time over the same kind of steps (events around every launch)
+    g.profile(1)
+    timed_pass(args.steps, tau)
+    prof = g.profile_read()
+    g.profile(0)
+    ab = algorithmic_bytes(g)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    avg_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
+    achieved = ab[dom] / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    kernels = {k: dict(launches=v["launches"], ms=round(v["ms"], 4),
+                       avg_us=round(1e3 * v["ms"] / max(1, v["launches"]), 3),
+                       alg_bytes=int(ab[k]),
+                       gbs=round(ab[k] / (v["ms"] / max(1, v["launches"]) * 1e-3) / 1e9, 2) if v["ms"] else None)
+               for k, v in prof.items()}
+
+    # time to gap and end-to-end: create from host arrays, solve to 1 mbb, copy x, y to host
+    ttg = e2e = None
+    if not args.no_ttg:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g2 = egt.Game(spec, device=local)
+        x_d = torch.empty((g2.S[0], g2.ld), device=dev)
+        y_d = torch.empty((g2.S[1], g2.ld), device=dev)
+        rep = g2.solve(x_d, y_d, variant=egt.EGT_AS, alpha=0.01, eps_mbb=1.0,
+                       max_iters=args.ttg_max_iters, gap_every=1)
+        x_h = torch.empty(x_d.shape, dtype=x_d.dtype, pin_memory=True)
+        y_h = torch.empty(y_d.shape, dtype=y_d.dtype, pin_memory=True)
+        x_h.copy_(x_d, non_blocking=True)
+        y_h.copy_(y_d, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ttg = dict(reached=rep["status"] == "EGT_OK", iters=rep["iters"], gap_mbb=round(rep["gap_mbb"], 4),
+                   backoffs=rep["backoffs"], solve_seconds=round(rep["seconds"], 4),
+                   products=rep["products"])
+        per_iter_scalars = 32      # EGV value pair + gap value pair read back per iteration
+        e2e = dict(value=round(rep["iters"] / (t1 - t0), 2), unit=UNIT,
+                   h2d_bytes_per_step=int(g2.table_bytes),
+                   d2h_bytes_per_step=int(x_h.numel() * 4 + y_h.numel() * 4 + per_iter_scalars * rep["iters"]),
+                   step="one request: egt_create_game from host arrays + egt_solve to 1 mbb/hand "
+                        "+ x, y copied to pinned host memory",
+                   seconds=round(t1 - t0, 4))
+        g2.close()
+    return dict(ms=ms_max, total_iters=total_iters, backoffs=backoffs, gap=gap, clocks=clk.summary(),
+                gpu_launches=gpu_launches, kernels=kernels, dom=dom, achieved=achieved, peak=peak,
+                peak_kind=peak_kind, avg_ms=avg_ms, ttg=ttg, e2e=e2e, g=g)
+
+
+def oracle_iterations(seconds, max_iters=None, seed=None):
+    """The FP64 oracle's EGT/as on the same game: (iterations done, seconds, threads)."""
+    from oracle import egt as OE
+    from oracle import payoff
+    from paper_1810_03063_b300 import synth
+
+    spec = synth.full_deck(seed=synth.BASE_SEED if seed is None else seed)
+    og = payoff.make_game(spec)
+    P = OE.Problem(og)
+    mu = 0.01 * P.theory_mu()
+    x, y = OE.initial_point(P, mu, mu)
+    mux = muy = mu
+    while P.egv(x, y, mux, muy) < 0:
+        mux, muy = 2 * mux, 2 * muy
+        x, y = OE.initial_point(P, mux, muy)
+    tau = 0.5
+    t0 = time.perf_counter()
+    n = 0
+    step_times = []
+    while True:
+        s0 = time.perf_counter()
+        me = 0 if mux > muy else 1
+        mu_me, mu_o = (mux, muy) if me == 0 else (muy, mux)
+        vm, vo = (x, y) if me == 0 else (y, x)
+        while True:
+            new = OE.step(P, me, mu_me, mu_o, vm, vo, tau)
+            xx, yy = (new[1], new[2]) if me == 0 else (new[2], new[1])
+            mx, my = (new[0], mu_o) if me == 0 else (mu_o, new[0])
+            if P.egv(xx, yy, mx, my) >= 0:
+                break
+            tau *= 0.5
+        x, y, mux, muy = xx, yy, mx, my
+        P.eps_sad(x, y)
+        n += 1
+        step_times.append(time.perf_counter() - s0)
+        el = time.perf_counter() - t0
+        if (max_iters is not None and n >= max_iters) or (max_iters is None and el >= seconds):
+            break
+    return n, time.perf_counter() - t0, step_times
+
+
+def threads_used():
+    try:
+        from threadpoolctl import threadpool_info
+        return max(int(i.get("num_threads", 1)) for i in threadpool_info()) or os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    n_warm, _, _ = oracle_iterations(0, max_iters=max(1, args.warmup))
+    n, sec, steps = oracle_iterations(0, max_iters=max(1, args.steps))
+    value = n / sec
+    cores = threads_used()
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * sec / n, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "hands": 1081, "seq_per_player": 61, "terminals": 81,
+                       "impl": "FP64 CPU oracle (numpy), one EGT/as iteration + stopping gap per step"},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} EGT/as iterations (+ FP64 gap each) after {n_warm} warm-up"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    r = run_ours(args, world, rank, local)
+    if rank != 0:
+        return
+    # bounded oracle sample on the host cores (rank 0 at N=1 only)
+    cpu = None
+    if world == 1 and args.cpu_seconds > 0:
+        n, sec, _ = oracle_iterations(args.cpu_seconds)
+        cpu = {"value": round(n / sec, 4), "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+               "sample": f"first {n} EGT/as iterations (+ FP64 gap each) of the same game, {sec:.1f} s"}
+    value = r["total_iters"] / (r["ms"] * 1e-3)
+    g = r["g"]
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(r["ms"] / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "hands": g.H, "seq_per_player": g.S[0],
+                   "terminals": g.T, "variant": "EGT/as (Alg. 3 + 4)", "gap_every": 1,
+                   "precision": "products and smoothed BR in f32 (compensated sums); gap, EGV sums, mu in f64",
+                   "l2": "flushed (256 MB write) before every timed iteration",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": r["dom"], "achieved": round(r["achieved"], 2),
+                     "peak": r["peak"], "unit": "GB/s", "frac": round(r["achieved"] / r["peak"], 5),
+                     "peak_source": r["peak_kind"], "traffic": None,
+                     "alg_bytes_per_launch": int(algorithmic_bytes(g)[r["dom"]]),
+                     "avg_launch_us": round(r["avg_ms"] * 1e3, 3)},
+        "kernels": r["kernels"],
+        "cpu_baseline": cpu,
+        "e2e": r["e2e"],
+        "time_to_gap": r["ttg"],
+        "gpu_launches": r["gpu_launches"],
+        "clocks": r["clocks"],
+        "backoffs_in_timed_region": r["backoffs"],
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

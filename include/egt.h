@@ -108,6 +108,7 @@ typedef struct {
   int32_t S[2], J[2], L[2];
   int32_t T, n_fold;
   double Z, normA, M[2], Omega[2];
+  int64_t table_bytes;   /* bytes of compiled tables uploaded by egt_create_game */
 } egt_dims;
 
 /* Compile the game (betting tree, treeplex tables, hand/card tables) and
@@ -242,11 +243,38 @@ EGT_API egt_status egt_state_get(egt_game* game, float* x, float* y, double* mu,
 EGT_API egt_status egt_state_set(egt_game* game, const float* x, const float* y, const double* mu,
                          void* stream);
 
+/* eps_sad of the current iterates in mbb per hand (host out), as egt_gap computes
+ * it: the stopping test of Alg. 1 / 3. */
+EGT_API egt_status egt_state_gap(egt_game* game, double* gap_mbb, void* stream);
+
 /* Run Alg. 1 / practical EGT / Alg. 3 from egt_solver_init to the gap target.
  * x_out, y_out: device, may be NULL.  rep: host, may be NULL.
  * Returns NOT_CONVERGED if eps_mbb > 0 was not reached within max_iters. */
 EGT_API egt_status egt_solve(egt_game* game, const egt_solve_opts* opts, float* x_out, float* y_out,
                      egt_solve_report* rep, void* stream);
+
+/* ---- per-kernel device time accounting -------------------------------------- */
+
+/* Kernel kinds of the accounting: FP32 product, FP64 product, smoothed best
+ * response, FP64 best response. */
+typedef enum {
+  EGT_KERNEL_GRAD_F32 = 0,
+  EGT_KERNEL_GRAD_F64 = 1,
+  EGT_KERNEL_SBR = 2,
+  EGT_KERNEL_BR_F64 = 3,
+  EGT_KERNEL_KINDS = 4
+} egt_kernel_kind;
+
+/* enable != 0: clear the totals and bracket every later kernel launch of this
+ * game with CUDA events on its stream; enable == 0: stop timing.  Either call
+ * restarts the launch counts (kept whether timing is on or off).  The events
+ * add a little host work per launch. */
+EGT_API egt_status egt_profile(egt_game* game, int32_t enable);
+
+/* Device milliseconds per kernel kind timed since the last enable, and launches
+ * per kind since the last egt_profile call (host arrays of EGT_KERNEL_KINDS
+ * entries, either may be NULL).  Waits for the recorded launches to finish. */
+EGT_API egt_status egt_profile_read(egt_game* game, double* ms, int64_t* launches);
 
 /* Message of the last failed call on this thread ("" if none). */
 EGT_API const char* egt_last_error(void);

@@ -79,6 +79,18 @@ struct egt_game {
   bool initialised = false;
   bool host_only = false;        // compiled tables only (device = -1): queries work, kernels do not
   long long products = 0;
+  // per-kernel device time accounting (egt_profile): CUDA events around each launch
+  struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<ProfRec> prof_pending;
+  double prof_ms[EGT_KERNEL_KINDS] = {0};
+  long long prof_n[EGT_KERNEL_KINDS] = {0};
+  long long launches[EGT_KERNEL_KINDS] = {0};   // always counted, reset by egt_profile
+  size_t table_bytes = 0;
 };
 
 namespace {
@@ -359,6 +371,7 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
   }
   const size_t used = reinterpret_cast<uintptr_t>(hp) - base_h;
   if (overflow || used > bytes) return fail(EGT_ERR_INVALID_ARG, "internal: table arena overflow");
+  G->table_bytes = used;
   CUDA_TRY(cudaMemcpyAsync(G->arena, host.data(), used, cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   return EGT_OK;
@@ -412,6 +425,11 @@ void free_game(egt_game* G) {
   cudaFree(G->vals);
   cudaFree(G->status);
   if (G->pinned) cudaFreeHost(G->pinned);
+  for (auto& r : G->prof_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : G->ev_pool) cudaEventDestroy(e);
   delete G;
 }
 
@@ -428,12 +446,60 @@ egt_status check_ptr(const void* p, const char* name) {
   return EGT_OK;
 }
 
+// ---- per-kernel timing ----
+
+cudaEvent_t prof_event(egt_game* G) {
+  if (!G->ev_pool.empty()) {
+    cudaEvent_t e = G->ev_pool.back();
+    G->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Fold finished timing records into the totals (waits for each record's end event).
+egt_status prof_drain(egt_game* G) {
+  for (auto& r : G->prof_pending) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventSynchronize(r.b));
+    CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+    G->prof_ms[r.kind] += ms;
+    G->prof_n[r.kind] += 1;
+    G->ev_pool.push_back(r.a);
+    G->ev_pool.push_back(r.b);
+  }
+  G->prof_pending.clear();
+  return EGT_OK;
+}
+
+// Run one kernel launch, bracketed by events when accounting is on.
+template <typename F>
+egt_status timed(egt_game* G, int kind, cudaStream_t st, const char* what, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (G->prof_on) {
+    if (G->prof_pending.size() > 4096) EGT_TRY(prof_drain(G));
+    a = prof_event(G);
+    b = prof_event(G);
+    cudaEventRecord(a, st);
+  }
+  launch();
+  G->launches[kind]++;
+  egt_status s = check_launch(what);
+  if (G->prof_on) {
+    cudaEventRecord(b, st);
+    G->prof_pending.push_back({kind, a, b});
+  }
+  return s;
+}
+
 // ---- internal launches (no argument checks) ----
 
 egt_status grad32(egt_game* G, int player, const float* in, float* out, cudaStream_t st) {
-  launch_grad<float, float>(G->dg, player, in, out, st);
   G->products++;
-  return check_launch("grad kernel");
+  return timed(G, EGT_KERNEL_GRAD_F32, st, "grad kernel",
+               [&] { launch_grad<float, float>(G->dg, player, in, out, st); });
 }
 
 // SBR of player p with loss gradient sign * g (player 1 receives A^T x and negates).
@@ -450,8 +516,7 @@ egt_status sbr(egt_game* G, int p, const float* g, double mu, const float* old, 
   a.partials = G->partials;
   a.counter = G->counter;
   a.status = G->status;
-  launch_sbr(G->dg, p, a, st);
-  return check_launch("sbr kernel");
+  return timed(G, EGT_KERNEL_SBR, st, "sbr kernel", [&] { launch_sbr(G->dg, p, a, st); });
 }
 
 // Copy value slots [first, first + n) to the pinned host buffer and check them.
@@ -465,14 +530,16 @@ egt_status read_vals(egt_game* G, int first, int n, cudaStream_t st) {
 }
 
 egt_status gap_internal(egt_game* G, const float* x, const float* y, double* gap_mbb, cudaStream_t st) {
-  launch_grad<float, double>(G->dg, 0, y, G->g64[0], st);   // A y
-  EGT_TRY(check_launch("grad f64 kernel"));
-  launch_grad<float, double>(G->dg, 1, x, G->g64[1], st);   // A^T x
-  EGT_TRY(check_launch("grad f64 kernel"));
-  launch_br64(G->dg, 0, G->g64[0], 1.0, G->vals + 8, G->partials, G->counter, st);    // min_x <x, Ay>
-  EGT_TRY(check_launch("br kernel"));
-  launch_br64(G->dg, 1, G->g64[1], -1.0, G->vals + 9, G->partials, G->counter, st);   // max_y <y, A^T x>
-  EGT_TRY(check_launch("br kernel"));
+  EGT_TRY(timed(G, EGT_KERNEL_GRAD_F64, st, "grad f64 kernel",               // A y
+                [&] { launch_grad<float, double>(G->dg, 0, y, G->g64[0], st); }));
+  EGT_TRY(timed(G, EGT_KERNEL_GRAD_F64, st, "grad f64 kernel",               // A^T x
+                [&] { launch_grad<float, double>(G->dg, 1, x, G->g64[1], st); }));
+  EGT_TRY(timed(G, EGT_KERNEL_BR_F64, st, "br kernel", [&] {                // min_x <x, Ay>
+    launch_br64(G->dg, 0, G->g64[0], 1.0, G->vals + 8, G->partials, G->counter, st);
+  }));
+  EGT_TRY(timed(G, EGT_KERNEL_BR_F64, st, "br kernel", [&] {                // max_y <y, A^T x>
+    launch_br64(G->dg, 1, G->g64[1], -1.0, G->vals + 9, G->partials, G->counter, st);
+  }));
   CUDA_TRY(cudaMemcpyAsync(G->pinned + 8, G->vals + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   const double eps = G->pinned[9] - G->pinned[8];
@@ -655,10 +722,11 @@ egt_status egt_create_game(const egt_game_desc* desc, int32_t device, void* stre
   if (st == EGT_OK && !host_only) {
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    const size_t room = (size_t)std::max(0, dev_smem - 1024);   // static shared memory of the kernels
     for (int p = 0; p < 2 && st == EGT_OK; ++p)
-      if (sbr_smem_bytes(G->dg, p) > (size_t)dev_smem || br_smem_bytes(G->dg, p) > (size_t)dev_smem)
+      if (sbr_smem_bytes(G->dg, p) > room || br_smem_bytes(G->dg, p) > room)
         st = fail(EGT_ERR_INVALID_ARG, "betting tree too large for the shared-memory SBR tile");
-    if (st == EGT_OK && grad_smem_bytes(G->dg, true) > (size_t)std::min(dev_smem, 200 * 1024))
+    if (st == EGT_OK && grad_smem_bytes(G->dg, true) > room)
       st = fail(EGT_ERR_INVALID_ARG, "hand count too large for the shared-memory gradient tile");
   }
   if (st != EGT_OK) {
@@ -699,6 +767,7 @@ egt_status egt_dims_query(const egt_game* G, egt_dims* o) {
   for (auto& t : G->comp.term) o->n_fold += t.kind == 0;
   o->Z = G->Z;
   o->normA = G->normA;
+  o->table_bytes = (int64_t)G->table_bytes;
   return EGT_OK;
 }
 
@@ -754,8 +823,9 @@ egt_status egt_grad_f64(egt_game* G, int32_t player, const double* in, double* o
   EGT_TRY(check_ptr(out, "out"));
   if ((const void*)in == (const void*)out) return fail(EGT_ERR_INVALID_ARG, "in and out must differ");
   DeviceGuard guard(G->device);
-  launch_grad<double, double>(G->dg, player, in, out, S(stream));
-  return check_launch("grad f64 kernel");
+  cudaStream_t st = S(stream);
+  return timed(G, EGT_KERNEL_GRAD_F64, st, "grad f64 kernel",
+               [&] { launch_grad<double, double>(G->dg, player, in, out, st); });
 }
 
 egt_status egt_smoothed_br(egt_game* G, int32_t player, const float* g, double mu, float* q_out,
@@ -784,9 +854,10 @@ egt_status egt_best_response_f64(egt_game* G, int32_t player, const double* g, d
   EGT_TRY(check_ptr(g, "g"));
   if (!value_out) return fail(EGT_ERR_INVALID_ARG, "value_out is NULL");
   DeviceGuard guard(G->device);
-  launch_br64(G->dg, player, g, player == 0 ? 1.0 : -1.0, G->vals + 10, G->partials, G->counter,
-              S(stream));
-  EGT_TRY(check_launch("br kernel"));
+  cudaStream_t st = S(stream);
+  EGT_TRY(timed(G, EGT_KERNEL_BR_F64, st, "br kernel", [&] {
+    launch_br64(G->dg, player, g, player == 0 ? 1.0 : -1.0, G->vals + 10, G->partials, G->counter, st);
+  }));
   CUDA_TRY(cudaMemcpyAsync(G->pinned + 10, G->vals + 10, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
   CUDA_TRY(cudaStreamSynchronize(S(stream)));
   *value_out = G->pinned[10];
@@ -850,6 +921,15 @@ egt_status egt_state_set(egt_game* G, const float* x, const float* y, const doub
   EGT_TRY(grad32(G, 1, G->x[c], G->gy[c], st));
   G->initialised = true;
   return EGT_OK;
+}
+
+egt_status egt_state_gap(egt_game* G, double* gap_mbb, void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  if (!G->initialised) return fail(EGT_ERR_INVALID_ARG, "egt_solver_init has not been called");
+  if (!gap_mbb) return fail(EGT_ERR_INVALID_ARG, "gap_mbb is NULL");
+  DeviceGuard guard(G->device);
+  return gap_internal(G, G->x[G->cur], G->y[G->cur], gap_mbb, S(stream));
 }
 
 egt_status egt_solve(egt_game* G, const egt_solve_opts* o, float* x_out, float* y_out,
@@ -920,6 +1000,34 @@ egt_status egt_solve(egt_game* G, const egt_solve_opts* o, float* x_out, float* 
   }
   if (o->eps_mbb > 0 && !(gap <= o->eps_mbb))
     return fail(EGT_ERR_NOT_CONVERGED, "gap target not reached within max_iters");
+  return EGT_OK;
+}
+
+egt_status egt_profile(egt_game* G, int32_t enable) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  DeviceGuard guard(G->device);
+  EGT_TRY(prof_drain(G));
+  for (int k = 0; k < EGT_KERNEL_KINDS; ++k) {
+    if (enable) {
+      G->prof_ms[k] = 0;
+      G->prof_n[k] = 0;
+    }
+    G->launches[k] = 0;
+  }
+  G->prof_on = enable != 0;
+  return EGT_OK;
+}
+
+egt_status egt_profile_read(egt_game* G, double* ms, int64_t* launches) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  DeviceGuard guard(G->device);
+  EGT_TRY(prof_drain(G));
+  for (int k = 0; k < EGT_KERNEL_KINDS; ++k) {
+    if (ms) ms[k] = G->prof_ms[k];
+    if (launches) launches[k] = G->launches[k];
+  }
   return EGT_OK;
 }
 

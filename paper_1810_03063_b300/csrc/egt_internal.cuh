@@ -50,6 +50,10 @@ struct DevGame {
   DevTerms terms[2];       // terms[p]: grouped by player p's sequences (output of player p)
 };
 
+// Opt a kernel into the largest dynamic shared memory the device allows next to
+// its static shared memory; returns the limit (bytes) or -1 on failure.
+int opt_in_dynamic_smem(const void* kernel);
+
 // ---- kernels ----
 template <typename TIn, typename T>
 void launch_grad(const DevGame& g, int player, const TIn* in, T* out, cudaStream_t st);

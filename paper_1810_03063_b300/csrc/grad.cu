@@ -246,12 +246,8 @@ size_t grad_smem_bytes(const DevGame& g, bool f64) {
 template <typename TIn, typename T>
 void launch_grad(const DevGame& g, int player, const TIn* in, T* out, cudaStream_t st) {
   const size_t smem = smem_for<T>(g);
-  static bool attr_set = false;   // one process-wide opt-in per instantiation
-  if (!attr_set) {
-    cudaFuncSetAttribute(grad_kernel<TIn, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
-    attr_set = true;
-  }
+  static int limit = 0;   // one process-wide opt-in per instantiation
+  if (limit == 0) limit = opt_in_dynamic_smem((const void*)grad_kernel<TIn, T>);
   grad_kernel<TIn, T><<<g.tpx[player].S, kGradThreads, smem, st>>>(g, player, in, out);
 }
 

@@ -7,6 +7,8 @@
 // exp(-g_hat_i / (mu beta_j)) and value  g_hat_i* + t log q_bar_i* + t log n_j
 // (t = mu beta_j) taken at i* = argmax q_bar (= argmin g_hat), which is
 // m - t log(sum_i exp(-(g_hat_i - m) / t)) + t log n_j with m = min g_hat.
+// The kernel evaluates that value as m - t log1p(sum_i expm1(-(g_hat_i - m)/t) / n_j),
+// the same quantity without the cancellation of the two logarithms in FP32.
 // Top-down: q_i = q_{p_j} q_bar_i.
 //
 // Sec. 6: the per-hand treeplexes form a Cartesian product at the root, so
@@ -83,17 +85,22 @@ __global__ void __launch_bounds__(kSbrHands* kSbrWarps)
         U[s * kSbrHands + lane] = gh;
         m = fminf(m, gh);
       }
+      // e_i = exp(-(g_hat_i - m)/t) keeps tiny q_bar accurate; X = sum_i (e_i - 1) from
+      // expm1 keeps the value accurate when t >> spread of g_hat (there log(sum e) and
+      // log n nearly cancel): t log q_bar_i* + t log n = -t log1p(X / n)
       const float it = itj[j];
-      float sum = 0.f;
+      float sum = 0.f, X = 0.f;
       for (int i = 0; i < n; ++i) {
         float* u = U + (s0 + i) * kSbrHands + lane;
-        const float e = expf(-(*u - m) * it);
+        const float d = -(*u - m) * it;
+        const float e = expf(d);
+        X += expm1f(d);
         *u = e;
         sum += e;
       }
       const float inv = 1.f / sum;
       for (int i = 0; i < n; ++i) U[(s0 + i) * kSbrHands + lane] *= inv;
-      V[j * kSbrHands + lane] = m - tj[j] * logf(sum) + tj[j] * tp.log_n[j];
+      V[j * kSbrHands + lane] = m - tj[j] * log1pf(X / (float)n);
     }
     __syncthreads();
   }
@@ -183,23 +190,30 @@ size_t br_smem_bytes(const DevGame& g, int player) {
   return (size_t)g.tpx[player].J * kSbrHands * sizeof(double);
 }
 
+int opt_in_dynamic_smem(const void* kernel) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, kernel) != cudaSuccess)
+    return -1;
+  const int limit = optin - (int)fa.sharedSizeBytes;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess)
+    return -1;
+  return limit;
+}
+
 void launch_sbr(const DevGame& g, int player, const SbrArgs& a, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(sbr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr_set = true;
-  }
+  static int limit = 0;
+  if (limit == 0) limit = opt_in_dynamic_smem((const void*)sbr_kernel);
   const int grid = g.ld / kSbrHands;
   sbr_kernel<<<grid, kSbrHands * kSbrWarps, sbr_smem_bytes(g, player), st>>>(g, player, a);
 }
 
 void launch_br64(const DevGame& g, int player, const double* gv, double sign, double* value_dev,
                  double* partials, unsigned int* counter, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(br64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr_set = true;
-  }
+  static int limit = 0;
+  if (limit == 0) limit = opt_in_dynamic_smem((const void*)br64_kernel);
   const int grid = g.ld / kSbrHands;
   br64_kernel<<<grid, kSbrHands * kSbrWarps, br_smem_bytes(g, player), st>>>(
       g, player, gv, sign, value_dev, partials, counter);

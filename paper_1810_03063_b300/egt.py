@@ -47,7 +47,8 @@ class GameDesc(C.Structure):
 class Dims(C.Structure):
     _fields_ = [("H", C.c_int32), ("ld", C.c_int32), ("S", C.c_int32 * 2), ("J", C.c_int32 * 2),
                 ("L", C.c_int32 * 2), ("T", C.c_int32), ("n_fold", C.c_int32), ("Z", C.c_double),
-                ("normA", C.c_double), ("M", C.c_double * 2), ("Omega", C.c_double * 2)]
+                ("normA", C.c_double), ("M", C.c_double * 2), ("Omega", C.c_double * 2),
+                ("table_bytes", C.c_int64)]
 
 
 class IterLog(C.Structure):
@@ -94,7 +95,11 @@ _SIGS = {
     "egt_state_get": [_vp, _vp, _vp, _vp, _vp],
     "egt_state_set": [_vp, _vp, _vp, _vp, _vp],
     "egt_solve": [_vp, C.POINTER(SolveOpts), _vp, _vp, C.POINTER(SolveReport), _vp],
+    "egt_state_gap": [_vp, C.POINTER(_f64), _vp],
+    "egt_profile": [_vp, _i32],
+    "egt_profile_read": [_vp, _vp, _vp],
 }
+KERNEL_KINDS = ("grad_f32", "grad_f64", "sbr", "br_f64")
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
@@ -181,6 +186,7 @@ class Game:
         self.Z, self.normA = dims.Z, dims.normA
         self.M = (dims.M[0], dims.M[1])
         self.Omega = (dims.Omega[0], dims.Omega[1])
+        self.table_bytes = dims.table_bytes
         order = np.empty(self.H, dtype=np.int32)
         _check(lib.egt_hand_order(self._h, order.ctypes.data))
         self.order = order
@@ -290,6 +296,20 @@ class Game:
     def state_set(self, x, y, mu, stream=None):
         m = (C.c_double * 2)(*mu)
         _check(lib.egt_state_set(self._h, _ptr(x), _ptr(y), C.cast(m, C.c_void_p), _stream(stream)))
+
+    def profile(self, enable):
+        _check(lib.egt_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        ms = np.zeros(len(KERNEL_KINDS), np.float64)
+        n = np.zeros(len(KERNEL_KINDS), np.int64)
+        _check(lib.egt_profile_read(self._h, ms.ctypes.data, n.ctypes.data))
+        return {k: dict(ms=float(ms[i]), launches=int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+    def state_gap(self, stream=None):
+        v = C.c_double()
+        _check(lib.egt_state_gap(self._h, C.byref(v), _stream(stream)))
+        return v.value
 
     def solve(self, x_out=None, y_out=None, stream=None, raise_on_not_converged=False, **kw):
         o, keep, log = self._opts(**kw)
