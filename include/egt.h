@@ -174,6 +174,22 @@ EGT_API egt_status egt_best_response_f64(egt_game* game, int32_t player, const d
 EGT_API egt_status egt_gap(egt_game* game, const float* x, const float* y, double* gap_mbb,
                    void* stream);
 
+/* The same residual as egt_gap, for callers that must not allocate device
+ * memory on their path (a serving process whose device memory is reserved up
+ * front by another allocator, or a latency-critical loop that cannot take the
+ * device-wide synchronisation of cudaMalloc / cudaFree).  The paper has no
+ * counterpart: this is a deployment variant.  It allocates nothing: its FP64
+ * product vectors and reduction scratch live in one static device array of
+ * 2 MiB that every GPU loading the library holds until exit, so games needing
+ * more ((S[0] + S[1]) * ld * 8 bytes plus about 9 KB) are rejected with
+ * INVALID_ARG and a message giving both sizes.  The first call on a device
+ * looks up the array's address with that device current: make it before any
+ * stream capture.  All calls share the array (each clears what must start at
+ * zero); calls that overlap on the GPU race, so serialise them (one stream).
+ * The game is only read.  x, y device [S_p][ld]; gap_mbb host. */
+EGT_API egt_status egt_gap_noalloc(const egt_game* game, const float* x, const float* y,
+                                   double* gap_mbb, void* stream);
+
 /* ---- solver (Algorithms 1-4) ---------------------------------------------- */
 
 typedef enum {

@@ -678,6 +678,19 @@ egt_status solver_init(egt_game* G, const egt_solve_opts* o, cudaStream_t st) {
 
 }  // namespace
 
+namespace egt {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+bool game_view(const egt_game* G, GameView* out) {
+  if (!G || !out) return false;
+  out->dg = &G->dg;
+  out->device = G->device;
+  out->bb = G->bb;
+  out->host_only = G->host_only;
+  return true;
+}
+}  // namespace egt
+
 extern "C" {
 
 const char* egt_last_error(void) { return g_last_error.c_str(); }

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace egt {
 
 constexpr int kGradThreads = 256;   // threads of a gradient CTA
@@ -49,6 +51,18 @@ struct DevGame {
   DevTpx tpx[2];
   DevTerms terms[2];       // terms[p]: grouped by player p's sequences (output of player p)
 };
+
+// Read-only view of a game's device tables, for entry points outside api.cu.
+struct GameView {
+  const DevGame* dg;
+  int device;
+  double bb;
+  bool host_only;
+};
+bool game_view(const struct egt_game* G, GameView* out);
+
+// Set the thread-local message returned by egt_last_error().
+void set_last_error(const std::string& msg);
 
 // Opt a kernel into the largest dynamic shared memory the device allows next to
 // its static shared memory; returns the limit (bytes) or -1 on failure.

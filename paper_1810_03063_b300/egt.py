@@ -96,6 +96,7 @@ _SIGS = {
     "egt_state_set": [_vp, _vp, _vp, _vp, _vp],
     "egt_solve": [_vp, C.POINTER(SolveOpts), _vp, _vp, C.POINTER(SolveReport), _vp],
     "egt_state_gap": [_vp, C.POINTER(_f64), _vp],
+    "egt_gap_noalloc": [_vp, _vp, _vp, C.POINTER(_f64), _vp],
     "egt_profile": [_vp, _i32],
     "egt_profile_read": [_vp, _vp, _vp],
 }
@@ -254,6 +255,11 @@ class Game:
     def gap(self, x, y, stream=None):
         v = C.c_double()
         _check(lib.egt_gap(self._h, _ptr(x), _ptr(y), C.byref(v), _stream(stream)))
+        return v.value
+
+    def gap_noalloc(self, x, y, stream=None):
+        v = C.c_double()
+        _check(lib.egt_gap_noalloc(self._h, _ptr(x), _ptr(y), C.byref(v), _stream(stream)))
         return v.value
 
     # ---- solver ----
