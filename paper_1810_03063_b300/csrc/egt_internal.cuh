@@ -7,9 +7,7 @@
 
 namespace egt {
 
-constexpr int kGradThreads = 256;   // threads of a gradient CTA
-constexpr int kSbrHands = 32;       // hands per SBR CTA (one per lane)
-constexpr int kSbrWarps = 8;        // warps per SBR CTA (simplexes of a level split over them)
+constexpr int kSbrHands = 32;       // hands per SBR item (one per lane)
 constexpr int kMaxListLen = 64;     // max hands holding one card (two per lane in a warp scan)
 
 // One player's per-hand treeplex on the device (Sec. 4 notation).

@@ -1,0 +1,190 @@
+// Smoothed best response (Sec. 5) and FP64 best response bodies, shared by the
+// standalone kernels and the solver engine.
+//
+// Sec. 5: argmin_q <q, g> + mu sum_j beta_j q_{p_j} d_j(q^j / q_{p_j}) is solved
+// bottom-up: at simplex j every branch i gets g_hat_i = g_i + (values of the
+// child simplexes D_j^i); the simplex problem has q_bar_i proportional to
+// exp(-g_hat_i / (mu beta_j)) and value  g_hat_i* + t log q_bar_i* + t log n_j
+// (t = mu beta_j) taken at i* = argmax q_bar (= argmin g_hat), which is
+// m - t log(sum_i exp(-(g_hat_i - m) / t)) + t log n_j with m = min g_hat.
+// The value is evaluated as m - t log1p(sum_i expm1(-(g_hat_i - m)/t) / n_j),
+// the same quantity without the cancellation of the two logarithms in FP32.
+// Top-down: q_i = q_{p_j} q_bar_i.
+//
+// Sec. 6: the per-hand treeplexes form a Cartesian product at the root, so
+// hands are independent.  One item = 32 hands (one per lane, sequence rows
+// load as 128-byte lines); the whole [S][32] tile of g (and of the previous
+// iterate that the output is mixed with) is fetched into shared memory in one
+// coalesced pass before the recursion, which then runs on shared memory: the
+// warps split the simplexes of a level, levels are separated by __syncthreads.
+#pragma once
+#include <math.h>
+
+#include "grad_impl.cuh"
+
+namespace egt {
+
+struct SbrItemArgs {
+  const float* g;          // [S][ld] gradient of the player's own loss up to `sign`; NULL = 0
+  float sign;              // +1 player 0 (g = A y), -1 player 1 (g = A^T x)
+  double mu;
+  const float* old;        // if non-NULL the output is (1 - tau) old + tau q
+  float tau;
+  float* out;              // [S][ld] or NULL (value only)
+  double* value_partial;   // if non-NULL: this item's sum over live hands and root simplexes
+};
+
+inline size_t sbr_item_smem(const DevGame& g, int player) {
+  const DevTpx& tp = g.tpx[player];
+  return ((size_t)2 * tp.S * kSbrHands + (size_t)tp.J * kSbrHands + 2 * (size_t)tp.J) * sizeof(float);
+}
+
+inline size_t br_item_smem(const DevGame& g, int player) {
+  const DevTpx& tp = g.tpx[player];
+  return ((size_t)tp.S * kSbrHands + (size_t)tp.J * kSbrHands) * sizeof(double);
+}
+
+// Sum of n partial values in a fixed order (lane-strided, then a shuffle tree);
+// called by one full warp, result valid in lane 0.
+__device__ __forceinline__ double reduce_partials(const double* p, int n, int lane) {
+  double v = 0.0;
+  for (int i = lane; i < n; i += 32) v += __ldcg(p + i);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  return v;
+}
+
+// One item (32 hands starting at blk * 32) of player `player`'s smoothed best response.
+__device__ inline void sbr_item(const DevGame& g, int player, int blk, const SbrItemArgs& a,
+                                float* sm) {
+  const DevTpx tp = g.tpx[player];
+  const int S = tp.S, J = tp.J, ld = g.ld;
+  constexpr int kWarps = kItemThreads / 32;
+  float* G = sm;                                   // [S][32] sign*g -> g_hat -> q_bar -> q
+  float* O = G + (size_t)S * kSbrHands;            // [S][32] previous iterate
+  float* V = O + (size_t)S * kSbrHands;            // [J][32] simplex values
+  float* tj = V + (size_t)J * kSbrHands;           // [J] t_j = mu beta_j
+  float* itj = tj + J;                             // [J] 1 / t_j
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int h0 = blk * kSbrHands, h = h0 + lane;
+  const bool live = h < g.H;
+
+  for (int idx = tid; idx < S * kSbrHands; idx += kItemThreads) {
+    const int s = idx / kSbrHands, l = idx % kSbrHands;
+    const size_t gi = (size_t)s * ld + h0 + l;
+    G[idx] = (a.g != nullptr && h0 + l < g.H) ? a.sign * __ldcg(a.g + gi) : 0.f;
+    if (a.old != nullptr) O[idx] = __ldcg(a.old + gi);
+  }
+  for (int j = tid; j < J; j += kItemThreads) {
+    const double t = a.mu * tp.beta[j];
+    tj[j] = (float)t;
+    itj[j] = (float)(1.0 / t);
+  }
+  __syncthreads();
+
+  for (int l = tp.L - 1; l >= 0; --l) {
+    for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
+      const int s0 = tp.inf_first[j], n = tp.inf_n[j];
+      float m = INFINITY;
+      for (int i = 0; i < n; ++i) {
+        const int s = s0 + i;
+        float gh = G[s * kSbrHands + lane];
+        for (int c = tp.child_ptr[s]; c < tp.child_ptr[s + 1]; ++c)
+          gh += V[tp.child_idx[c] * kSbrHands + lane];
+        G[s * kSbrHands + lane] = gh;
+        m = fminf(m, gh);
+      }
+      // e_i = exp(-(g_hat_i - m)/t) keeps tiny q_bar accurate; X = sum_i (e_i - 1) via expm1
+      // keeps the value accurate: t log q_bar_i* + t log n = -t log1p(X / n)
+      const float it = itj[j];
+      float sum = 0.f, X = 0.f;
+      for (int i = 0; i < n; ++i) {
+        float* u = G + (s0 + i) * kSbrHands + lane;
+        const float d = -(*u - m) * it;
+        const float e = expf(d);
+        X += expm1f(d);
+        *u = e;
+        sum += e;
+      }
+      const float inv = 1.f / sum;
+      for (int i = 0; i < n; ++i) G[(s0 + i) * kSbrHands + lane] *= inv;
+      V[j * kSbrHands + lane] = m - tj[j] * log1pf(X / (float)n);
+    }
+    __syncthreads();
+  }
+
+  if (a.value_partial != nullptr && warp == 0) {
+    double v = 0.0;
+    if (live)
+      for (int j = tp.level_ptr[0]; j < tp.level_ptr[1]; ++j) v += (double)V[j * kSbrHands + lane];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if (lane == 0) *a.value_partial = v;
+  }
+
+  if (a.out != nullptr) {
+    const float tau = a.tau, omt = 1.f - a.tau;
+    for (int l = 0; l < tp.L; ++l) {
+      for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
+        const int p = tp.inf_parent[j];
+        const float qp = p < 0 ? 1.f : G[p * kSbrHands + lane];
+        const int s0 = tp.inf_first[j], n = tp.inf_n[j];
+        for (int i = 0; i < n; ++i) {
+          const int s = s0 + i;
+          const float q = qp * G[s * kSbrHands + lane];
+          G[s * kSbrHands + lane] = q;
+          float o = q;
+          if (a.old != nullptr) o = omt * O[s * kSbrHands + lane] + tau * q;
+          a.out[(size_t)s * ld + h] = live ? o : 0.f;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();   // shared memory is reused by the caller's next item
+}
+
+// One item of the FP64 best-response value: sign * min over the treeplex of
+// <q, sign * g> summed over the item's live hands, written to *value_partial.
+__device__ inline void br64_item(const DevGame& g, int player, int blk, const double* gv,
+                                 double sign, double* value_partial, double* sm) {
+  const DevTpx tp = g.tpx[player];
+  const int S = tp.S, ld = g.ld;
+  constexpr int kWarps = kItemThreads / 32;
+  double* G = sm;                                  // [S][32]
+  double* V = G + (size_t)S * kSbrHands;           // [J][32]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int h0 = blk * kSbrHands, h = h0 + lane;
+  const bool live = h < g.H;
+  for (int idx = tid; idx < S * kSbrHands; idx += kItemThreads) {
+    const int s = idx / kSbrHands, l = idx % kSbrHands;
+    G[idx] = h0 + l < g.H ? sign * __ldcg(gv + (size_t)s * ld + h0 + l) : 0.0;
+  }
+  __syncthreads();
+  for (int l = tp.L - 1; l >= 0; --l) {
+    for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
+      const int s0 = tp.inf_first[j], n = tp.inf_n[j];
+      double m = INFINITY;
+      for (int i = 0; i < n; ++i) {
+        const int s = s0 + i;
+        double gh = G[s * kSbrHands + lane];
+        for (int c = tp.child_ptr[s]; c < tp.child_ptr[s + 1]; ++c)
+          gh += V[tp.child_idx[c] * kSbrHands + lane];
+        m = fmin(m, gh);
+      }
+      V[j * kSbrHands + lane] = m;
+    }
+    __syncthreads();
+  }
+  if (warp == 0) {
+    double v = 0.0;
+    if (live)
+      for (int j = tp.level_ptr[0]; j < tp.level_ptr[1]; ++j) v += V[j * kSbrHands + lane];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if (lane == 0) *value_partial = sign * v;
+  }
+  __syncthreads();
+}
+
+}  // namespace egt
