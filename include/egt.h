@@ -210,7 +210,12 @@ typedef struct {
  *   FP64); <= 0 runs max_iters.
  * replay: if replay_n > 0, iteration t steps player replay_player[t] with
  *   tau = replay_tau[t] (no EGV check) for replay_n iterations (host arrays).
- * log: optional host array of log_cap entries filled per iteration. */
+ * log: optional host array of log_cap entries filled per iteration.
+ * engine: EGT_ENGINE_DEVICE (0) runs the iterations in one cooperative launch
+ *   (egt_iterate) when the device supports it and no replay is given;
+ *   EGT_ENGINE_HOST (1) drives every Step from the host (egt_step).  Both give
+ *   the same iterates bit for bit. */
+typedef enum { EGT_ENGINE_DEVICE = 0, EGT_ENGINE_HOST = 1 } egt_engine;
 typedef struct {
   int32_t variant;
   double alpha;
@@ -223,6 +228,7 @@ typedef struct {
   const double* replay_tau;
   int32_t log_cap;
   egt_iter_log* log;
+  int32_t engine;
 } egt_solve_opts;
 
 typedef struct {
@@ -263,6 +269,18 @@ EGT_API egt_status egt_state_set(egt_game* game, const float* x, const float* y,
  * it: the stopping test of Alg. 1 / 3. */
 EGT_API egt_status egt_state_gap(egt_game* game, double* gap_mbb, void* stream);
 
+/* Continue the solver for up to n_iters iterations of opts->variant on the
+ * device: one cooperative launch runs every Step (Alg. 2) with the EGT/as
+ * back-off of Alg. 4, the mu / tau bookkeeping and the FP64 residual every
+ * opts->gap_every iterations and after the last one, stopping early once it is
+ * <= opts->eps_mbb (if > 0).  No host round trip happens inside.  rep (host,
+ * may be NULL): iterations run, products, back-offs, residual checks, the last
+ * residual (NaN if none yet), mu, tau.  Each grid barrier of the launch waits
+ * at most ~2 s; if one runs out the call returns EGT_ERR_TIMEOUT and the
+ * solver must be re-initialised.  Replay schedules are not accepted. */
+EGT_API egt_status egt_iterate(egt_game* game, const egt_solve_opts* opts, int32_t n_iters,
+                               egt_solve_report* rep, void* stream);
+
 /* Run Alg. 1 / practical EGT / Alg. 3 from egt_solver_init to the gap target.
  * x_out, y_out: device, may be NULL.  rep: host, may be NULL.
  * Returns NOT_CONVERGED if eps_mbb > 0 was not reached within max_iters. */
@@ -272,13 +290,14 @@ EGT_API egt_status egt_solve(egt_game* game, const egt_solve_opts* opts, float* 
 /* ---- per-kernel device time accounting -------------------------------------- */
 
 /* Kernel kinds of the accounting: FP32 product, FP64 product, smoothed best
- * response, FP64 best response. */
+ * response, FP64 best response, device-resident driver (egt_iterate). */
 typedef enum {
   EGT_KERNEL_GRAD_F32 = 0,
   EGT_KERNEL_GRAD_F64 = 1,
   EGT_KERNEL_SBR = 2,
   EGT_KERNEL_BR_F64 = 3,
-  EGT_KERNEL_KINDS = 4
+  EGT_KERNEL_ENGINE = 4,
+  EGT_KERNEL_KINDS = 5
 } egt_kernel_kind;
 
 /* enable != 0: clear the totals and bracket every later kernel launch of this

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -10,6 +11,7 @@
 
 #include "../../include/egt.h"
 #include "egt_internal.cuh"
+#include "engine.cuh"
 #include "tree.hpp"
 
 using namespace egt;
@@ -76,7 +78,15 @@ struct egt_game {
   int* status = nullptr;         // device NaN flag
   double* pinned = nullptr;      // host readback of value slots
   double mu[2] = {0, 0};
+  int t = 0;                     // iterations since egt_solver_init
+  double tau = 0.5;              // EGT/as step size carried between iterations
+  double last_gap = NAN;         // last residual computed by the solver (mbb)
   bool initialised = false;
+  // device-resident driver (engine.cu)
+  EngineCtl* ctl_dev = nullptr;
+  EngineCtl* ctl_host = nullptr;
+  double* eng_partials = nullptr;
+  int eng_grid = -2;             // -2: not queried yet, <= 0: engine unavailable
   bool host_only = false;        // compiled tables only (device = -1): queries work, kernels do not
   long long products = 0;
   // per-kernel device time accounting (egt_profile): CUDA events around each launch
@@ -407,6 +417,9 @@ egt_status alloc_state(egt_game* G) {
   CUDA_TRY(cudaMalloc(&G->status, sizeof(int)));
   CUDA_TRY(cudaMemset(G->status, 0, sizeof(int)));
   CUDA_TRY(cudaHostAlloc(&G->pinned, 16 * sizeof(double), cudaHostAllocDefault));
+  CUDA_TRY(cudaMalloc(&G->ctl_dev, sizeof(EngineCtl)));
+  CUDA_TRY(cudaHostAlloc(&G->ctl_host, sizeof(EngineCtl), cudaHostAllocDefault));
+  CUDA_TRY(cudaMalloc(&G->eng_partials, 4 * (size_t)(G->ld / kSbrHands) * sizeof(double)));
   return EGT_OK;
 }
 
@@ -425,6 +438,9 @@ void free_game(egt_game* G) {
   cudaFree(G->vals);
   cudaFree(G->status);
   if (G->pinned) cudaFreeHost(G->pinned);
+  cudaFree(G->ctl_dev);
+  if (G->ctl_host) cudaFreeHost(G->ctl_host);
+  cudaFree(G->eng_partials);
   for (auto& r : G->prof_pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -628,6 +644,8 @@ egt_status do_step(egt_game* G, int player, double* tau_io, int mode, egt_step_i
   if (accepted) {
     G->mu[me] *= (1.0 - tau);
     G->cur = 1 - G->cur;
+    G->t += 1;
+    if (mode == EGT_STEP_DECR) G->tau = tau;
   }
   *tau_io = tau;
   if (info) {
@@ -672,7 +690,99 @@ egt_status solver_init(egt_game* G, const egt_solve_opts* o, cudaStream_t st) {
       EGT_TRY(init_point(G, st));
     }
   }
+  G->t = 0;
+  G->tau = 0.5;
+  G->last_gap = NAN;
   G->initialised = true;
+  return EGT_OK;
+}
+
+// Grid of the device-resident driver for this game (0: not available here).
+int engine_grid(egt_game* G) {
+  if (G->eng_grid == -2) {
+    const int maxg = engine_max_grid(G->dg);
+    const int NB = G->ld / kSbrHands;
+    const int S0 = G->comp.tpx[0].S, S1 = G->comp.tpx[1].S;
+    const int items = std::max(2 * NB, S0 + S1);
+    G->eng_grid = maxg <= 0 ? 0 : std::min(maxg, items);
+  }
+  return G->eng_grid;
+}
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+
+// Run up to n iterations of `variant` from the solver state on the device (one
+// cooperative launch), as the host loop of egt_solve would: Step (with the
+// EGT/as back-off), then the residual every gap_every iterations and at the end.
+egt_status engine_run(egt_game* G, int variant, double eps_mbb, int gap_every, int n,
+                      egt_iter_log* log_dev, int log_cap, egt_solve_report* rep, cudaStream_t st) {
+  const int grid = engine_grid(G);
+  if (grid <= 0) return fail(EGT_ERR_CUDA, "the device-resident driver cannot run on this device");
+  EngineCtl& c = *G->ctl_host;
+  std::memset(&c, 0, sizeof(c));
+  c.variant = variant;
+  c.n_iters = n;
+  c.gap_every = std::max(1, gap_every);
+  c.max_t = G->t + n;
+  c.eps_mbb = eps_mbb;
+  c.bb = G->bb;
+  c.mu[0] = G->mu[0];
+  c.mu[1] = G->mu[1];
+  c.tau = G->tau;
+  c.cur = G->cur;
+  c.t = G->t;
+  c.gap_mbb = G->last_gap;
+  c.egv = c.last_tau = c.last_egv = NAN;
+  EngineBufs b{};
+  for (int i = 0; i < 2; ++i) {
+    b.x[i] = G->x[i];
+    b.y[i] = G->y[i];
+    b.gx[i] = G->gx[i];
+    b.gy[i] = G->gy[i];
+    b.g64[i] = G->g64[i];
+  }
+  b.tx = G->tx;
+  b.ty = G->ty;
+  b.partials = G->eng_partials;
+  b.log = log_dev;
+  b.log_cap = log_cap;
+  // fault-injection hooks for tests: phantom arrivals make every grid barrier wait run
+  // out after the time limit instead of completing
+  const unsigned expected = (unsigned)(grid + std::max(0, env_int("EGT_TEST_BARRIER_EXTRA", 0)));
+  const unsigned long long limit_ns =
+      1000000ull * (unsigned long long)std::max(1, env_int("EGT_BARRIER_TIMEOUT_MS", 2000));
+  CUDA_TRY(cudaMemcpyAsync(G->ctl_dev, &c, sizeof(c), cudaMemcpyHostToDevice, st));
+  cudaError_t le = cudaSuccess;
+  EGT_TRY(timed(G, EGT_KERNEL_ENGINE, st, "engine kernel",
+                [&] { le = engine_launch(G->dg, b, G->ctl_dev, grid, expected, limit_ns, st); }));
+  if (le != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("engine launch: ") + cudaGetErrorString(le));
+  CUDA_TRY(cudaMemcpyAsync(&c, G->ctl_dev, sizeof(c), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  G->mu[0] = c.mu[0];
+  G->mu[1] = c.mu[1];
+  G->cur = c.cur;
+  G->t = c.t;
+  G->tau = c.tau;
+  G->last_gap = c.gap_mbb;
+  G->products += c.products;
+  if (rep) {
+    rep->iters = c.done_iters;
+    rep->products = c.products;
+    rep->backoffs = c.backoffs;
+    rep->gap_checks = c.gap_checks;
+    rep->gap_mbb = c.gap_mbb;
+    rep->mu[0] = c.mu[0];
+    rep->mu[1] = c.mu[1];
+    rep->tau = c.tau;
+  }
+  if (c.status == EGT_ERR_TIMEOUT)
+    return fail(EGT_ERR_TIMEOUT, "a grid barrier of the device-resident driver ran out of time; "
+                                 "the solver state is undefined until egt_solver_init");
+  if (c.status == EGT_ERR_TAU_UNDERFLOW) return fail(EGT_ERR_TAU_UNDERFLOW, "Decr halved tau below 2^-30");
+  if (c.status != 0) return fail((egt_status)c.status, "non-finite value in the device-resident driver");
   return EGT_OK;
 }
 
@@ -945,6 +1055,30 @@ egt_status egt_state_gap(egt_game* G, double* gap_mbb, void* stream) {
   return gap_internal(G, G->x[G->cur], G->y[G->cur], gap_mbb, S(stream));
 }
 
+egt_status egt_iterate(egt_game* G, const egt_solve_opts* o, int32_t n_iters, egt_solve_report* rep,
+                       void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  if (!G->initialised) return fail(EGT_ERR_INVALID_ARG, "egt_solver_init has not been called");
+  if (!o) return fail(EGT_ERR_INVALID_ARG, "opts is NULL");
+  if (o->variant < 0 || o->variant > 2) return fail(EGT_ERR_INVALID_ARG, "unknown variant");
+  if (o->replay_n > 0) return fail(EGT_ERR_INVALID_ARG, "replay schedules run on the host-driven loop (egt_solve)");
+  if (n_iters < 0) return fail(EGT_ERR_INVALID_ARG, "n_iters < 0");
+  DeviceGuard guard(G->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  egt_solve_report r{};
+  r.gap_mbb = G->last_gap;
+  r.mu[0] = G->mu[0];
+  r.mu[1] = G->mu[1];
+  r.tau = G->tau;
+  if (n_iters > 0) EGT_TRY(engine_run(G, o->variant, o->eps_mbb, o->gap_every, n_iters, nullptr, 0, &r, S(stream)));
+  if (rep) {
+    *rep = r;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return EGT_OK;
+}
+
 egt_status egt_solve(egt_game* G, const egt_solve_opts* o, float* x_out, float* y_out,
                      egt_solve_report* rep, void* stream) {
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
@@ -961,6 +1095,44 @@ egt_status egt_solve(egt_game* G, const egt_solve_opts* o, float* x_out, float* 
   G->products = 0;
   EGT_TRY(solver_init(G, o, st));
   const int gap_every = std::max(1, o->gap_every);
+  if (o->engine == EGT_ENGINE_DEVICE && o->replay_n <= 0 && engine_grid(G) > 0) {
+    // residual at t = 0 (the loop test of Alg. 1 / 3), then the iterations on the device
+    double gap = INFINITY;
+    EGT_TRY(gap_internal(G, G->x[G->cur], G->y[G->cur], &gap, st));
+    G->last_gap = gap;
+    egt_solve_report r{};
+    r.gap_mbb = gap;
+    r.mu[0] = G->mu[0];
+    r.mu[1] = G->mu[1];
+    r.tau = G->tau;
+    const bool done = (o->eps_mbb > 0 && gap <= o->eps_mbb) || o->max_iters == 0;
+    egt_iter_log* dlog = nullptr;
+    const int log_n = (o->log && o->log_cap > 0) ? std::min(o->log_cap, o->max_iters) : 0;
+    if (log_n > 0) CUDA_TRY(cudaMalloc(&dlog, (size_t)log_n * sizeof(egt_iter_log)));
+    egt_status es = EGT_OK;
+    if (!done) es = engine_run(G, o->variant, o->eps_mbb, gap_every, o->max_iters, dlog, log_n, &r, st);
+    if (dlog) {
+      if (es == EGT_OK) {
+        const int n = std::min(log_n, r.iters);
+        cudaMemcpyAsync(o->log, dlog, (size_t)n * sizeof(egt_iter_log), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+      }
+      cudaFree(dlog);
+    }
+    if (es != EGT_OK) return es;
+    if (x_out) CUDA_TRY(cudaMemcpyAsync(x_out, G->x[G->cur], vec_elems(G, 0) * 4, cudaMemcpyDeviceToDevice, st));
+    if (y_out) CUDA_TRY(cudaMemcpyAsync(y_out, G->y[G->cur], vec_elems(G, 1) * 4, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (rep) {
+      *rep = r;
+      rep->products = (int32_t)G->products;
+      rep->gap_checks = r.gap_checks + 1;
+      rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (o->eps_mbb > 0 && !(r.gap_mbb <= o->eps_mbb))
+      return fail(EGT_ERR_NOT_CONVERGED, "gap target not reached within max_iters");
+    return EGT_OK;
+  }
   int t = 0, backoffs = 0, gap_checks = 0;
   double tau = 0.5, gap = INFINITY;
   for (;;) {

@@ -1,0 +1,295 @@
+// Device-resident EGT driver: one cooperative launch runs whole iterations of
+// Alg. 1 (theory schedule), practical EGT or Alg. 3 / 4 (EGT/as) -- every phase
+// of Alg. 2's Step, the excessive-gap check with its tau back-off, the mu / tau
+// bookkeeping and the FP64 stopping residual -- with no host round trip.
+//
+// Phases are separated by a grid barrier; the work of a phase (32-hand SBR
+// items, one output sequence per gradient item) is spread over the CTAs.
+// Decisions (EGV sign, gap target) are taken by one warp of CTA 0 from per-item
+// FP64 partials summed in the same fixed order as the standalone kernels, so a
+// run here reproduces the host-driven loop of api.cu bit for bit.
+//
+// The grid barrier spins on a generation word with a time limit: if it runs out
+// (a CTA that never arrives), the kernel records EGT_ERR_TIMEOUT and every CTA
+// returns; the host reads the status and the context stays usable.
+#include <algorithm>
+
+#include "../../include/egt.h"
+#include "egt_internal.cuh"
+#include "engine.cuh"
+#include "grad_impl.cuh"
+#include "sbr_impl.cuh"
+
+namespace egt {
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T vload(const T* p) {
+  return *reinterpret_cast<const volatile T*>(p);
+}
+
+struct GridBar {
+  unsigned int* count;
+  unsigned int* gen;
+  int* status;
+  unsigned int expected;        // arrivals that complete the barrier (gridDim.x unless a test adds phantoms)
+  unsigned long long limit_ns;
+};
+
+// All CTAs meet here; returns false (in every thread) if the barrier timed out
+// anywhere or an error status was recorded.
+__device__ bool grid_sync(const GridBar& b) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int g0 = vload(b.gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(b.count, 1u) + 1u;
+    if (arrived == b.expected) {
+      atomicExch(b.count, 0u);
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (vload(b.gen) == g0) {
+        if (global_ns() - t0 > b.limit_ns) {
+          atomicCAS(b.status, 0, (int)EGT_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (vload(b.status) != 0) ok = 0;
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// One SBR phase: all 32-hand items of `player`, spread over the CTAs.
+__device__ __forceinline__ void run_sbr(const DevGame& g, int player, const float* gv, double mu,
+                                        const float* old, double tau, float* out, double* partials,
+                                        unsigned char* sm) {
+  const int NB = g.ld / kSbrHands;
+  for (int item = blockIdx.x; item < NB; item += gridDim.x) {
+    SbrItemArgs a;
+    a.g = gv;
+    a.sign = player == 0 ? 1.f : -1.f;
+    a.mu = mu;
+    a.old = old;
+    a.tau = (float)tau;
+    a.out = out;
+    a.value_partial = partials ? partials + item : nullptr;
+    sbr_item(g, player, item, a, reinterpret_cast<float*>(sm));
+  }
+}
+
+// One product phase: every output sequence of `player`.
+__device__ __forceinline__ void run_grad(const DevGame& g, int player, const float* in, float* out,
+                                         unsigned char* sm) {
+  for (int item = blockIdx.x; item < g.tpx[player].S; item += gridDim.x)
+    grad_item<float, float>(g, player, item, in, out, sm);
+}
+
+__global__ void __launch_bounds__(kItemThreads, 1)
+    engine_kernel(DevGame g, EngineBufs b, EngineCtl* ctl, unsigned int expected,
+                  unsigned long long limit_ns) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const GridBar bar{&ctl->bar_count, &ctl->bar_gen, &ctl->status, expected, limit_ns};
+  const int NB = g.ld / kSbrHands;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool leader = blockIdx.x == 0 && warp == 0;
+  double* partA = b.partials;
+  double* partB = b.partials + NB;
+  double* partBR0 = b.partials + 2 * NB;
+  double* partBR1 = b.partials + 3 * NB;
+  const int variant = ctl->variant, n_iters = ctl->n_iters, gap_every = ctl->gap_every;
+  const int max_t = ctl->max_t;
+  const double eps_mbb = ctl->eps_mbb;
+
+  for (int it = 0; it < n_iters; ++it) {
+    const int t = vload(&ctl->t);
+    const int cur = vload(&ctl->cur), nxt = 1 - cur;
+    const double mu0 = vload(&ctl->mu[0]), mu1 = vload(&ctl->mu[1]);
+    int me;
+    double tau;
+    if (variant == EGT_THEORY) {
+      me = t % 2 == 0 ? 0 : 1;
+      tau = 2.0 / (t + 3);
+    } else {
+      me = mu0 > mu1 ? 0 : 1;
+      tau = variant == EGT_PRACTICAL ? 2.0 / (t + 3) : vload(&ctl->tau);
+    }
+    const bool check = variant == EGT_AS;
+    int backoffs = 0;
+    double egv = 0.0 / 0.0;
+    // Alg. 2 Step focused on `me` (the y-focused step swaps roles, A -> -A^T)
+    const int ot = 1 - me;
+    const bool xs = me == 0;
+    float* v_me = xs ? b.x[cur] : b.y[cur];          // my iterate
+    float* v_ot = xs ? b.y[cur] : b.x[cur];          // the other's iterate
+    float* v_me_n = xs ? b.x[nxt] : b.y[nxt];
+    float* v_ot_n = xs ? b.y[nxt] : b.x[nxt];
+    float* g_me = xs ? b.gx[cur] : b.gy[cur];        // my loss gradient at v_ot
+    float* g_me_n = xs ? b.gx[nxt] : b.gy[nxt];
+    float* g_ot_n = xs ? b.gy[nxt] : b.gx[nxt];
+    float* t_me = xs ? b.tx : b.ty;
+    float* t_ot = xs ? b.ty : b.tx;
+    const double mu_me = xs ? mu0 : mu1, mu_ot = xs ? mu1 : mu0;
+    for (;;) {
+      // v_hat = (1 - tau) v + tau v_mu(other)
+      run_sbr(g, me, g_me, mu_me, v_me, tau, t_me, nullptr, sm);
+      if (!grid_sync(bar)) return;
+      run_grad(g, ot, t_me, t_ot, sm);                  // the other's loss gradient at v_hat
+      if (!grid_sync(bar)) return;
+      // other_+ = (1 - tau) other + tau other_mu(v_hat)
+      run_sbr(g, ot, t_ot, mu_ot, v_ot, tau, v_ot_n, nullptr, sm);
+      if (!grid_sync(bar)) return;
+      run_grad(g, me, v_ot_n, g_me_n, sm);              // my loss gradient at other_+
+      if (!grid_sync(bar)) return;
+      // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part
+      run_sbr(g, me, g_me_n, (1 - tau) * mu_me, v_me, tau, v_me_n, partA, sm);
+      if (!grid_sync(bar)) return;
+      run_grad(g, ot, v_me_n, g_ot_n, sm);              // the other's loss gradient at v_+
+      if (!grid_sync(bar)) return;
+      if (!check) break;
+      run_sbr(g, ot, g_ot_n, mu_ot, nullptr, 0.0, nullptr, partB, sm);   // the other's EGV part
+      if (!grid_sync(bar)) return;
+      if (leader) {
+        const double a = reduce_partials(partA, NB, lane);
+        const double c = reduce_partials(partB, NB, lane);
+        if (lane == 0) {
+          const double phi = xs ? a : c, negf = xs ? c : a;
+          const double v = phi + negf;
+          int retry = 0;
+          if (!isfinite(v)) {
+            atomicCAS(&ctl->status, 0, (int)EGT_ERR_NUMERIC);
+          } else if (v < 0) {
+            const double nt = tau * 0.5;
+            if (nt < 1.0 / (1u << 30)) atomicCAS(&ctl->status, 0, (int)EGT_ERR_TAU_UNDERFLOW);
+            else retry = 1;
+            ctl->tau = nt;
+          }
+          ctl->egv = v;
+          ctl->retry = retry;
+          __threadfence();
+        }
+      }
+      if (!grid_sync(bar)) return;
+      egv = vload(&ctl->egv);
+      if (!vload(&ctl->retry)) break;
+      tau = vload(&ctl->tau);
+      ++backoffs;
+    }
+    // accept (Alg. 2 last lines): mu_me^+ = (1 - tau) mu_me, swap the iterate buffers
+    const int t1 = t + 1;
+    const bool gap_due = t1 % gap_every == 0 || t1 >= max_t;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (xs) ctl->mu[0] = mu0 * (1.0 - tau);
+      else ctl->mu[1] = mu1 * (1.0 - tau);
+      ctl->cur = nxt;
+      ctl->t = t1;
+      if (variant == EGT_AS) ctl->tau = tau;
+      ctl->backoffs += backoffs;
+      ctl->products += 3 * (backoffs + 1);
+      ctl->done_iters += 1;
+      ctl->last_player = me;
+      ctl->last_backoffs = backoffs;
+      ctl->last_tau = tau;
+      ctl->last_egv = egv;
+      if (b.log != nullptr && it < b.log_cap) {
+        egt_iter_log& L = b.log[it];
+        L.t = t;
+        L.player = me;
+        L.backoffs = backoffs;
+        L.tau = tau;
+        L.mu[0] = xs ? mu0 * (1.0 - tau) : mu0;
+        L.mu[1] = xs ? mu1 : mu1 * (1.0 - tau);
+        L.egv = check ? egv : 0.0 / 0.0;
+        L.gap_mbb = vload(&ctl->gap_mbb);
+      }
+      __threadfence();
+    }
+    if (gap_due) {
+      // eps_sad of the new iterates: FP64 products of both players, then both best responses
+      const float* xn = b.x[nxt];
+      const float* yn = b.y[nxt];
+      const int S0 = g.tpx[0].S, S1 = g.tpx[1].S;
+      for (int item = blockIdx.x; item < S0 + S1; item += gridDim.x) {
+        if (item < S0) grad_item<float, double>(g, 0, item, yn, b.g64[0], sm);
+        else grad_item<float, double>(g, 1, item - S0, xn, b.g64[1], sm);
+      }
+      if (!grid_sync(bar)) return;
+      for (int item = blockIdx.x; item < 2 * NB; item += gridDim.x) {
+        if (item < NB)
+          br64_item(g, 0, item, b.g64[0], 1.0, partBR0 + item, reinterpret_cast<double*>(sm));
+        else
+          br64_item(g, 1, item - NB, b.g64[1], -1.0, partBR1 + item - NB, reinterpret_cast<double*>(sm));
+      }
+      if (!grid_sync(bar)) return;
+      if (leader) {
+        const double vmin = reduce_partials(partBR0, NB, lane);
+        const double vmax = reduce_partials(partBR1, NB, lane);
+        if (lane == 0) {
+          const double gap = (vmax - vmin) / ctl->bb * 1000.0;
+          if (!isfinite(gap)) atomicCAS(&ctl->status, 0, (int)EGT_ERR_NUMERIC);
+          ctl->gap_mbb = gap;
+          ctl->gap_checks += 1;
+          ctl->reached = eps_mbb > 0 && gap <= eps_mbb ? 1 : 0;
+          __threadfence();
+        }
+      }
+    }
+    if (!grid_sync(bar)) return;
+    if (vload(&ctl->reached) || vload(&ctl->t) >= max_t) return;
+  }
+}
+
+}  // namespace
+
+size_t engine_smem_bytes(const DevGame& g) {
+  size_t m = std::max(grad_item_smem(g, true), grad_item_smem(g, false));
+  for (int p = 0; p < 2; ++p) {
+    m = std::max(m, sbr_item_smem(g, p));
+    m = std::max(m, br_item_smem(g, p));
+  }
+  return m;
+}
+
+cudaError_t engine_launch(const DevGame& g, const EngineBufs& b, EngineCtl* ctl, int grid,
+                          unsigned int expected, unsigned long long limit_ns, cudaStream_t st) {
+  const size_t smem = engine_smem_bytes(g);
+  DevGame gg = g;
+  EngineBufs bb = b;
+  void* args[] = {&gg, &bb, &ctl, &expected, &limit_ns};
+  return cudaLaunchCooperativeKernel((const void*)engine_kernel, dim3(grid), dim3(kItemThreads), args,
+                                     smem, st);
+}
+
+int engine_max_grid(const DevGame& g) {
+  static int limit = 0;
+  if (limit == 0) limit = opt_in_dynamic_smem((const void*)engine_kernel);
+  if (limit < 0) return -1;
+  const size_t smem = engine_smem_bytes(g);
+  if (smem > (size_t)limit) return 0;
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel, kItemThreads, smem) !=
+          cudaSuccess)
+    return -1;
+  if (!coop) return 0;
+  return sms * per_sm;
+}
+
+}  // namespace egt

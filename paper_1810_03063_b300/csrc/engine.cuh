@@ -1,0 +1,54 @@
+// Device-resident EGT driver (engine.cu): control block, buffers, launch helpers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/egt.h"
+#include "egt_internal.cuh"
+
+namespace egt {
+
+// Control block in device memory, one per game.  The host writes the
+// configuration and the solver state before a launch and reads everything back
+// after it.
+struct EngineCtl {
+  // configuration
+  int variant, n_iters, gap_every, max_t;
+  double eps_mbb, bb;
+  // solver state (persists between launches)
+  double mu[2];
+  double tau;
+  int cur, t;
+  // results of the launch
+  int status, reached, retry, done_iters, backoffs, products, gap_checks;
+  int last_player, last_backoffs;
+  double gap_mbb, egv, last_tau, last_egv;
+  // grid barrier
+  unsigned int bar_count, bar_gen;
+};
+
+struct EngineBufs {
+  float* x[2];
+  float* y[2];
+  float* gx[2];     // A y of the matching y buffer
+  float* gy[2];     // A^T x of the matching x buffer
+  float* tx;
+  float* ty;
+  double* g64[2];   // FP64 products of the residual
+  double* partials; // 4 x (ld / 32) per-item values
+  egt_iter_log* log;
+  int log_cap;
+};
+
+size_t engine_smem_bytes(const DevGame& g);
+
+// Largest co-resident grid for the engine on the current device (0: cannot run,
+// -1: CUDA error).
+int engine_max_grid(const DevGame& g);
+
+// Cooperative launch of `grid` CTAs; `expected` is the number of barrier
+// arrivals that completes a grid barrier (grid, or more in a timeout test) and
+// limit_ns the barrier's time limit.
+cudaError_t engine_launch(const DevGame& g, const EngineBufs& b, EngineCtl* ctl, int grid,
+                          unsigned int expected, unsigned long long limit_ns, cudaStream_t st);
+
+}  // namespace egt

@@ -62,7 +62,7 @@ class SolveOpts(C.Structure):
                 ("eps_mbb", C.c_double), ("max_iters", C.c_int32), ("gap_every", C.c_int32),
                 ("replay_n", C.c_int32), ("replay_player", C.POINTER(C.c_int32)),
                 ("replay_tau", C.POINTER(C.c_double)), ("log_cap", C.c_int32),
-                ("log", C.POINTER(IterLog))]
+                ("log", C.POINTER(IterLog)), ("engine", C.c_int32)]
 
 
 class SolveReport(C.Structure):
@@ -97,10 +97,12 @@ _SIGS = {
     "egt_solve": [_vp, C.POINTER(SolveOpts), _vp, _vp, C.POINTER(SolveReport), _vp],
     "egt_state_gap": [_vp, C.POINTER(_f64), _vp],
     "egt_gap_noalloc": [_vp, _vp, _vp, C.POINTER(_f64), _vp],
+    "egt_iterate": [_vp, C.POINTER(SolveOpts), _i32, C.POINTER(SolveReport), _vp],
     "egt_profile": [_vp, _i32],
     "egt_profile_read": [_vp, _vp, _vp],
 }
-KERNEL_KINDS = ("grad_f32", "grad_f64", "sbr", "br_f64")
+KERNEL_KINDS = ("grad_f32", "grad_f64", "sbr", "br_f64", "engine")
+ENGINE_DEVICE, ENGINE_HOST = 0, 1
 for _name, _args in _SIGS.items():
     _fn = getattr(lib, _name)
     _fn.argtypes = _args
@@ -265,11 +267,12 @@ class Game:
     # ---- solver ----
     @staticmethod
     def _opts(variant=EGT_AS, alpha=0.01, mu0=None, eps_mbb=1.0, max_iters=1000, gap_every=1,
-              replay=None, log_cap=0):
+              replay=None, log_cap=0, engine=ENGINE_DEVICE):
         o = SolveOpts()
         o.variant, o.alpha = variant, alpha
         o.mu0[0], o.mu0[1] = (mu0 if mu0 is not None else (0.0, 0.0))
         o.eps_mbb, o.max_iters, o.gap_every = eps_mbb, max_iters, gap_every
+        o.engine = engine
         keep = []
         if replay is not None and len(replay):
             pl = np.ascontiguousarray([p for p, _ in replay], dtype=np.int32)
@@ -311,6 +314,14 @@ class Game:
         n = np.zeros(len(KERNEL_KINDS), np.int64)
         _check(lib.egt_profile_read(self._h, ms.ctypes.data, n.ctypes.data))
         return {k: dict(ms=float(ms[i]), launches=int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+    def iterate(self, n_iters, variant=EGT_AS, eps_mbb=0.0, gap_every=1, stream=None):
+        o, keep, _ = self._opts(variant=variant, eps_mbb=eps_mbb, gap_every=gap_every)
+        rep = SolveReport()
+        _check(lib.egt_iterate(self._h, C.byref(o), int(n_iters), C.byref(rep), _stream(stream)))
+        return dict(iters=rep.iters, products=rep.products, backoffs=rep.backoffs,
+                    gap_checks=rep.gap_checks, gap_mbb=rep.gap_mbb, mu=(rep.mu[0], rep.mu[1]),
+                    tau=rep.tau, seconds=rep.seconds)
 
     def state_gap(self, stream=None):
         v = C.c_double()
