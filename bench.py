@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample (cpu_baseline)")
     ap.add_argument("--ttg-max-iters", type=int, default=20000)
     ap.add_argument("--no-ttg", action="store_true")
+    ap.add_argument("--engine", default="device", choices=["device", "host"],
+                    help="device: each step is one egt_iterate launch; host: egt_step + egt_state_gap")
     return ap.parse_args()
 
 
@@ -171,6 +173,10 @@ def algorithmic_bytes(g):
     out["grad_f64"] = sum(gf64) / 2
     out["sbr"] = sum(sbr) / 2
     out["br_f64"] = sum(br) / 2
+    # one EGT/as iteration without back-off: 3 products, 3 mixing SBRs, 1 value-only SBR
+    # (gradient read), the residual's 2 FP64 products and 2 FP64 best responses
+    out["engine"] = (3 * out["grad_f32"] + 3 * out["sbr"] + out["sbr"] / 3 + 2 * out["grad_f64"]
+                     + 2 * out["br_f64"])
     return out
 
 
@@ -187,6 +193,9 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def one_step(tau):
+        if args.engine == "device":
+            r = g.iterate(1, variant=egt.EGT_AS, gap_every=1)
+            return dict(tau=r["tau"], backoffs=r["backoffs"]), r["gap_mbb"]
         info = g.step(-1, tau, mode=egt.STEP_DECR)
         return info, g.state_gap()
 
@@ -212,10 +221,10 @@ def run_ours(args, world, rank, local):
         return ms, tau, backoffs, gap
 
     g.profile(0)                          # restart launch counts
+    clk = ClockSampler(local).__enter__()  # sampled over every GPU-busy phase below
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        ms, tau, backoffs, gap = timed_pass(args.steps, tau)
+    ms, tau, backoffs, gap = timed_pass(args.steps, tau)
     torch.cuda.synchronize()
     barrier(world)
     launches = g.profile_read()
@@ -258,14 +267,15 @@ def run_ours(args, world, rank, local):
         ttg = dict(reached=rep["status"] == "EGT_OK", iters=rep["iters"], gap_mbb=round(rep["gap_mbb"], 4),
                    backoffs=rep["backoffs"], solve_seconds=round(rep["seconds"], 4),
                    products=rep["products"])
-        per_iter_scalars = 32      # EGV value pair + gap value pair read back per iteration
+        readback = 256             # the solver's control block, read once per solve
         e2e = dict(value=round(rep["iters"] / (t1 - t0), 2), unit=UNIT,
                    h2d_bytes_per_step=int(g2.table_bytes),
-                   d2h_bytes_per_step=int(x_h.numel() * 4 + y_h.numel() * 4 + per_iter_scalars * rep["iters"]),
+                   d2h_bytes_per_step=int(x_h.numel() * 4 + y_h.numel() * 4 + readback),
                    step="one request: egt_create_game from host arrays + egt_solve to 1 mbb/hand "
                         "+ x, y copied to pinned host memory",
                    seconds=round(t1 - t0, 4))
         g2.close()
+    clk.__exit__(None, None, None)
     return dict(ms=ms_max, total_iters=total_iters, backoffs=backoffs, gap=gap, clocks=clk.summary(),
                 gpu_launches=gpu_launches, kernels=kernels, dom=dom, achieved=achieved, peak=peak,
                 peak_kind=peak_kind, avg_ms=avg_ms, ttg=ttg, e2e=e2e, g=g)
@@ -365,6 +375,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "hands": g.H, "seq_per_player": g.S[0],
                    "terminals": g.T, "variant": "EGT/as (Alg. 3 + 4)", "gap_every": 1,
+                   "engine": args.engine,
                    "precision": "products and smoothed BR in f32 (compensated sums); gap, EGV sums, mu in f64",
                    "l2": "flushed (256 MB write) before every timed iteration",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

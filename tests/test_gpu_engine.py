@@ -1,0 +1,118 @@
+"""The device-resident driver (egt_iterate, egt_solve with the device engine).
+
+It runs the same kernel bodies and the same fixed-order FP64 reductions as the
+host-driven loop, so its iterates, mu, tau, decisions and residuals must equal
+the host loop's bit for bit; and that loop is the one held to the oracle in
+test_gpu_parity.py.  Its grid barriers are bounded: a barrier that cannot
+complete (phantom arrivals requested through the test hook) must end the
+launch with EGT_ERR_TIMEOUT, leaving the context usable.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1810_03063_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def egtlib():
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device")
+    from paper_1810_03063_b300 import egt
+    return egt
+
+
+GAMES = {}
+
+
+def game(egtlib, name):
+    if name not in GAMES:
+        spec = {"tiny": synth.tiny, "full": synth.full_deck, "kuhn": synth.kuhn,
+                "large": synth.large}[name]()
+        GAMES[name] = egtlib.Game(spec, device=0)
+    return GAMES[name]
+
+
+def run(egtlib, g, engine, variant, iters, eps=0.0, gap_every=1, log_cap=0):
+    x = torch.empty((g.S[0], g.ld), device="cuda")
+    y = torch.empty((g.S[1], g.ld), device="cuda")
+    rep = g.solve(x, y, variant=variant, alpha=0.01, eps_mbb=eps, max_iters=iters,
+                  gap_every=gap_every, engine=engine, log_cap=log_cap)
+    torch.cuda.synchronize()
+    return x, y, rep
+
+
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "full"])
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_device_engine_equals_host_loop_bitwise(egtlib, name, variant):
+    g = game(egtlib, name)
+    xd, yd, rd = run(egtlib, g, egtlib.ENGINE_DEVICE, variant, 60, log_cap=60)
+    xh, yh, rh = run(egtlib, g, egtlib.ENGINE_HOST, variant, 60, log_cap=60)
+    assert torch.equal(xd, xh) and torch.equal(yd, yh)
+    assert rd["iters"] == rh["iters"] == 60
+    assert rd["mu"] == rh["mu"] and rd["tau"] == rh["tau"]
+    assert rd["gap_mbb"] == rh["gap_mbb"]
+    assert rd["backoffs"] == rh["backoffs"] and rd["products"] == rh["products"]
+    assert rd["gap_checks"] == rh["gap_checks"]
+    for a, b in zip(rd["log"], rh["log"]):
+        assert (a["player"], a["tau"], a["mu"], a["backoffs"]) == (b["player"], b["tau"], b["mu"], b["backoffs"])
+        assert a["gap_mbb"] == b["gap_mbb"]
+        assert (np.isnan(a["egv"]) and np.isnan(b["egv"])) or a["egv"] == b["egv"]
+
+
+def test_device_engine_stops_at_the_gap_target(egtlib):
+    g = game(egtlib, "tiny")
+    xd, yd, rd = run(egtlib, g, egtlib.ENGINE_DEVICE, 2, 20000, eps=200.0)
+    xh, yh, rh = run(egtlib, g, egtlib.ENGINE_HOST, 2, 20000, eps=200.0)
+    assert rd["status"] == rh["status"] == "EGT_OK"
+    assert rd["iters"] == rh["iters"] and rd["gap_mbb"] == rh["gap_mbb"] <= 200.0
+    assert torch.equal(xd, xh) and torch.equal(yd, yh)
+
+
+def test_iterate_in_chunks_equals_one_launch(egtlib):
+    g = game(egtlib, "full")
+    g.solver_init(variant=2, alpha=0.01)
+    g.iterate(25, variant=2, gap_every=5)
+    g.iterate(15, variant=2, gap_every=5)
+    x1 = torch.empty((g.S[0], g.ld), device="cuda")
+    g.state_get(x1, None)
+    g.solver_init(variant=2, alpha=0.01)
+    rep = g.iterate(40, variant=2, gap_every=5)
+    x2 = torch.empty((g.S[0], g.ld), device="cuda")
+    g.state_get(x2, None)
+    assert rep["iters"] == 40
+    assert torch.equal(x1, x2)
+
+
+def test_iterate_gap_matches_state_gap(egtlib):
+    g = game(egtlib, "full")
+    g.solver_init(variant=2, alpha=0.01)
+    rep = g.iterate(10, variant=2, gap_every=1)
+    assert rep["gap_mbb"] == g.state_gap()
+
+
+def test_large_game_runs_on_the_device_engine(egtlib):
+    g = game(egtlib, "large")
+    xd, yd, rd = run(egtlib, g, egtlib.ENGINE_DEVICE, 2, 20, gap_every=10)
+    xh, yh, rh = run(egtlib, g, egtlib.ENGINE_HOST, 2, 20, gap_every=10)
+    assert torch.equal(xd, xh) and rd["gap_mbb"] == rh["gap_mbb"]
+
+
+def test_barrier_timeout_is_reported_and_context_survives(egtlib, monkeypatch):
+    g = game(egtlib, "tiny")
+    g.solver_init(variant=2, alpha=0.01)
+    monkeypatch.setenv("EGT_TEST_BARRIER_EXTRA", "1")       # a CTA that never arrives
+    monkeypatch.setenv("EGT_BARRIER_TIMEOUT_MS", "50")
+    with pytest.raises(egtlib.EGTError) as e:
+        g.iterate(3, variant=2)
+    assert e.value.status == 7                              # EGT_ERR_TIMEOUT
+    monkeypatch.delenv("EGT_TEST_BARRIER_EXTRA")
+    monkeypatch.delenv("EGT_BARRIER_TIMEOUT_MS")
+    # the device is still usable and the solver runs normally after re-initialisation
+    xd, yd, rd = run(egtlib, g, egtlib.ENGINE_DEVICE, 2, 10)
+    xh, yh, rh = run(egtlib, g, egtlib.ENGINE_HOST, 2, 10)
+    assert torch.equal(xd, xh)
