@@ -218,6 +218,19 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
                           count_below(hcard[s].y, grp[s].x), count_below(hcard[s].y, grp[s].y));
   }
   std::vector<uint16_t> card_hands((size_t)G->n_slots * G->lmax, 0);
+  // per-hand record of flat shared-memory indices used by the product kernels
+  std::vector<uint4> hinfo(ld);
+  {
+    const unsigned ls = (unsigned)G->lmax + 1;
+    for (int s = 0; s < ld; ++s) {
+      const unsigned a = hcard[s].x, b = hcard[s].y;
+      const unsigned la = (unsigned)lists[a].size(), lb = (unsigned)lists[b].size();
+      hinfo[s] = make_uint4(grp[s].x | ((unsigned)grp[s].y << 16),
+                            (a * ls + cpos[s].x) | ((a * ls + cpos[s].y) << 16),
+                            (a * ls + la) | ((b * ls + cpos[s].z) << 16),
+                            (b * ls + cpos[s].w) | ((b * ls + lb) << 16));
+    }
+  }
   std::vector<int> card_len(G->n_slots);
   for (int c = 0; c < G->n_slots; ++c) {
     card_len[c] = (int)lists[c].size();
@@ -318,7 +331,8 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
 
   if (!to_device) return EGT_OK;
   size_t bytes = 1 << 16;
-  bytes += ld * (sizeof(uchar2) + sizeof(ushort2) + sizeof(uchar4)) + card_hands.size() * 2 + card_len.size() * 4;
+  bytes += ld * (sizeof(uchar2) + sizeof(ushort2) + sizeof(uchar4) + sizeof(uint4)) + card_hands.size() * 2 +
+           card_len.size() * 4;
   for (int p = 0; p < 2; ++p) {
     bytes += ld * (2 * sizeof(float) + 2 * sizeof(double));
     const Treeplex& T = C.tpx[p];
@@ -352,6 +366,7 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
   g.hcard = (const uchar2*)put(hcard.data(), ld * sizeof(uchar2));
   g.grp = (const ushort2*)put(grp.data(), ld * sizeof(ushort2));
   g.cpos = (const uchar4*)put(cpos.data(), ld * sizeof(uchar4));
+  g.hinfo = (const uint4*)put(hinfo.data(), ld * sizeof(uint4));
   g.card_hands = (const uint16_t*)put(card_hands.data(), card_hands.size() * 2);
   g.card_len = (const int*)put(card_len.data(), card_len.size() * 4);
   for (int p = 0; p < 2; ++p) {

@@ -40,6 +40,10 @@ struct DevGame {
   const uchar2* hcard;     // [ld] card slots of each (sorted) hand
   const ushort2* grp;      // [ld] tie group [lo, hi) in sorted order
   const uchar4* cpos;      // [ld] hands of card k before lo / hi: (lo0, hi0, lo1, hi1)
+  // [ld] per hand, eight uint16: tie group lo, hi; then for each of its two card slots the
+  // flat index (slot * (lmax + 1) + position) of the per-card prefix before lo, before hi,
+  // and of the card's total
+  const uint4* hinfo;
   const uint16_t* card_hands;  // [n_slots][lmax] sorted hand indices holding the card
   const int* card_len;     // [n_slots]
   const float* r[2];       // [ld] normalised ranges (0 on padding)

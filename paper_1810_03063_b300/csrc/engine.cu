@@ -75,11 +75,41 @@ __device__ bool grid_sync(const GridBar& b) {
   return ok_s != 0;
 }
 
+// Tables staged once per launch at the start of shared memory.
+struct Tabs {
+  GradTab grad;
+  TpxTab tpx[2];
+};
+
+__host__ __device__ inline size_t tabs_bytes(const DevGame& g) {
+  return grad_tab_bytes(g) + tpx_tab_bytes(g, 0) + tpx_tab_bytes(g, 1);
+}
+
+// Field-by-field selection (a runtime index into a struct array would force a
+// local-memory copy of the array)
+__device__ __forceinline__ TpxTab pick(const Tabs& tb, int p) {
+  const TpxTab& a = tb.tpx[0];
+  const TpxTab& c = tb.tpx[1];
+  TpxTab t;
+  t.S = p ? c.S : a.S;
+  t.J = p ? c.J : a.J;
+  t.L = p ? c.L : a.L;
+  t.beta = p ? c.beta : a.beta;
+  t.level_ptr = p ? c.level_ptr : a.level_ptr;
+  t.inf_first = p ? c.inf_first : a.inf_first;
+  t.inf_n = p ? c.inf_n : a.inf_n;
+  t.inf_parent = p ? c.inf_parent : a.inf_parent;
+  t.child_ptr = p ? c.child_ptr : a.child_ptr;
+  t.child_idx = p ? c.child_idx : a.child_idx;
+  return t;
+}
+
 // One SBR phase: all 32-hand items of `player`, spread over the CTAs.
-__device__ __forceinline__ void run_sbr(const DevGame& g, int player, const float* gv, double mu,
+__device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int player, const float* gv, double mu,
                                         const float* old, double tau, float* out, double* partials,
                                         unsigned char* sm) {
   const int NB = g.ld / kSbrHands;
+  const TpxTab tp = pick(tb, player);
   for (int item = blockIdx.x; item < NB; item += gridDim.x) {
     SbrItemArgs a;
     a.g = gv;
@@ -89,21 +119,28 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, int player, const floa
     a.tau = (float)tau;
     a.out = out;
     a.value_partial = partials ? partials + item : nullptr;
-    sbr_item(g, player, item, a, reinterpret_cast<float*>(sm));
+    sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
   }
 }
 
 // One product phase: every output sequence of `player`.
-__device__ __forceinline__ void run_grad(const DevGame& g, int player, const float* in, float* out,
-                                         unsigned char* sm) {
-  for (int item = blockIdx.x; item < g.tpx[player].S; item += gridDim.x)
-    grad_item<float, float>(g, player, item, in, out, sm);
+__device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, int player, const float* in,
+                                         float* out, unsigned char* sm) {
+  const int S = player ? g.tpx[1].S : g.tpx[0].S;
+  for (int item = blockIdx.x; item < S; item += gridDim.x)
+    grad_item<float, float>(g, tb.grad, player, item, in, out, sm);
 }
 
 __global__ void __launch_bounds__(kItemThreads, 1)
     engine_kernel(DevGame g, EngineBufs b, EngineCtl* ctl, unsigned int expected,
                   unsigned long long limit_ns) {
-  extern __shared__ __align__(16) unsigned char sm[];
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  Tabs tb;
+  tb.grad = stage_grad_tab(g, smem_all);
+  tb.tpx[0] = stage_tpx_tab(g, 0, smem_all + grad_tab_bytes(g));
+  tb.tpx[1] = stage_tpx_tab(g, 1, smem_all + grad_tab_bytes(g) + tpx_tab_bytes(g, 0));
+  __syncthreads();
+  unsigned char* sm = smem_all + tabs_bytes(g);   // per-phase working area
   const GridBar bar{&ctl->bar_count, &ctl->bar_gen, &ctl->status, expected, limit_ns};
   const int NB = g.ld / kSbrHands;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -135,34 +172,42 @@ __global__ void __launch_bounds__(kItemThreads, 1)
     // Alg. 2 Step focused on `me` (the y-focused step swaps roles, A -> -A^T)
     const int ot = 1 - me;
     const bool xs = me == 0;
-    float* v_me = xs ? b.x[cur] : b.y[cur];          // my iterate
-    float* v_ot = xs ? b.y[cur] : b.x[cur];          // the other's iterate
-    float* v_me_n = xs ? b.x[nxt] : b.y[nxt];
-    float* v_ot_n = xs ? b.y[nxt] : b.x[nxt];
-    float* g_me = xs ? b.gx[cur] : b.gy[cur];        // my loss gradient at v_ot
-    float* g_me_n = xs ? b.gx[nxt] : b.gy[nxt];
-    float* g_ot_n = xs ? b.gy[nxt] : b.gx[nxt];
+    float* xc = cur ? b.x[1] : b.x[0];
+    float* xn = cur ? b.x[0] : b.x[1];
+    float* yc = cur ? b.y[1] : b.y[0];
+    float* yn = cur ? b.y[0] : b.y[1];
+    float* gxc = cur ? b.gx[1] : b.gx[0];
+    float* gxn = cur ? b.gx[0] : b.gx[1];
+    float* gyc = cur ? b.gy[1] : b.gy[0];
+    float* gyn = cur ? b.gy[0] : b.gy[1];
+    float* v_me = xs ? xc : yc;                      // my iterate
+    float* v_ot = xs ? yc : xc;                      // the other's iterate
+    float* v_me_n = xs ? xn : yn;
+    float* v_ot_n = xs ? yn : xn;
+    float* g_me = xs ? gxc : gyc;                    // my loss gradient at v_ot
+    float* g_me_n = xs ? gxn : gyn;
+    float* g_ot_n = xs ? gyn : gxn;
     float* t_me = xs ? b.tx : b.ty;
     float* t_ot = xs ? b.ty : b.tx;
     const double mu_me = xs ? mu0 : mu1, mu_ot = xs ? mu1 : mu0;
     for (;;) {
       // v_hat = (1 - tau) v + tau v_mu(other)
-      run_sbr(g, me, g_me, mu_me, v_me, tau, t_me, nullptr, sm);
+      run_sbr(g, tb, me, g_me, mu_me, v_me, tau, t_me, nullptr, sm);
       if (!grid_sync(bar)) return;
-      run_grad(g, ot, t_me, t_ot, sm);                  // the other's loss gradient at v_hat
+      run_grad(g, tb, ot, t_me, t_ot, sm);                  // the other's loss gradient at v_hat
       if (!grid_sync(bar)) return;
       // other_+ = (1 - tau) other + tau other_mu(v_hat)
-      run_sbr(g, ot, t_ot, mu_ot, v_ot, tau, v_ot_n, nullptr, sm);
+      run_sbr(g, tb, ot, t_ot, mu_ot, v_ot, tau, v_ot_n, nullptr, sm);
       if (!grid_sync(bar)) return;
-      run_grad(g, me, v_ot_n, g_me_n, sm);              // my loss gradient at other_+
+      run_grad(g, tb, me, v_ot_n, g_me_n, sm);              // my loss gradient at other_+
       if (!grid_sync(bar)) return;
       // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part
-      run_sbr(g, me, g_me_n, (1 - tau) * mu_me, v_me, tau, v_me_n, partA, sm);
+      run_sbr(g, tb, me, g_me_n, (1 - tau) * mu_me, v_me, tau, v_me_n, partA, sm);
       if (!grid_sync(bar)) return;
-      run_grad(g, ot, v_me_n, g_ot_n, sm);              // the other's loss gradient at v_+
+      run_grad(g, tb, ot, v_me_n, g_ot_n, sm);              // the other's loss gradient at v_+
       if (!grid_sync(bar)) return;
       if (!check) break;
-      run_sbr(g, ot, g_ot_n, mu_ot, nullptr, 0.0, nullptr, partB, sm);   // the other's EGV part
+      run_sbr(g, tb, ot, g_ot_n, mu_ot, nullptr, 0.0, nullptr, partB, sm);   // the other's EGV part
       if (!grid_sync(bar)) return;
       if (leader) {
         const double a = reduce_partials(partA, NB, lane);
@@ -221,19 +266,18 @@ __global__ void __launch_bounds__(kItemThreads, 1)
     }
     if (gap_due) {
       // eps_sad of the new iterates: FP64 products of both players, then both best responses
-      const float* xn = b.x[nxt];
-      const float* yn = b.y[nxt];
       const int S0 = g.tpx[0].S, S1 = g.tpx[1].S;
       for (int item = blockIdx.x; item < S0 + S1; item += gridDim.x) {
-        if (item < S0) grad_item<float, double>(g, 0, item, yn, b.g64[0], sm);
-        else grad_item<float, double>(g, 1, item - S0, xn, b.g64[1], sm);
+        if (item < S0) grad_item<float, double>(g, tb.grad, 0, item, yn, b.g64[0], sm);
+        else grad_item<float, double>(g, tb.grad, 1, item - S0, xn, b.g64[1], sm);
       }
       if (!grid_sync(bar)) return;
       for (int item = blockIdx.x; item < 2 * NB; item += gridDim.x) {
         if (item < NB)
-          br64_item(g, 0, item, b.g64[0], 1.0, partBR0 + item, reinterpret_cast<double*>(sm));
+          br64_item(g, tb.tpx[0], item, b.g64[0], 1.0, partBR0 + item, reinterpret_cast<double*>(sm));
         else
-          br64_item(g, 1, item - NB, b.g64[1], -1.0, partBR1 + item - NB, reinterpret_cast<double*>(sm));
+          br64_item(g, tb.tpx[1], item - NB, b.g64[1], -1.0, partBR1 + item - NB,
+                    reinterpret_cast<double*>(sm));
       }
       if (!grid_sync(bar)) return;
       if (leader) {
@@ -262,7 +306,7 @@ size_t engine_smem_bytes(const DevGame& g) {
     m = std::max(m, sbr_item_smem(g, p));
     m = std::max(m, br_item_smem(g, p));
   }
-  return m;
+  return tabs_bytes(g) + m;
 }
 
 cudaError_t engine_launch(const DevGame& g, const EngineBufs& b, EngineCtl* ctl, int grid,

@@ -273,18 +273,45 @@ constexpr int kMaxHandsPerThread = 8;   // ld <= 2048 with 256 threads per half
 
 }  // namespace gradimpl
 
-// Shared memory of one gradient CTA.
+// Shared memory of one gradient CTA (without the staged tables).
 inline size_t grad_item_smem(const DevGame& g, bool f64) {
   return 2 * (f64 ? gradimpl::half_bytes<double>(g.ld, g.n_slots, g.lmax)
                   : gradimpl::half_bytes<float>(g.ld, g.n_slots, g.lmax));
+}
+
+// Per-game tables the product reads for every terminal, staged once in shared memory.
+struct GradTab {
+  const uint4* hinfo;          // [ld] per-hand flat indices (see DevGame::hinfo)
+  const int* card_len;         // [n_slots]
+  const uint16_t* card_hands;  // [n_slots][lmax]
+};
+
+__host__ __device__ inline size_t grad_tab_bytes(const DevGame& g) {
+  using gradimpl::align16;
+  return align16((size_t)g.ld * sizeof(uint4)) + align16((size_t)g.n_slots * sizeof(int)) +
+         align16((size_t)g.n_slots * g.lmax * sizeof(uint16_t));
+}
+
+// Copy the tables into dst (all threads of the CTA; the caller synchronises before use).
+__device__ inline GradTab stage_grad_tab(const DevGame& g, unsigned char* dst) {
+  using gradimpl::align16;
+  uint4* hi = reinterpret_cast<uint4*>(dst);
+  int* cl = reinterpret_cast<int*>(dst + align16((size_t)g.ld * sizeof(uint4)));
+  uint16_t* ch = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(cl) +
+                                             align16((size_t)g.n_slots * sizeof(int)));
+  for (int i = threadIdx.x; i < g.ld; i += blockDim.x) hi[i] = g.hinfo[i];
+  for (int i = threadIdx.x; i < g.n_slots; i += blockDim.x) cl[i] = g.card_len[i];
+  for (int i = threadIdx.x; i < g.n_slots * g.lmax; i += blockDim.x) ch[i] = g.card_hands[i];
+  return {hi, cl, ch};
 }
 
 // Output column s of player `player` (out[s][*] = (A in)[s] for player 0, (A^T in)[s]
 // for player 1), computed by one CTA of kItemThreads threads.  `in` is read through L2
 // (it may have been written earlier in the same launch by other CTAs).
 template <typename TIn, typename T>
-__device__ inline void grad_item(const DevGame& g, int player, int s, const TIn* __restrict__ in,
-                                 T* __restrict__ out, unsigned char* smem) {
+__device__ inline void grad_item(const DevGame& g, const GradTab& tb, int player, int s,
+                                 const TIn* __restrict__ in, T* __restrict__ out,
+                                 unsigned char* smem) {
   using namespace gradimpl;
   using C = Conv<T>;
   constexpr int NL = C::NL;
@@ -358,8 +385,8 @@ __device__ inline void grad_item(const DevGame& g, int player, int s, const TIn*
 
     // per-card exclusive prefixes, one warp per card slot
     for (int c = hw; c < g.n_slots; c += kHalfWarps) {
-      const int len = g.card_len[c];
-      const uint16_t* lst = g.card_hands + (size_t)c * g.lmax;
+      const int len = tb.card_len[c];
+      const uint16_t* lst = tb.card_hands + (size_t)c * g.lmax;
       const Fx<NL> v0 = lane < len ? F[lst[lane]] : fx_zero<NL>();
       const Fx<NL> v1 = lane + 32 < len ? F[lst[lane + 32]] : fx_zero<NL>();
       const Fx<NL> a0 = fx_scan(v0, lane);
@@ -377,21 +404,17 @@ __device__ inline void grad_item(const DevGame& g, int player, int s, const TIn*
     for (int k = 0; k < kMaxHandsPerThread; ++k) {
       const int h = th + k * kHalfThreads;
       if (h >= ld) break;
-      const uchar2 cc = g.hcard[h];
-      const Fx<NL>* pc0 = PC + (size_t)cc.x * lstride;
-      const Fx<NL>* pc1 = PC + (size_t)cc.y * lstride;
-      const Fx<NL> C0 = pc0[g.card_len[cc.x]];
-      const Fx<NL> C1 = pc1[g.card_len[cc.y]];
+      const uint4 hi = tb.hinfo[h];
+      const Fx<NL> C0 = PC[hi.z & 0xffffu];
+      const Fx<NL> C1 = PC[hi.w >> 16];
       Fx<NL> val;
       if (kind == 0) {
         val = fx_sub(fx_sub(W, C0), C1);
         if (g.hand_size == 2) val = fx_add(val, F[h]);
       } else {
-        const ushort2 gr = g.grp[h];
-        const uchar4 cp = g.cpos[h];
-        const Fx<NL> lt = fx_sub(fx_sub(P[gr.x], pc0[cp.x]), pc1[cp.z]);
-        const Fx<NL> gt = fx_sub(fx_sub(fx_sub(W, P[gr.y]), fx_sub(C0, pc0[cp.y])),
-                                 fx_sub(C1, pc1[cp.w]));
+        const Fx<NL> lt = fx_sub(fx_sub(P[hi.x & 0xffffu], PC[hi.y & 0xffffu]), PC[hi.z >> 16]);
+        const Fx<NL> gt = fx_sub(fx_sub(fx_sub(W, P[hi.x >> 16]), fx_sub(C0, PC[hi.y >> 16])),
+                                 fx_sub(C1, PC[hi.w & 0xffffu]));
         val = fx_sub(gt, lt);
       }
       acc[k].add(coef, C::from_fx(val, ex));

@@ -40,7 +40,10 @@ __global__ void __launch_bounds__(kItemThreads) sbr_kernel(DevGame g, int player
   ia.tau = a.tau;
   ia.out = a.out;
   ia.value_partial = a.value_dev != nullptr ? a.partials + blockIdx.x : nullptr;
-  sbr_item(g, player, blockIdx.x, ia, sm);
+  unsigned char* raw = reinterpret_cast<unsigned char*>(sm);
+  const TpxTab tt = stage_tpx_tab(g, player, raw);
+  __syncthreads();
+  sbr_item(g, tt, blockIdx.x, ia, reinterpret_cast<float*>(raw + tpx_tab_bytes(g, player)));
   if (a.value_dev != nullptr) finish_value(a.partials, a.counter, a.value_dev, a.status);
 }
 
@@ -48,15 +51,23 @@ __global__ void __launch_bounds__(kItemThreads)
     br64_kernel(DevGame g, int player, const double* __restrict__ gv, double sign,
                 double* value_dev, double* partials, unsigned int* counter) {
   extern __shared__ __align__(16) double smd[];
-  br64_item(g, player, blockIdx.x, gv, sign, partials + blockIdx.x, smd);
+  unsigned char* raw = reinterpret_cast<unsigned char*>(smd);
+  const TpxTab tt = stage_tpx_tab(g, player, raw);
+  __syncthreads();
+  br64_item(g, tt, blockIdx.x, gv, sign, partials + blockIdx.x,
+            reinterpret_cast<double*>(raw + tpx_tab_bytes(g, player)));
   finish_value(partials, counter, value_dev, nullptr);
 }
 
 }  // namespace
 
-size_t sbr_smem_bytes(const DevGame& g, int player) { return sbr_item_smem(g, player); }
+size_t sbr_smem_bytes(const DevGame& g, int player) {
+  return tpx_tab_bytes(g, player) + sbr_item_smem(g, player);
+}
 
-size_t br_smem_bytes(const DevGame& g, int player) { return br_item_smem(g, player); }
+size_t br_smem_bytes(const DevGame& g, int player) {
+  return tpx_tab_bytes(g, player) + br_item_smem(g, player);
+}
 
 int opt_in_dynamic_smem(const void* kernel) {
   int dev = 0, optin = 0;
@@ -75,7 +86,7 @@ void launch_sbr(const DevGame& g, int player, const SbrArgs& a, cudaStream_t st)
   static int limit = 0;
   if (limit == 0) limit = opt_in_dynamic_smem((const void*)sbr_kernel);
   const int grid = g.ld / kSbrHands;
-  sbr_kernel<<<grid, kItemThreads, sbr_item_smem(g, player), st>>>(g, player, a);
+  sbr_kernel<<<grid, kItemThreads, sbr_smem_bytes(g, player), st>>>(g, player, a);
 }
 
 void launch_br64(const DevGame& g, int player, const double* gv, double sign, double* value_dev,
@@ -83,8 +94,8 @@ void launch_br64(const DevGame& g, int player, const double* gv, double sign, do
   static int limit = 0;
   if (limit == 0) limit = opt_in_dynamic_smem((const void*)br64_kernel);
   const int grid = g.ld / kSbrHands;
-  br64_kernel<<<grid, kItemThreads, br_item_smem(g, player), st>>>(g, player, gv, sign, value_dev,
-                                                                    partials, counter);
+  br64_kernel<<<grid, kItemThreads, br_smem_bytes(g, player), st>>>(g, player, gv, sign, value_dev,
+                                                                     partials, counter);
 }
 
 }  // namespace egt

@@ -34,6 +34,7 @@ struct SbrItemArgs {
   double* value_partial;   // if non-NULL: this item's sum over live hands and root simplexes
 };
 
+// (the shared memory below excludes the staged tables)
 inline size_t sbr_item_smem(const DevGame& g, int player) {
   const DevTpx& tp = g.tpx[player];
   return ((size_t)2 * tp.S * kSbrHands + (size_t)tp.J * kSbrHands + 2 * (size_t)tp.J) * sizeof(float);
@@ -42,6 +43,59 @@ inline size_t sbr_item_smem(const DevGame& g, int player) {
 inline size_t br_item_smem(const DevGame& g, int player) {
   const DevTpx& tp = g.tpx[player];
   return ((size_t)tp.S * kSbrHands + (size_t)tp.J * kSbrHands) * sizeof(double);
+}
+
+// One player's treeplex tables (Sec. 4 notation), staged once in shared memory.
+struct TpxTab {
+  int S, J, L;
+  const double* beta;      // [J]
+  const int* level_ptr;    // [L+1]
+  const int* inf_first;    // [J]
+  const int* inf_n;        // [J]
+  const int* inf_parent;   // [J]
+  const int* child_ptr;    // [S+1]
+  const int* child_idx;    // [<= J]
+};
+
+__host__ __device__ inline size_t tpx_tab_bytes(const DevGame& g, int player) {
+  const DevTpx& tp = g.tpx[player];
+  return gradimpl::align16((size_t)tp.J * sizeof(double)) +
+         gradimpl::align16((size_t)(tp.L + 1 + 4 * tp.J + tp.S + 1) * sizeof(int));
+}
+
+// Copy player's tables into dst (all threads; the caller synchronises before use).
+__device__ inline TpxTab stage_tpx_tab(const DevGame& g, int player, unsigned char* dst) {
+  const DevTpx& tp = g.tpx[player];
+  TpxTab t;
+  t.S = tp.S;
+  t.J = tp.J;
+  t.L = tp.L;
+  double* beta = reinterpret_cast<double*>(dst);
+  int* ip = reinterpret_cast<int*>(dst + gradimpl::align16((size_t)tp.J * sizeof(double)));
+  int* lp = ip;
+  int* fi = lp + tp.L + 1;
+  int* nn = fi + tp.J;
+  int* pa = nn + tp.J;
+  int* cp = pa + tp.J;
+  int* ci = cp + tp.S + 1;
+  const int nchild = tp.child_ptr[tp.S];
+  for (int i = threadIdx.x; i < tp.J; i += blockDim.x) {
+    beta[i] = tp.beta[i];
+    fi[i] = tp.inf_first[i];
+    nn[i] = tp.inf_n[i];
+    pa[i] = tp.inf_parent[i];
+  }
+  for (int i = threadIdx.x; i <= tp.L; i += blockDim.x) lp[i] = tp.level_ptr[i];
+  for (int i = threadIdx.x; i <= tp.S; i += blockDim.x) cp[i] = tp.child_ptr[i];
+  for (int i = threadIdx.x; i < nchild; i += blockDim.x) ci[i] = tp.child_idx[i];
+  t.beta = beta;
+  t.level_ptr = lp;
+  t.inf_first = fi;
+  t.inf_n = nn;
+  t.inf_parent = pa;
+  t.child_ptr = cp;
+  t.child_idx = ci;
+  return t;
 }
 
 // Sum of n partial values in a fixed order (lane-strided, then a shuffle tree);
@@ -55,9 +109,8 @@ __device__ __forceinline__ double reduce_partials(const double* p, int n, int la
 }
 
 // One item (32 hands starting at blk * 32) of player `player`'s smoothed best response.
-__device__ inline void sbr_item(const DevGame& g, int player, int blk, const SbrItemArgs& a,
+__device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, const SbrItemArgs& a,
                                 float* sm) {
-  const DevTpx tp = g.tpx[player];
   const int S = tp.S, J = tp.J, ld = g.ld;
   constexpr int kWarps = kItemThreads / 32;
   float* G = sm;                                   // [S][32] sign*g -> g_hat -> q_bar -> q
@@ -76,9 +129,9 @@ __device__ inline void sbr_item(const DevGame& g, int player, int blk, const Sbr
     if (a.old != nullptr) O[idx] = __ldcg(a.old + gi);
   }
   for (int j = tid; j < J; j += kItemThreads) {
-    const double t = a.mu * tp.beta[j];
-    tj[j] = (float)t;
-    itj[j] = (float)(1.0 / t);
+    const float t = (float)(a.mu * tp.beta[j]);
+    tj[j] = t;
+    itj[j] = 1.f / t;
   }
   __syncthreads();
 
@@ -146,9 +199,8 @@ __device__ inline void sbr_item(const DevGame& g, int player, int blk, const Sbr
 
 // One item of the FP64 best-response value: sign * min over the treeplex of
 // <q, sign * g> summed over the item's live hands, written to *value_partial.
-__device__ inline void br64_item(const DevGame& g, int player, int blk, const double* gv,
+__device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, const double* gv,
                                  double sign, double* value_partial, double* sm) {
-  const DevTpx tp = g.tpx[player];
   const int S = tp.S, ld = g.ld;
   constexpr int kWarps = kItemThreads / 32;
   double* G = sm;                                  // [S][32]
