@@ -311,6 +311,17 @@ EGT_API egt_status egt_profile(egt_game* game, int32_t enable);
  * entries, either may be NULL).  Waits for the recorded launches to finish. */
 EGT_API egt_status egt_profile_read(egt_game* game, double* ms, int64_t* launches);
 
+/* Device time of the device-resident driver (egt_iterate / egt_solve) by phase,
+ * measured by CTA 0 between consecutive grid-barrier exits (so a phase includes
+ * the wait for its slowest CTA and the barrier), summed since the last reset:
+ * 0-6 the Step's SBR / product / SBR / product / SBR / product phases and the
+ * EGV smoothed best response, 7 the EGV decision, 8 the accept barrier of an
+ * iteration without residual, 9 the residual's FP64 products, 10 its FP64 best
+ * responses and decision.  Host arrays of 11 entries (microseconds, counts),
+ * either may be NULL; reset != 0 clears the sums after reading. */
+EGT_API egt_status egt_engine_trace(egt_game* game, int32_t reset, double* phase_us,
+                                    int64_t* phase_count);
+
 /* Message of the last failed call on this thread ("" if none). */
 EGT_API const char* egt_last_error(void);
 

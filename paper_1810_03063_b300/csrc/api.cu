@@ -87,6 +87,8 @@ struct egt_game {
   EngineCtl* ctl_host = nullptr;
   double* eng_partials = nullptr;
   int eng_grid = -2;             // -2: not queried yet, <= 0: engine unavailable
+  double eng_phase_ns[kEnginePhases] = {0};
+  long long eng_phase_n[kEnginePhases] = {0};
   bool host_only = false;        // compiled tables only (device = -1): queries work, kernels do not
   long long products = 0;
   // per-kernel device time accounting (egt_profile): CUDA events around each launch
@@ -783,6 +785,10 @@ egt_status engine_run(egt_game* G, int variant, double eps_mbb, int gap_every, i
   G->tau = c.tau;
   G->last_gap = c.gap_mbb;
   G->products += c.products;
+  for (int k = 0; k < kEnginePhases; ++k) {
+    G->eng_phase_ns[k] += (double)c.phase_ns[k];
+    G->eng_phase_n[k] += (long long)c.phase_n[k];
+  }
   if (rep) {
     rep->iters = c.done_iters;
     rep->products = c.products;
@@ -1216,6 +1222,19 @@ egt_status egt_profile(egt_game* G, int32_t enable) {
     G->launches[k] = 0;
   }
   G->prof_on = enable != 0;
+  return EGT_OK;
+}
+
+egt_status egt_engine_trace(egt_game* G, int32_t reset, double* phase_us, int64_t* phase_count) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  for (int k = 0; k < kEnginePhases; ++k) {
+    if (phase_us) phase_us[k] = G->eng_phase_ns[k] * 1e-3;
+    if (phase_count) phase_count[k] = G->eng_phase_n[k];
+    if (reset) {
+      G->eng_phase_ns[k] = 0;
+      G->eng_phase_n[k] = 0;
+    }
+  }
   return EGT_OK;
 }
 

@@ -5,13 +5,16 @@
 //
 // Phases are separated by a grid barrier; the work of a phase (32-hand SBR
 // items, one output sequence per gradient item) is spread over the CTAs.
-// Decisions (EGV sign, gap target) are taken by one warp of CTA 0 from per-item
-// FP64 partials summed in the same fixed order as the standalone kernels, so a
-// run here reproduces the host-driven loop of api.cu bit for bit.
+// Every CTA keeps its own copy of the solver state (t, mu, tau, buffer index)
+// and takes every decision (EGV sign, tau back-off, gap target) itself from
+// the same per-item FP64 partials, summed in the same fixed order as the
+// standalone kernels: all CTAs agree without a broadcast, and a run here
+// reproduces the host-driven loop of api.cu bit for bit.
 //
-// The grid barrier spins on a generation word with a time limit: if it runs out
-// (a CTA that never arrives), the kernel records EGT_ERR_TIMEOUT and every CTA
-// returns; the host reads the status and the context stays usable.
+// The grid barrier is a monotone 64-bit arrival counter: barrier k completes
+// when it reaches k x (number of CTAs).  Waits are bounded in time: if one runs
+// out (a CTA that never arrives), the kernel records EGT_ERR_TIMEOUT and every
+// CTA returns; the host reads the status and the context stays usable.
 #include <algorithm>
 
 #include "../../include/egt.h"
@@ -29,50 +32,74 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-template <typename T>
-__device__ __forceinline__ T vload(const T* p) {
-  return *reinterpret_cast<const volatile T*>(p);
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
 }
 
 struct GridBar {
-  unsigned int* count;
-  unsigned int* gen;
+  unsigned long long* arrive;   // monotone arrival counter (zeroed by the host per launch)
   int* status;
-  unsigned int expected;        // arrivals that complete the barrier (gridDim.x unless a test adds phantoms)
+  unsigned long long expected;  // arrivals per barrier (the grid, unless a test adds phantoms)
   unsigned long long limit_ns;
 };
 
-// All CTAs meet here; returns false (in every thread) if the barrier timed out
-// anywhere or an error status was recorded.
-__device__ bool grid_sync(const GridBar& b) {
+// All CTAs meet here; k counts this CTA's barriers.  Returns false (in every
+// thread) if the wait ran out or an error status was recorded.
+__device__ bool grid_sync(const GridBar& b, unsigned long long& k) {
   __shared__ int ok_s;
   __syncthreads();
+  ++k;
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned int g0 = vload(b.gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(b.count, 1u) + 1u;
-    if (arrived == b.expected) {
-      atomicExch(b.count, 0u);
-      __threadfence();
-      atomicAdd(b.gen, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (vload(b.gen) == g0) {
-        if (global_ns() - t0 > b.limit_ns) {
+    __threadfence();                       // release this CTA's writes of the phase
+    atomicAdd(b.arrive, 1ull);
+    const unsigned long long target = k * b.expected;
+    unsigned int polls = 0;
+    unsigned long long t0 = 0;
+    while (ld_acquire(b.arrive) < target) {
+      if ((++polls & 1023u) == 0) {
+        const unsigned long long now = global_ns();
+        if (t0 == 0) {
+          t0 = now;
+        } else if (now - t0 > b.limit_ns) {
           atomicCAS(b.status, 0, (int)EGT_ERR_TIMEOUT);
           ok = 0;
           break;
         }
-        __nanosleep(32);
+        if (ld_volatile(b.status) != 0) {
+          ok = 0;
+          break;
+        }
       }
     }
-    __threadfence();
-    if (vload(b.status) != 0) ok = 0;
+    if (ld_volatile(b.status) != 0) ok = 0;
     ok_s = ok;
   }
   __syncthreads();
   return ok_s != 0;
+}
+
+// Phase clock of CTA 0 (thread 0): time since the previous barrier exit, kept in
+// shared memory and written to the control block at exit.
+struct PhaseClock {
+  unsigned long long last;
+  unsigned long long ns[kEnginePhases];
+  unsigned int n[kEnginePhases];
+};
+
+__device__ __forceinline__ void phase_mark(PhaseClock* c, int phase) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long now = global_ns();
+    c->ns[phase] += now - c->last;
+    c->n[phase] += 1;
+    c->last = now;
+  }
 }
 
 // Tables staged once per launch at the start of shared memory.
@@ -105,9 +132,9 @@ __device__ __forceinline__ TpxTab pick(const Tabs& tb, int p) {
 }
 
 // One SBR phase: all 32-hand items of `player`, spread over the CTAs.
-__device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int player, const float* gv, double mu,
-                                        const float* old, double tau, float* out, double* partials,
-                                        unsigned char* sm) {
+__device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int player, const float* gv,
+                                        double mu, const float* old, double tau, float* out,
+                                        double* partials, unsigned char* sm) {
   const int NB = g.ld / kSbrHands;
   const TpxTab tp = pick(tb, player);
   for (int item = blockIdx.x; item < NB; item += gridDim.x) {
@@ -131,8 +158,26 @@ __device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, int p
     grad_item<float, float>(g, tb.grad, player, item, in, out, sm);
 }
 
+// Two fixed-order sums of per-item partials, computed by warp 0 of every CTA
+// and shared with the CTA.
+__device__ __forceinline__ void reduce_pair(const double* p, const double* q, int n, double& a, double& c) {
+  __shared__ double s[2];
+  if (threadIdx.x < 32) {
+    const double va = reduce_partials(p, n, threadIdx.x);
+    const double vc = reduce_partials(q, n, threadIdx.x);
+    if (threadIdx.x == 0) {
+      s[0] = va;
+      s[1] = vc;
+    }
+  }
+  __syncthreads();
+  a = s[0];
+  c = s[1];
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kItemThreads, 1)
-    engine_kernel(DevGame g, EngineBufs b, EngineCtl* ctl, unsigned int expected,
+    engine_kernel(DevGame g, EngineBufs b, EngineCtl* ctl, unsigned long long expected,
                   unsigned long long limit_ns) {
   extern __shared__ __align__(16) unsigned char smem_all[];
   Tabs tb;
@@ -141,22 +186,36 @@ __global__ void __launch_bounds__(kItemThreads, 1)
   tb.tpx[1] = stage_tpx_tab(g, 1, smem_all + grad_tab_bytes(g) + tpx_tab_bytes(g, 0));
   __syncthreads();
   unsigned char* sm = smem_all + tabs_bytes(g);   // per-phase working area
-  const GridBar bar{&ctl->bar_count, &ctl->bar_gen, &ctl->status, expected, limit_ns};
+  const GridBar bar{&ctl->bar_arrive, &ctl->status, expected, limit_ns};
+  unsigned long long bk = 0;                      // barriers passed by this CTA
+  __shared__ PhaseClock clk_s;
+  PhaseClock* clk = &clk_s;
+  if (threadIdx.x == 0) {
+    clk->last = global_ns();
+    for (int k = 0; k < kEnginePhases; ++k) {
+      clk->ns[k] = 0;
+      clk->n[k] = 0;
+    }
+  }
+  const bool writer = blockIdx.x == 0 && threadIdx.x == 0;
   const int NB = g.ld / kSbrHands;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool leader = blockIdx.x == 0 && warp == 0;
   double* partA = b.partials;
   double* partB = b.partials + NB;
   double* partBR0 = b.partials + 2 * NB;
   double* partBR1 = b.partials + 3 * NB;
   const int variant = ctl->variant, n_iters = ctl->n_iters, gap_every = ctl->gap_every;
   const int max_t = ctl->max_t;
-  const double eps_mbb = ctl->eps_mbb;
+  const double eps_mbb = ctl->eps_mbb, bb = ctl->bb;
 
-  for (int it = 0; it < n_iters; ++it) {
-    const int t = vload(&ctl->t);
-    const int cur = vload(&ctl->cur), nxt = 1 - cur;
-    const double mu0 = vload(&ctl->mu[0]), mu1 = vload(&ctl->mu[1]);
+  // solver state, identical in every CTA
+  int t = ctl->t, cur = ctl->cur;
+  double mu0 = ctl->mu[0], mu1 = ctl->mu[1], tau_as = ctl->tau, gap = ctl->gap_mbb;
+  int done = 0, backoffs_total = 0, products = 0, gap_checks = 0, reached = 0, status = 0;
+  int last_player = -1, last_backoffs = 0;
+  double last_tau = 0.0 / 0.0, last_egv = 0.0 / 0.0;
+
+  for (int it = 0; it < n_iters && status == 0; ++it) {
+    const int nxt = 1 - cur;
     int me;
     double tau;
     if (variant == EGT_THEORY) {
@@ -164,7 +223,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
       tau = 2.0 / (t + 3);
     } else {
       me = mu0 > mu1 ? 0 : 1;
-      tau = variant == EGT_PRACTICAL ? 2.0 / (t + 3) : vload(&ctl->tau);
+      tau = variant == EGT_PRACTICAL ? 2.0 / (t + 3) : tau_as;
     }
     const bool check = variant == EGT_AS;
     int backoffs = 0;
@@ -193,85 +252,79 @@ __global__ void __launch_bounds__(kItemThreads, 1)
     for (;;) {
       // v_hat = (1 - tau) v + tau v_mu(other)
       run_sbr(g, tb, me, g_me, mu_me, v_me, tau, t_me, nullptr, sm);
-      if (!grid_sync(bar)) return;
+      if (!grid_sync(bar, bk)) return;
+      phase_mark(clk, 0);
       run_grad(g, tb, ot, t_me, t_ot, sm);                  // the other's loss gradient at v_hat
-      if (!grid_sync(bar)) return;
+      if (!grid_sync(bar, bk)) return;
+      phase_mark(clk, 1);
       // other_+ = (1 - tau) other + tau other_mu(v_hat)
       run_sbr(g, tb, ot, t_ot, mu_ot, v_ot, tau, v_ot_n, nullptr, sm);
-      if (!grid_sync(bar)) return;
+      if (!grid_sync(bar, bk)) return;
+      phase_mark(clk, 2);
       run_grad(g, tb, me, v_ot_n, g_me_n, sm);              // my loss gradient at other_+
-      if (!grid_sync(bar)) return;
+      if (!grid_sync(bar, bk)) return;
+      phase_mark(clk, 3);
       // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part
       run_sbr(g, tb, me, g_me_n, (1 - tau) * mu_me, v_me, tau, v_me_n, partA, sm);
-      if (!grid_sync(bar)) return;
+      if (!grid_sync(bar, bk)) return;
+      phase_mark(clk, 4);
       run_grad(g, tb, ot, v_me_n, g_ot_n, sm);              // the other's loss gradient at v_+
-      if (!grid_sync(bar)) return;
+      if (!grid_sync(bar, bk)) return;
+      phase_mark(clk, 5);
+      products += 3;
       if (!check) break;
       run_sbr(g, tb, ot, g_ot_n, mu_ot, nullptr, 0.0, nullptr, partB, sm);   // the other's EGV part
-      if (!grid_sync(bar)) return;
-      if (leader) {
-        const double a = reduce_partials(partA, NB, lane);
-        const double c = reduce_partials(partB, NB, lane);
-        if (lane == 0) {
-          const double phi = xs ? a : c, negf = xs ? c : a;
-          const double v = phi + negf;
-          int retry = 0;
-          if (!isfinite(v)) {
-            atomicCAS(&ctl->status, 0, (int)EGT_ERR_NUMERIC);
-          } else if (v < 0) {
-            const double nt = tau * 0.5;
-            if (nt < 1.0 / (1u << 30)) atomicCAS(&ctl->status, 0, (int)EGT_ERR_TAU_UNDERFLOW);
-            else retry = 1;
-            ctl->tau = nt;
-          }
-          ctl->egv = v;
-          ctl->retry = retry;
-          __threadfence();
-        }
+      if (!grid_sync(bar, bk)) return;
+      phase_mark(clk, 6);
+      double a, c;
+      reduce_pair(partA, partB, NB, a, c);
+      const double phi = xs ? a : c, negf = xs ? c : a;
+      egv = phi + negf;
+      if (!isfinite(egv)) {
+        status = EGT_ERR_NUMERIC;
+        break;
       }
-      if (!grid_sync(bar)) return;
-      egv = vload(&ctl->egv);
-      if (!vload(&ctl->retry)) break;
-      tau = vload(&ctl->tau);
+      if (egv >= 0) break;
+      tau *= 0.5;
+      if (tau < 1.0 / (1u << 30)) {
+        status = EGT_ERR_TAU_UNDERFLOW;
+        break;
+      }
       ++backoffs;
     }
+    if (status != 0) break;
     // accept (Alg. 2 last lines): mu_me^+ = (1 - tau) mu_me, swap the iterate buffers
-    const int t1 = t + 1;
-    const bool gap_due = t1 % gap_every == 0 || t1 >= max_t;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      if (xs) ctl->mu[0] = mu0 * (1.0 - tau);
-      else ctl->mu[1] = mu1 * (1.0 - tau);
-      ctl->cur = nxt;
-      ctl->t = t1;
-      if (variant == EGT_AS) ctl->tau = tau;
-      ctl->backoffs += backoffs;
-      ctl->products += 3 * (backoffs + 1);
-      ctl->done_iters += 1;
-      ctl->last_player = me;
-      ctl->last_backoffs = backoffs;
-      ctl->last_tau = tau;
-      ctl->last_egv = egv;
-      if (b.log != nullptr && it < b.log_cap) {
-        egt_iter_log& L = b.log[it];
-        L.t = t;
-        L.player = me;
-        L.backoffs = backoffs;
-        L.tau = tau;
-        L.mu[0] = xs ? mu0 * (1.0 - tau) : mu0;
-        L.mu[1] = xs ? mu1 : mu1 * (1.0 - tau);
-        L.egv = check ? egv : 0.0 / 0.0;
-        L.gap_mbb = vload(&ctl->gap_mbb);
-      }
-      __threadfence();
+    if (xs) mu0 *= (1.0 - tau);
+    else mu1 *= (1.0 - tau);
+    if (variant == EGT_AS) tau_as = tau;
+    if (writer && b.log != nullptr && it < b.log_cap) {
+      egt_iter_log& L = b.log[it];
+      L.t = t;
+      L.player = me;
+      L.backoffs = backoffs;
+      L.tau = tau;
+      L.mu[0] = mu0;
+      L.mu[1] = mu1;
+      L.egv = check ? egv : 0.0 / 0.0;
+      L.gap_mbb = gap;
     }
-    if (gap_due) {
+    cur = nxt;
+    t += 1;
+    backoffs_total += backoffs;
+    done += 1;
+    last_player = me;
+    last_backoffs = backoffs;
+    last_tau = tau;
+    last_egv = egv;
+    if (t % gap_every == 0 || t >= max_t) {
       // eps_sad of the new iterates: FP64 products of both players, then both best responses
       const int S0 = g.tpx[0].S, S1 = g.tpx[1].S;
       for (int item = blockIdx.x; item < S0 + S1; item += gridDim.x) {
         if (item < S0) grad_item<float, double>(g, tb.grad, 0, item, yn, b.g64[0], sm);
         else grad_item<float, double>(g, tb.grad, 1, item - S0, xn, b.g64[1], sm);
       }
-      if (!grid_sync(bar)) return;
+      if (!grid_sync(bar, bk)) return;
+      phase_mark(clk, 9);
       for (int item = blockIdx.x; item < 2 * NB; item += gridDim.x) {
         if (item < NB)
           br64_item(g, tb.tpx[0], item, b.g64[0], 1.0, partBR0 + item, reinterpret_cast<double*>(sm));
@@ -279,22 +332,43 @@ __global__ void __launch_bounds__(kItemThreads, 1)
           br64_item(g, tb.tpx[1], item - NB, b.g64[1], -1.0, partBR1 + item - NB,
                     reinterpret_cast<double*>(sm));
       }
-      if (!grid_sync(bar)) return;
-      if (leader) {
-        const double vmin = reduce_partials(partBR0, NB, lane);
-        const double vmax = reduce_partials(partBR1, NB, lane);
-        if (lane == 0) {
-          const double gap = (vmax - vmin) / ctl->bb * 1000.0;
-          if (!isfinite(gap)) atomicCAS(&ctl->status, 0, (int)EGT_ERR_NUMERIC);
-          ctl->gap_mbb = gap;
-          ctl->gap_checks += 1;
-          ctl->reached = eps_mbb > 0 && gap <= eps_mbb ? 1 : 0;
-          __threadfence();
-        }
+      if (!grid_sync(bar, bk)) return;
+      double vmin, vmax;
+      reduce_pair(partBR0, partBR1, NB, vmin, vmax);
+      gap = (vmax - vmin) / bb * 1000.0;
+      gap_checks += 1;
+      phase_mark(clk, 10);
+      if (!isfinite(gap)) {
+        status = EGT_ERR_NUMERIC;
+        break;
       }
+      reached = eps_mbb > 0 && gap <= eps_mbb ? 1 : 0;
     }
-    if (!grid_sync(bar)) return;
-    if (vload(&ctl->reached) || vload(&ctl->t) >= max_t) return;
+    if (reached || t >= max_t) break;
+  }
+
+  if (writer) {
+    ctl->t = t;
+    ctl->cur = cur;
+    ctl->mu[0] = mu0;
+    ctl->mu[1] = mu1;
+    ctl->tau = tau_as;
+    ctl->gap_mbb = gap;
+    ctl->reached = reached;
+    ctl->done_iters = done;
+    ctl->backoffs = backoffs_total;
+    ctl->products = products;
+    ctl->gap_checks = gap_checks;
+    ctl->last_player = last_player;
+    ctl->last_backoffs = last_backoffs;
+    ctl->last_tau = last_tau;
+    ctl->last_egv = last_egv;
+    if (status != 0) atomicCAS(&ctl->status, 0, status);
+#pragma unroll
+    for (int k = 0; k < kEnginePhases; ++k) {
+      ctl->phase_ns[k] = clk->ns[k];
+      ctl->phase_n[k] = clk->n[k];
+    }
   }
 }
 
@@ -314,7 +388,8 @@ cudaError_t engine_launch(const DevGame& g, const EngineBufs& b, EngineCtl* ctl,
   const size_t smem = engine_smem_bytes(g);
   DevGame gg = g;
   EngineBufs bb = b;
-  void* args[] = {&gg, &bb, &ctl, &expected, &limit_ns};
+  unsigned long long exp64 = expected;
+  void* args[] = {&gg, &bb, &ctl, &exp64, &limit_ns};
   return cudaLaunchCooperativeKernel((const void*)engine_kernel, dim3(grid), dim3(kItemThreads), args,
                                      smem, st);
 }

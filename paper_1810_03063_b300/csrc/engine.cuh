@@ -7,6 +7,12 @@
 
 namespace egt {
 
+// Phases of an iteration timed by the engine (egt_engine_trace): the Step's
+// three SBR and three product phases, the EGV SBR (with the EGV decision), two
+// slots kept for compatibility (0 now: those barriers are gone), the residual's
+// FP64 products, its FP64 best responses (with the gap decision).
+constexpr int kEnginePhases = 11;
+
 // Control block in device memory, one per game.  The host writes the
 // configuration and the solver state before a launch and reads everything back
 // after it.
@@ -22,8 +28,11 @@ struct EngineCtl {
   int status, reached, retry, done_iters, backoffs, products, gap_checks;
   int last_player, last_backoffs;
   double gap_mbb, egv, last_tau, last_egv;
-  // grid barrier
-  unsigned int bar_count, bar_gen;
+  // grid barrier: monotone arrival counter
+  unsigned long long bar_arrive;
+  // device time per phase (CTA 0, between consecutive barrier exits), ns
+  unsigned long long phase_ns[kEnginePhases];
+  unsigned long long phase_n[kEnginePhases];
 };
 
 struct EngineBufs {

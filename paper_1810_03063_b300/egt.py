@@ -98,6 +98,7 @@ _SIGS = {
     "egt_state_gap": [_vp, C.POINTER(_f64), _vp],
     "egt_gap_noalloc": [_vp, _vp, _vp, C.POINTER(_f64), _vp],
     "egt_iterate": [_vp, C.POINTER(SolveOpts), _i32, C.POINTER(SolveReport), _vp],
+    "egt_engine_trace": [_vp, _i32, _vp, _vp],
     "egt_profile": [_vp, _i32],
     "egt_profile_read": [_vp, _vp, _vp],
 }
@@ -305,6 +306,16 @@ class Game:
     def state_set(self, x, y, mu, stream=None):
         m = (C.c_double * 2)(*mu)
         _check(lib.egt_state_set(self._h, _ptr(x), _ptr(y), C.cast(m, C.c_void_p), _stream(stream)))
+
+    ENGINE_PHASES = ("sbr_hat", "grad_1", "sbr_other", "grad_2", "sbr_tilde", "grad_3",
+                     "sbr_egv", "egv_decision", "accept", "gap_grad_f64", "gap_br_f64")
+
+    def engine_trace(self, reset=True):
+        us = np.zeros(len(self.ENGINE_PHASES), np.float64)
+        n = np.zeros(len(self.ENGINE_PHASES), np.int64)
+        _check(lib.egt_engine_trace(self._h, int(reset), us.ctypes.data, n.ctypes.data))
+        return {k: dict(us=float(us[i]), n=int(n[i]), avg_us=float(us[i] / n[i]) if n[i] else 0.0)
+                for i, k in enumerate(self.ENGINE_PHASES)}
 
     def profile(self, enable):
         _check(lib.egt_profile(self._h, int(enable)))
