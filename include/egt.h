@@ -17,7 +17,7 @@
  * - "device" pointers are CUDA global memory on the game's device; "host"
  *   pointers are ordinary CPU memory.
  * - Strategy and gradient vectors are laid out [seq][hand] with a leading
- *   dimension ld (egt_dims.ld, a multiple of 32 >= H): element (s, h) is at
+ *   dimension ld (egt_dims.ld, a multiple of 32 >= H, at most 1536): element (s, h) is at
  *   s * ld + h.  Hands are in ascending strength order (ties by input index),
  *   see egt_hand_order.  Columns h >= H are ignored on input and written as
  *   0 on output.  Vector base pointers must be 16-byte aligned.

@@ -52,7 +52,7 @@ struct DeviceGuard {
   }
 };
 
-constexpr int kMaxLd = 2048;
+constexpr int kMaxLd = 1536;   // 6 hands per thread of a 256-thread half in the product kernels
 constexpr double kTauMin = 1.0 / (1u << 30);
 
 }  // namespace
@@ -849,7 +849,7 @@ egt_status egt_create_game(const egt_game_desc* desc, int32_t device, void* stre
   G->pot = desc->pot;
   if (G->ld > kMaxLd) {
     delete G;
-    return fail(EGT_ERR_INVALID_ARG, "n_hands above 2048");
+    return fail(EGT_ERR_INVALID_ARG, "n_hands above 1536");
   }
   std::string err = compile_betting(desc->pot, desc->stack, desc->bet_fracs, desc->n_bets,
                                     desc->allin != 0, desc->raise_cap, G->comp);

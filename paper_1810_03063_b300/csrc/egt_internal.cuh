@@ -76,6 +76,10 @@ void launch_grad(const DevGame& g, int player, const TIn* in, T* out, cudaStream
 
 size_t grad_smem_bytes(const DevGame& g, bool f64);
 
+// One product with both results: out32 (FP32) and out64 (FP64) from the same exact sums.
+void launch_grad_dual(const DevGame& g, int player, const float* in, float* out32, double* out64,
+                      cudaStream_t st);
+
 // SBR of player p on g (sign: +1 player 0, -1 player 1), temperature mu * beta_j.
 // g may be NULL (treated as 0: the uniform behavioural strategy).  If out is
 // non-NULL writes q, or (1 - tau) old + tau q when old is non-NULL.  If

@@ -150,12 +150,24 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int pl
   }
 }
 
-// One product phase: every output sequence of `player`.
+// One product phase: every output sequence of `player`; out64 (FP64 copy for the
+// residual) may be NULL.
 __device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, int player, const float* in,
-                                         float* out, unsigned char* sm) {
+                                         float* out, double* out64, unsigned char* sm) {
   const int S = player ? g.tpx[1].S : g.tpx[0].S;
   for (int item = blockIdx.x; item < S; item += gridDim.x)
-    grad_item<float, float>(g, tb.grad, player, item, in, out, sm);
+    grad_item<float>(g, tb.grad, player, item, in, out, out64, sm);
+}
+
+// The residual's two FP64 best responses as items [first, first + 2 NB) of a phase
+// (br item i < NB: player 0, else player 1), partials to partBR0 / partBR1.
+__device__ __forceinline__ void run_br_items(const DevGame& g, const Tabs& tb, int item, int NB,
+                                             const EngineBufs& b, double* partBR0, double* partBR1,
+                                             unsigned char* sm) {
+  if (item < NB)
+    br64_item(g, tb.tpx[0], item, b.g64[0], 1.0, partBR0 + item, reinterpret_cast<double*>(sm));
+  else
+    br64_item(g, tb.tpx[1], item - NB, b.g64[1], -1.0, partBR1 + item - NB, reinterpret_cast<double*>(sm));
 }
 
 // Two fixed-order sums of per-item partials, computed by warp 0 of every CTA
@@ -249,31 +261,56 @@ __global__ void __launch_bounds__(kItemThreads, 1)
     float* t_me = xs ? b.tx : b.ty;
     float* t_ot = xs ? b.ty : b.tx;
     const double mu_me = xs ? mu0 : mu1, mu_ot = xs ? mu1 : mu0;
+    // the residual of the new point is due: the Step's products of y_+ and x_+ also
+    // write their FP64 copies, and the best responses run with the EGV phase
+    const bool gap_due = (t + 1) % gap_every == 0 || t + 1 >= max_t;
+    double* g64_me = gap_due ? (xs ? b.g64[0] : b.g64[1]) : nullptr;
+    double* g64_ot = gap_due ? (xs ? b.g64[1] : b.g64[0]) : nullptr;
     for (;;) {
       // v_hat = (1 - tau) v + tau v_mu(other)
       run_sbr(g, tb, me, g_me, mu_me, v_me, tau, t_me, nullptr, sm);
       if (!grid_sync(bar, bk)) return;
       phase_mark(clk, 0);
-      run_grad(g, tb, ot, t_me, t_ot, sm);                  // the other's loss gradient at v_hat
+      run_grad(g, tb, ot, t_me, t_ot, nullptr, sm);         // the other's loss gradient at v_hat
       if (!grid_sync(bar, bk)) return;
       phase_mark(clk, 1);
       // other_+ = (1 - tau) other + tau other_mu(v_hat)
       run_sbr(g, tb, ot, t_ot, mu_ot, v_ot, tau, v_ot_n, nullptr, sm);
       if (!grid_sync(bar, bk)) return;
       phase_mark(clk, 2);
-      run_grad(g, tb, me, v_ot_n, g_me_n, sm);              // my loss gradient at other_+
+      run_grad(g, tb, me, v_ot_n, g_me_n, g64_me, sm);      // my loss gradient at other_+
       if (!grid_sync(bar, bk)) return;
       phase_mark(clk, 3);
       // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part
       run_sbr(g, tb, me, g_me_n, (1 - tau) * mu_me, v_me, tau, v_me_n, partA, sm);
       if (!grid_sync(bar, bk)) return;
       phase_mark(clk, 4);
-      run_grad(g, tb, ot, v_me_n, g_ot_n, sm);              // the other's loss gradient at v_+
+      run_grad(g, tb, ot, v_me_n, g_ot_n, g64_ot, sm);      // the other's loss gradient at v_+
       if (!grid_sync(bar, bk)) return;
       phase_mark(clk, 5);
       products += 3;
       if (!check) break;
-      run_sbr(g, tb, ot, g_ot_n, mu_ot, nullptr, 0.0, nullptr, partB, sm);   // the other's EGV part
+      {
+        // the other's EGV part (items [0, NB)) and, when due, the residual's best
+        // responses (items [NB, 3 NB)) in one phase
+        const TpxTab tp = pick(tb, ot);
+        const int n_items = gap_due ? 3 * NB : NB;
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+          if (item < NB) {
+            SbrItemArgs a;
+            a.g = g_ot_n;
+            a.sign = ot == 0 ? 1.f : -1.f;
+            a.mu = mu_ot;
+            a.old = nullptr;
+            a.tau = 0.f;
+            a.out = nullptr;
+            a.value_partial = partB + item;
+            sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
+          } else {
+            run_br_items(g, tb, item - NB, NB, b, partBR0, partBR1, sm);
+          }
+        }
+      }
       if (!grid_sync(bar, bk)) return;
       phase_mark(clk, 6);
       double a, c;
@@ -316,23 +353,14 @@ __global__ void __launch_bounds__(kItemThreads, 1)
     last_backoffs = backoffs;
     last_tau = tau;
     last_egv = egv;
-    if (t % gap_every == 0 || t >= max_t) {
-      // eps_sad of the new iterates: FP64 products of both players, then both best responses
-      const int S0 = g.tpx[0].S, S1 = g.tpx[1].S;
-      for (int item = blockIdx.x; item < S0 + S1; item += gridDim.x) {
-        if (item < S0) grad_item<float, double>(g, tb.grad, 0, item, yn, b.g64[0], sm);
-        else grad_item<float, double>(g, tb.grad, 1, item - S0, xn, b.g64[1], sm);
+    if (gap_due) {
+      // eps_sad of the new iterates from the FP64 products of the Step; the best
+      // responses already ran with the EGV phase under EGT/as, otherwise here
+      if (!check) {
+        for (int item = blockIdx.x; item < 2 * NB; item += gridDim.x)
+          run_br_items(g, tb, item, NB, b, partBR0, partBR1, sm);
+        if (!grid_sync(bar, bk)) return;
       }
-      if (!grid_sync(bar, bk)) return;
-      phase_mark(clk, 9);
-      for (int item = blockIdx.x; item < 2 * NB; item += gridDim.x) {
-        if (item < NB)
-          br64_item(g, tb.tpx[0], item, b.g64[0], 1.0, partBR0 + item, reinterpret_cast<double*>(sm));
-        else
-          br64_item(g, tb.tpx[1], item - NB, b.g64[1], -1.0, partBR1 + item - NB,
-                    reinterpret_cast<double*>(sm));
-      }
-      if (!grid_sync(bar, bk)) return;
       double vmin, vmax;
       reduce_pair(partBR0, partBR1, NB, vmin, vmax);
       gap = (vmax - vmin) / bb * 1000.0;
@@ -375,7 +403,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
 }  // namespace
 
 size_t engine_smem_bytes(const DevGame& g) {
-  size_t m = std::max(grad_item_smem(g, true), grad_item_smem(g, false));
+  size_t m = grad_item_smem(g);
   for (int p = 0; p < 2; ++p) {
     m = std::max(m, sbr_item_smem(g, p));
     m = std::max(m, br_item_smem(g, p));

@@ -1,4 +1,4 @@
-// Gradient product body shared by the standalone kernel and the solver engine.
+// Gradient product body shared by the standalone kernels and the solver engine.
 //
 // Sec. 3: every EGT step needs grad f = A y and grad phi = A^T x.  For a
 // terminal b and an output hand h (Sec. 7 payoffs, chance r1 r2 / Z):
@@ -14,15 +14,19 @@
 //
 // One CTA (512 threads) per output sequence; its two halves take the
 // sequence's terminals in pairs (every sequence of the river games has one or
-// two).  Sums are exact: each w is converted once to fixed point (int64 limbs,
-// a per-terminal power-of-two scale from max |w| leaving 2^59 headroom), so
-// prefix sums, per-card corrections and the tie-aware differences are integer
-// operations in any order -- deterministic, and on the full-rate integer pipes.
-// FP32 path: one limb (resolution max|w| 2^-48); FP64 path: two limbs (the
-// second holds the next 40 bits of the first's fraction).  The per-hand result
-// is rounded once to T, scaled by the terminal's coefficient and accumulated
-// over terminals in float-float (FP32) or double (FP64).
+// two).  All sums are exact: each w is put in fixed point with two int64 limbs
+// (integer part at a per-terminal power-of-two scale leaving 2^59 headroom,
+// then 40 more fraction bits), so prefix sums, per-card corrections and the
+// tie-aware differences are integer operations, deterministic in any order and
+// on the full-rate integer pipes.  For FP32 inputs w = r (FP64 range) x y is
+// formed exactly as the 77-bit product of the two mantissas, with integer
+// operations only (B300's FP64 pipe is a small fraction of the integer rate).
+// From the same exact sums the CTA can emit an FP32 result (float-float
+// accumulation over terminals, the path of every EGT step) and an FP64 result
+// (the stopping residual); asking for the FP64 one does not change the FP32 one.
 #pragma once
+#include <climits>
+
 #include "egt_internal.cuh"
 
 namespace egt {
@@ -51,47 +55,24 @@ __device__ __forceinline__ FF ff_prod(float c, float v) {
   return {p, __fmaf_rn(c, v, -p)};
 }
 
-template <int NL>
+// fixed point: v0 = integer part, v1 = the next 40 fraction bits (both carry the sign)
 struct Fx {
-  long long v[NL];
+  long long v0, v1;
 };
 
-template <int NL>
-__device__ __forceinline__ Fx<NL> fx_zero() {
-  Fx<NL> r;
-#pragma unroll
-  for (int i = 0; i < NL; ++i) r.v[i] = 0;
-  return r;
+__device__ __forceinline__ Fx fx_zero() { return {0, 0}; }
+__device__ __forceinline__ Fx fx_add(Fx a, Fx b) { return {a.v0 + b.v0, a.v1 + b.v1}; }
+__device__ __forceinline__ Fx fx_sub(Fx a, Fx b) { return {a.v0 - b.v0, a.v1 - b.v1}; }
+__device__ __forceinline__ Fx fx_shfl_up(Fx a, int d) {
+  return {__shfl_up_sync(0xffffffffu, a.v0, d), __shfl_up_sync(0xffffffffu, a.v1, d)};
 }
-template <int NL>
-__device__ __forceinline__ Fx<NL> fx_add(Fx<NL> a, Fx<NL> b) {
-#pragma unroll
-  for (int i = 0; i < NL; ++i) a.v[i] += b.v[i];
-  return a;
+__device__ __forceinline__ Fx fx_shfl(Fx a, int src) {
+  return {__shfl_sync(0xffffffffu, a.v0, src), __shfl_sync(0xffffffffu, a.v1, src)};
 }
-template <int NL>
-__device__ __forceinline__ Fx<NL> fx_sub(Fx<NL> a, Fx<NL> b) {
-#pragma unroll
-  for (int i = 0; i < NL; ++i) a.v[i] -= b.v[i];
-  return a;
-}
-template <int NL>
-__device__ __forceinline__ Fx<NL> fx_shfl_up(Fx<NL> a, int d) {
-#pragma unroll
-  for (int i = 0; i < NL; ++i) a.v[i] = __shfl_up_sync(0xffffffffu, a.v[i], d);
-  return a;
-}
-template <int NL>
-__device__ __forceinline__ Fx<NL> fx_shfl(Fx<NL> a, int src) {
-#pragma unroll
-  for (int i = 0; i < NL; ++i) a.v[i] = __shfl_sync(0xffffffffu, a.v[i], src);
-  return a;
-}
-template <int NL>
-__device__ __forceinline__ Fx<NL> fx_scan(Fx<NL> v, int lane) {
+__device__ __forceinline__ Fx fx_scan(Fx v, int lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    Fx<NL> o = fx_shfl_up(v, d);
+    Fx o = fx_shfl_up(v, d);
     if (lane >= d) v = fx_add(v, o);
   }
   return v;
@@ -101,18 +82,6 @@ __device__ __forceinline__ Fx<NL> fx_scan(Fx<NL> v, int lane) {
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 __device__ __forceinline__ double pow2d(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
-}
-
-// Conversions to and from fixed point work on the IEEE bit fields with integer
-// operations: B300's FP64 pipe (and 64-bit conversions routed through it) runs
-// at a small fraction of the integer rate.
-
-// round(m 2^sh) for an integer mantissa m (sh < 0: right shift, half rounds up)
-__device__ __forceinline__ long long shift_round(unsigned long long m, int sh) {
-  if (sh >= 0) return (long long)(m << sh);
-  const int r = -sh;
-  if (r > 63) return 0;
-  return (long long)((m >> r) + ((m >> (r - 1)) & 1ull));
 }
 
 // int64 -> float rounded to nearest even (leading-zero count and shifts)
@@ -137,118 +106,103 @@ __device__ __forceinline__ float i64_to_f32(long long v) {
   return v < 0 ? -f : f;
 }
 
-template <typename T>
-struct Conv;
+// floor(P / 2^k) of the 128-bit P = hi:lo, low 64 bits
+__device__ __forceinline__ unsigned long long shr128(unsigned long long hi, unsigned long long lo, int k) {
+  if (k <= 0) return lo;
+  if (k >= 128) return 0;
+  if (k >= 64) return hi >> (k - 64);
+  return (lo >> k) | (hi << (64 - k));
+}
 
-template <>
-struct Conv<float> {
-  static constexpr int NL = 1;
-  // round(w 2^e): w = m 2^(E - 150) with a 24-bit integer mantissa m
-  static __device__ __forceinline__ Fx<1> to_fx(float w, int e) {
-    const unsigned bits = __float_as_uint(w);
-    int E = (bits >> 23) & 0xff;
-    unsigned m = bits & 0x7fffffu;
-    Fx<1> r;
-    r.v[0] = 0;
-    if (E == 0 && m == 0) return r;
-    if (E == 0) E = 1;
-    else m |= 0x800000u;
-    const long long a = shift_round(m, E - 150 + e);
-    r.v[0] = (bits >> 31) ? -a : a;
-    return r;
-  }
-  static __device__ __forceinline__ float from_fx(Fx<1> a, int e) {
-    const int e1 = e >> 1;
-    return i64_to_f32(a.v[0]) * pow2f(-e1) * pow2f(e1 - e);
-  }
-  static __device__ __forceinline__ float absmax(float a, float b) { return fmaxf(a, fabsf(b)); }
-  // scale exponent so that |sum| of up to 2048 terms stays below 2^59
-  static __device__ __forceinline__ int scale(float M) {
-    return M > 0.f ? 48 - (ilogbf(M) + 1) : 0;
-  }
+// |w| = P 2^E with P = hi:lo an exact integer, sign neg, lg = floor(log2 |w|)
+// (INT_MIN when w = 0).
+struct WBits {
+  unsigned long long hi, lo;
+  int E, lg, neg;
 };
 
-template <>
-struct Conv<double> {
-  static constexpr int NL = 2;
-  // |w| 2^e split as a + b 2^-40 (a the integer part, b the next 40 bits of the
-  // fraction, both truncated), w = m 2^(E - 1075) with a 53-bit integer mantissa m
-  static __device__ __forceinline__ Fx<2> to_fx(double w, int e) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(w);
-    int E = (int)((bits >> 52) & 0x7ffull);
-    unsigned long long m = bits & ((1ull << 52) - 1);
-    Fx<2> r;
-    r.v[0] = r.v[1] = 0;
-    if (E == 0 && m == 0) return r;
-    if (E == 0) E = 1;
-    else m |= (1ull << 52);
-    const int sh = E - 1075 + e;
-    long long a = 0, b = 0;
-    if (sh >= 0) {
-      a = (long long)(m << sh);
-    } else {
-      const int k = -sh;                       // fractional bits of m 2^sh
-      if (k < 64) {
-        a = (long long)(m >> k);
-        const unsigned long long frac = m & ((1ull << k) - 1);
-        b = k <= 40 ? (long long)(frac << (40 - k)) : (k - 40 < 64 ? (long long)(frac >> (k - 40)) : 0);
-      } else if (k - 40 < 64) {
-        b = (long long)(m >> (k - 40));
-      }
-    }
-    if (bits >> 63) {
-      a = -a;
-      b = -b;
-    }
-    r.v[0] = a;
-    r.v[1] = b;
-    return r;
+// w = r * y exactly: 53-bit x 24-bit mantissa product
+__device__ __forceinline__ WBits wprod(double r, float y) {
+  const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
+  const unsigned yb = __float_as_uint(y);
+  int er = (int)((rb >> 52) & 0x7ffull), ey = (int)((yb >> 23) & 0xffu);
+  unsigned long long mr = rb & ((1ull << 52) - 1), my = yb & 0x7fffffu;
+  WBits w;
+  w.neg = (int)((rb >> 63) ^ (yb >> 31));
+  if ((er == 0 && mr == 0) || (ey == 0 && my == 0)) {
+    w.hi = w.lo = 0;
+    w.E = 0;
+    w.lg = INT_MIN;
+    return w;
   }
-  static __device__ __forceinline__ double from_fx(Fx<2> a, int e) {
-    const double s = (double)a.v[0] + (double)a.v[1] * (1.0 / 1099511627776.0);
-    const int e1 = e >> 1;
-    return s * pow2d(-e1) * pow2d(e1 - e);
+  if (er == 0) er = 1;
+  else mr |= 1ull << 52;
+  if (ey == 0) ey = 1;
+  else my |= 1ull << 23;
+  w.lo = mr * my;
+  w.hi = __umul64hi(mr, my);
+  w.E = (er - 1075) + (ey - 150);
+  const int nb = w.hi ? 128 - __clzll(w.hi) : 64 - __clzll(w.lo);
+  w.lg = w.E + nb - 1;
+  return w;
+}
+
+// w = r * y for an FP64 y: rounded once in FP64, then exact from there
+__device__ __forceinline__ WBits wprod(double r, double y) {
+  const double w = r * y;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+  int e = (int)((b >> 52) & 0x7ffull);
+  unsigned long long m = b & ((1ull << 52) - 1);
+  WBits x;
+  x.neg = (int)(b >> 63);
+  if (e == 0 && m == 0) {
+    x.hi = x.lo = 0;
+    x.E = 0;
+    x.lg = INT_MIN;
+    return x;
   }
-  static __device__ __forceinline__ double absmax(double a, double b) { return fmax(a, fabs(b)); }
-  static __device__ __forceinline__ int scale(double M) { return M > 0.0 ? 48 - (ilogb(M) + 1) : 0; }
-};
+  if (e == 0) e = 1;
+  else m |= 1ull << 52;
+  x.hi = 0;
+  x.lo = m;
+  x.E = e - 1075;
+  x.lg = x.E + (64 - __clzll(m)) - 1;
+  return x;
+}
 
-template <typename T>
-__device__ __forceinline__ const T* ranges(const DevGame& g, int p);
-template <>
-__device__ __forceinline__ const float* ranges<float>(const DevGame& g, int p) { return g.r[p]; }
-template <>
-__device__ __forceinline__ const double* ranges<double>(const DevGame& g, int p) { return g.r64[p]; }
-template <typename T>
-__device__ __forceinline__ const T* ranges_z(const DevGame& g, int p);
-template <>
-__device__ __forceinline__ const float* ranges_z<float>(const DevGame& g, int p) { return g.rz[p]; }
-template <>
-__device__ __forceinline__ const double* ranges_z<double>(const DevGame& g, int p) { return g.rz64[p]; }
-template <typename T>
-__device__ __forceinline__ T term_coef(const DevTerms& t, int e);
-template <>
-__device__ __forceinline__ float term_coef<float>(const DevTerms& t, int e) { return t.coef[e]; }
-template <>
-__device__ __forceinline__ double term_coef<double>(const DevTerms& t, int e) { return t.coef64[e]; }
+// |w| 2^ex as integer part + 40 truncated fraction bits, signed
+__device__ __forceinline__ Fx to_fx(const WBits& w, int ex) {
+  if (w.lg == INT_MIN) return fx_zero();
+  const int s = w.E + ex;
+  unsigned long long a, b;
+  if (s >= 0) {
+    a = w.lo << s;          // |w| 2^ex < 2^48 keeps this in range
+    b = 0;
+  } else {
+    const int k = -s;       // fraction bits of P 2^s
+    a = shr128(w.hi, w.lo, k);
+    b = k >= 40 ? (shr128(w.hi, w.lo, k - 40) & ((1ull << 40) - 1))
+                : ((w.lo & ((1ull << k) - 1)) << (40 - k));
+  }
+  const long long sa = (long long)a, sb = (long long)b;
+  return w.neg ? Fx{-sa, -sb} : Fx{sa, sb};
+}
 
-// accumulator of one hand over terminals
-template <typename T>
-struct Acc;
-template <>
-struct Acc<float> {
-  FF a;
-  __device__ __forceinline__ void zero() { a = {0.f, 0.f}; }
-  __device__ __forceinline__ void add(float c, float v) { a = ff_add(a, ff_prod(c, v)); }
-  __device__ __forceinline__ float value() const { return __fadd_rn(a.hi, a.lo); }
-};
-template <>
-struct Acc<double> {
-  double a;
-  __device__ __forceinline__ void zero() { a = 0.0; }
-  __device__ __forceinline__ void add(double c, double v) { a += c * v; }
-  __device__ __forceinline__ double value() const { return a; }
-};
+// scale so that |w| 2^ex < 2^48 for the largest |w| (sums of 2048 terms < 2^59)
+__device__ __forceinline__ int scale_of(int maxlg) { return maxlg == INT_MIN ? 0 : 47 - maxlg; }
+
+// FP32 value of a fixed-point sum (fraction rounded into the integer part)
+__device__ __forceinline__ float fx_to_f32(Fx a, int ex) {
+  const long long v = a.v0 + ((a.v1 + (1ll << 39)) >> 40);
+  const int e1 = ex >> 1;
+  return i64_to_f32(v) * pow2f(-e1) * pow2f(e1 - ex);
+}
+
+__device__ __forceinline__ double fx_to_f64(Fx a, int ex) {
+  const double s = (double)a.v0 + (double)a.v1 * (1.0 / 1099511627776.0);
+  const int e1 = ex >> 1;
+  return s * pow2d(-e1) * pow2d(e1 - ex);
+}
 
 __device__ __forceinline__ void half_sync(int half) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(kHalfThreads) : "memory");
@@ -256,27 +210,25 @@ __device__ __forceinline__ void half_sync(int half) {
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-// shared memory of one half: w, F (w in fixed point), P, PC, warp maxima, warp totals
-template <typename T>
+// shared memory of one half: input cache / combine area, F (w in fixed point), P, PC,
+// warp maxima, warp totals
 __host__ __device__ inline size_t half_bytes(int ld, int n_slots, int lmax) {
-  constexpr int NL = sizeof(T) == 4 ? 1 : 2;
-  const size_t fx = sizeof(long long) * NL;
-  size_t b = align16((size_t)ld * sizeof(T));
+  const size_t fx = sizeof(Fx);
+  size_t b = align16((size_t)ld * 16);
   b += align16((size_t)ld * fx);
   b += align16((size_t)(ld + 1) * fx);
   b += align16((size_t)n_slots * (lmax + 1) * fx);
-  b += 8 * sizeof(T) + 8 * fx + 16;
+  b += 8 * sizeof(int) + 8 * fx + 16;
   return align16(b);
 }
 
-constexpr int kMaxHandsPerThread = 8;   // ld <= 2048 with 256 threads per half
+constexpr int kMaxHandsPerThread = 6;   // ld <= 1536 with 256 threads per half
 
 }  // namespace gradimpl
 
 // Shared memory of one gradient CTA (without the staged tables).
-inline size_t grad_item_smem(const DevGame& g, bool f64) {
-  return 2 * (f64 ? gradimpl::half_bytes<double>(g.ld, g.n_slots, g.lmax)
-                  : gradimpl::half_bytes<float>(g.ld, g.n_slots, g.lmax));
+__host__ __device__ inline size_t grad_item_smem(const DevGame& g) {
+  return 2 * gradimpl::half_bytes(g.ld, g.n_slots, g.lmax);
 }
 
 // Per-game tables the product reads for every terminal, staged once in shared memory.
@@ -284,61 +236,81 @@ struct GradTab {
   const uint4* hinfo;          // [ld] per-hand flat indices (see DevGame::hinfo)
   const int* card_len;         // [n_slots]
   const uint16_t* card_hands;  // [n_slots][lmax]
+  const double* r64[2];        // [ld] normalised ranges of both players
 };
 
 __host__ __device__ inline size_t grad_tab_bytes(const DevGame& g) {
   using gradimpl::align16;
   return align16((size_t)g.ld * sizeof(uint4)) + align16((size_t)g.n_slots * sizeof(int)) +
-         align16((size_t)g.n_slots * g.lmax * sizeof(uint16_t));
+         align16((size_t)g.n_slots * g.lmax * sizeof(uint16_t)) + 2 * align16((size_t)g.ld * sizeof(double));
 }
 
 // Copy the tables into dst (all threads of the CTA; the caller synchronises before use).
 __device__ inline GradTab stage_grad_tab(const DevGame& g, unsigned char* dst) {
   using gradimpl::align16;
   uint4* hi = reinterpret_cast<uint4*>(dst);
-  int* cl = reinterpret_cast<int*>(dst + align16((size_t)g.ld * sizeof(uint4)));
-  uint16_t* ch = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(cl) +
-                                             align16((size_t)g.n_slots * sizeof(int)));
-  for (int i = threadIdx.x; i < g.ld; i += blockDim.x) hi[i] = g.hinfo[i];
+  unsigned char* p = dst + align16((size_t)g.ld * sizeof(uint4));
+  int* cl = reinterpret_cast<int*>(p);
+  p += align16((size_t)g.n_slots * sizeof(int));
+  uint16_t* ch = reinterpret_cast<uint16_t*>(p);
+  p += align16((size_t)g.n_slots * g.lmax * sizeof(uint16_t));
+  double* r0 = reinterpret_cast<double*>(p);
+  double* r1 = r0 + align16((size_t)g.ld * sizeof(double)) / sizeof(double);
+  for (int i = threadIdx.x; i < g.ld; i += blockDim.x) {
+    hi[i] = g.hinfo[i];
+    r0[i] = g.r64[0][i];
+    r1[i] = g.r64[1][i];
+  }
   for (int i = threadIdx.x; i < g.n_slots; i += blockDim.x) cl[i] = g.card_len[i];
   for (int i = threadIdx.x; i < g.n_slots * g.lmax; i += blockDim.x) ch[i] = g.card_hands[i];
-  return {hi, cl, ch};
+  GradTab t;
+  t.hinfo = hi;
+  t.card_len = cl;
+  t.card_hands = ch;
+  t.r64[0] = r0;
+  t.r64[1] = r1;
+  return t;
 }
 
-// Output column s of player `player` (out[s][*] = (A in)[s] for player 0, (A^T in)[s]
-// for player 1), computed by one CTA of kItemThreads threads.  `in` is read through L2
-// (it may have been written earlier in the same launch by other CTAs).
-template <typename TIn, typename T>
+// Output column s of player `player`: (A in)[s] for player 0, (A^T in)[s] for player 1,
+// written to out32 (FP32) and / or out64 (FP64), either may be NULL; computed by one CTA
+// of kItemThreads threads.  `in` is read through L2 (it may have been written earlier in
+// the same launch by other CTAs).
+template <typename TIn>
 __device__ inline void grad_item(const DevGame& g, const GradTab& tb, int player, int s,
-                                 const TIn* __restrict__ in, T* __restrict__ out,
-                                 unsigned char* smem) {
+                                 const TIn* __restrict__ in, float* __restrict__ out32,
+                                 double* __restrict__ out64, unsigned char* smem) {
   using namespace gradimpl;
-  using C = Conv<T>;
-  constexpr int NL = C::NL;
   const int ld = g.ld, H = g.H, opp = 1 - player;
   const int tid = threadIdx.x, half = tid / kHalfThreads, th = tid % kHalfThreads;
   const int lane = tid & 31, hw = th >> 5;
   constexpr int kHalfWarps = kHalfThreads / 32;
   const int lstride = g.lmax + 1;
+  const size_t hb = half_bytes(ld, g.n_slots, g.lmax);
 
-  unsigned char* hs = smem + half * half_bytes<T>(ld, g.n_slots, g.lmax);
-  T* w = reinterpret_cast<T*>(hs);
-  Fx<NL>* F = reinterpret_cast<Fx<NL>*>(hs + align16((size_t)ld * sizeof(T)));
-  Fx<NL>* P = reinterpret_cast<Fx<NL>*>(reinterpret_cast<unsigned char*>(F) +
-                                        align16((size_t)ld * sizeof(Fx<NL>)));
-  Fx<NL>* PC = reinterpret_cast<Fx<NL>*>(reinterpret_cast<unsigned char*>(P) +
-                                         align16((size_t)(ld + 1) * sizeof(Fx<NL>)));
-  T* wmax = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(PC) +
-                                 align16((size_t)g.n_slots * lstride * sizeof(Fx<NL>)));
-  Fx<NL>* wtot = reinterpret_cast<Fx<NL>*>(reinterpret_cast<unsigned char*>(wmax) + 8 * sizeof(T));
+  unsigned char* hs = smem + half * hb;
+  TIn* cache = reinterpret_cast<TIn*>(hs);                                 // [ld] input column
+  Fx* F = reinterpret_cast<Fx*>(hs + align16((size_t)ld * 16));
+  Fx* P = F + ld;                                                          // [ld + 1]
+  Fx* PC = reinterpret_cast<Fx*>(reinterpret_cast<unsigned char*>(P) + align16((size_t)(ld + 1) * sizeof(Fx)));
+  int* wmax = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(PC) +
+                                     align16((size_t)g.n_slots * lstride * sizeof(Fx)));
+  Fx* wtot = reinterpret_cast<Fx*>(wmax + 8);
 
-  const DevTerms tm = g.terms[player];
+  // (selects instead of runtime indices into struct arrays, which would go to local memory)
+  const DevTerms tm = player ? g.terms[1] : g.terms[0];
   const int e0 = tm.ptr[s], e1 = tm.ptr[s + 1];
-  const T* __restrict__ r_opp = ranges<T>(g, opp);
+  const double* __restrict__ r_opp = opp ? tb.r64[1] : tb.r64[0];
+  const float* __restrict__ rz = player ? g.rz[1] : g.rz[0];
+  const double* __restrict__ rz64 = player ? g.rz64[1] : g.rz64[0];
 
-  Acc<T> acc[kMaxHandsPerThread];
+  FF acc32[kMaxHandsPerThread];
+  double acc64[kMaxHandsPerThread];
 #pragma unroll
-  for (int k = 0; k < kMaxHandsPerThread; ++k) acc[k].zero();
+  for (int k = 0; k < kMaxHandsPerThread; ++k) {
+    acc32[k] = {0.f, 0.f};
+    acc64[k] = 0.0;
+  }
 
   const int K = (ld + kHalfThreads - 1) / kHalfThreads;   // raking chunk
   const int k0 = min(th * K, ld), k1 = min(k0 + K, ld);
@@ -348,33 +320,36 @@ __device__ inline void grad_item(const DevGame& g, const GradTab& tb, int player
     if (e >= e1) continue;                                   // uniform within a half
     const int os = tm.opp_seq[e];
     const int kind = tm.kind[e];
-    const T coef = term_coef<T>(tm, e);
+    const float coef32 = tm.coef[e];
+    const double coef64 = tm.coef64[e];
     const TIn* col = in + (size_t)os * ld;
 
-    T m = T(0);
+    // pass 1: input cached, largest exponent of |w|
+    int mlg = INT_MIN;
     for (int h = th; h < ld; h += kHalfThreads) {
-      const T wv = h < H ? r_opp[h] * (T)__ldcg(col + h) : T(0);
-      w[h] = wv;
-      m = C::absmax(m, wv);
+      const TIn y = h < H ? __ldcg(col + h) : TIn(0);
+      cache[h] = y;
+      mlg = max(mlg, wprod(r_opp[h], y).lg);
     }
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) m = C::absmax(m, __shfl_xor_sync(0xffffffffu, m, d));
-    if (lane == 0) wmax[hw] = m;
+    for (int d = 16; d > 0; d >>= 1) mlg = max(mlg, __shfl_xor_sync(0xffffffffu, mlg, d));
+    if (lane == 0) wmax[hw] = mlg;
     half_sync(half);
-    T M = T(0);
+    int M = INT_MIN;
 #pragma unroll
-    for (int q = 0; q < kHalfWarps; ++q) M = C::absmax(M, wmax[q]);
-    const int ex = C::scale(M);
-    for (int h = th; h < ld; h += kHalfThreads) F[h] = C::to_fx(w[h], ex);
+    for (int q = 0; q < kHalfWarps; ++q) M = max(M, wmax[q]);
+    const int ex = scale_of(M);
+    // pass 2: exact fixed point
+    for (int h = th; h < ld; h += kHalfThreads) F[h] = to_fx(wprod(r_opp[h], cache[h]), ex);
     half_sync(half);
 
     // exclusive prefix over ascending strength: P[i] = sum_{k < i} w[k], P[ld] = total
-    Fx<NL> loc = fx_zero<NL>();
+    Fx loc = fx_zero();
     for (int i = k0; i < k1; ++i) loc = fx_add(loc, F[i]);
-    const Fx<NL> inc = fx_scan(loc, lane);
+    const Fx inc = fx_scan(loc, lane);
     if (lane == 31) wtot[hw] = inc;
-    Fx<NL> run = fx_shfl_up(inc, 1);
-    if (lane == 0) run = fx_zero<NL>();
+    Fx run = fx_shfl_up(inc, 1);
+    if (lane == 0) run = fx_zero();
     half_sync(half);
     for (int q = 0; q < hw; ++q) run = fx_add(run, wtot[q]);
     for (int i = k0; i < k1; ++i) {
@@ -387,61 +362,65 @@ __device__ inline void grad_item(const DevGame& g, const GradTab& tb, int player
     for (int c = hw; c < g.n_slots; c += kHalfWarps) {
       const int len = tb.card_len[c];
       const uint16_t* lst = tb.card_hands + (size_t)c * g.lmax;
-      const Fx<NL> v0 = lane < len ? F[lst[lane]] : fx_zero<NL>();
-      const Fx<NL> v1 = lane + 32 < len ? F[lst[lane + 32]] : fx_zero<NL>();
-      const Fx<NL> a0 = fx_scan(v0, lane);
-      const Fx<NL> t0 = fx_shfl(a0, 31);
-      const Fx<NL> a1 = fx_add(fx_scan(v1, lane), t0);
-      Fx<NL>* pc = PC + (size_t)c * lstride;
-      if (lane == 0) pc[0] = fx_zero<NL>();
+      const Fx v0 = lane < len ? F[lst[lane]] : fx_zero();
+      const Fx v1 = lane + 32 < len ? F[lst[lane + 32]] : fx_zero();
+      const Fx a0 = fx_scan(v0, lane);
+      const Fx a1 = fx_add(fx_scan(v1, lane), fx_shfl(a0, 31));
+      Fx* pc = PC + (size_t)c * lstride;
+      if (lane == 0) pc[0] = fx_zero();
       if (lane < len) pc[lane + 1] = a0;
       if (lane + 32 < len) pc[lane + 33] = a1;
     }
     half_sync(half);
 
-    const Fx<NL> W = P[ld];
+    const Fx W = P[ld];
 #pragma unroll
     for (int k = 0; k < kMaxHandsPerThread; ++k) {
       const int h = th + k * kHalfThreads;
       if (h >= ld) break;
       const uint4 hi = tb.hinfo[h];
-      const Fx<NL> C0 = PC[hi.z & 0xffffu];
-      const Fx<NL> C1 = PC[hi.w >> 16];
-      Fx<NL> val;
+      const Fx C0 = PC[hi.z & 0xffffu];
+      const Fx C1 = PC[hi.w >> 16];
+      Fx val;
       if (kind == 0) {
         val = fx_sub(fx_sub(W, C0), C1);
         if (g.hand_size == 2) val = fx_add(val, F[h]);
       } else {
-        const Fx<NL> lt = fx_sub(fx_sub(P[hi.x & 0xffffu], PC[hi.y & 0xffffu]), PC[hi.z >> 16]);
-        const Fx<NL> gt = fx_sub(fx_sub(fx_sub(W, P[hi.x >> 16]), fx_sub(C0, PC[hi.y >> 16])),
-                                 fx_sub(C1, PC[hi.w & 0xffffu]));
+        const Fx lt = fx_sub(fx_sub(P[hi.x & 0xffffu], PC[hi.y & 0xffffu]), PC[hi.z >> 16]);
+        const Fx gt = fx_sub(fx_sub(fx_sub(W, P[hi.x >> 16]), fx_sub(C0, PC[hi.y >> 16])),
+                             fx_sub(C1, PC[hi.w & 0xffffu]));
         val = fx_sub(gt, lt);
       }
-      acc[k].add(coef, C::from_fx(val, ex));
+      if (out32 != nullptr) acc32[k] = ff_add(acc32[k], ff_prod(coef32, fx_to_f32(val, ex)));
+      if (out64 != nullptr) acc64[k] += coef64 * fx_to_f64(val, ex);
     }
-    half_sync(half);   // w / F / P / PC are rewritten by the next terminal of this half
+    half_sync(half);   // the cache / F / P / PC are rewritten by the next terminal of this half
   }
 
-  // combine the halves: half 1 leaves its per-hand sums in its w area
+  // combine the halves: half 1 leaves its per-hand sums in its cache area
   __syncthreads();
-  T* other = reinterpret_cast<T*>(smem + half_bytes<T>(ld, g.n_slots, g.lmax));
+  float* other32 = reinterpret_cast<float*>(smem + hb);
+  double* other64 = reinterpret_cast<double*>(smem + hb + align16((size_t)ld * 4));
   if (half == 1) {
 #pragma unroll
     for (int k = 0; k < kMaxHandsPerThread; ++k) {
       const int h = th + k * kHalfThreads;
       if (h >= ld) break;
-      other[h] = acc[k].value();
+      other32[h] = __fadd_rn(acc32[k].hi, acc32[k].lo);
+      other64[h] = acc64[k];
     }
   }
   __syncthreads();
   if (half == 0) {
-    const T* __restrict__ rz = ranges_z<T>(g, player);
-    T* o = out + (size_t)s * ld;
 #pragma unroll
     for (int k = 0; k < kMaxHandsPerThread; ++k) {
       const int h = th + k * kHalfThreads;
       if (h >= ld) break;
-      o[h] = h < H ? rz[h] * (acc[k].value() + other[h]) : T(0);
+      const bool live = h < H;
+      if (out32 != nullptr)
+        out32[(size_t)s * ld + h] = live ? rz[h] * (__fadd_rn(acc32[k].hi, acc32[k].lo) + other32[h]) : 0.f;
+      if (out64 != nullptr)
+        out64[(size_t)s * ld + h] = live ? rz64[h] * (acc64[k] + other64[h]) : 0.0;
     }
   }
   __syncthreads();   // shared memory is reused by the caller's next item
