@@ -181,7 +181,7 @@ EGT_API egt_status egt_gap(egt_game* game, const float* x, const float* y, doubl
  * counterpart: this is a deployment variant.  It allocates nothing: its FP64
  * product vectors and reduction scratch live in one static device array of
  * 2 MiB that every GPU loading the library holds until exit, so games needing
- * more ((S[0] + S[1]) * ld * 8 bytes plus about 9 KB) are rejected with
+ * more (2 * T * ld * 8 bytes for T terminals, plus about 9 KB) are rejected with
  * INVALID_ARG and a message giving both sizes.  The first call on a device
  * looks up the array's address with that device current: make it before any
  * stream capture.  All calls share the array (each clears what must start at

@@ -69,9 +69,12 @@ struct egt_game {
   DevGame dg{};
   // solver state and scratch (device)
   float* vec = nullptr;          // all float vectors
-  float *x[2], *y[2], *gx[2], *gy[2], *tx, *ty;   // [S0|S1][ld]
+  // iterates x, y [S_p][ld]; products gx, gy in terminal-contribution form [T][ld];
+  // scratch tx [max(S0, T)][ld], ty [max(S1, T)][ld]
+  float *x[2], *y[2], *gx[2], *gy[2], *tx, *ty;
   int cur = 0;                   // index of the current iterate / cached products
-  double* g64[2] = {nullptr, nullptr};   // FP64 products for the gap
+  double* g64[2] = {nullptr, nullptr};   // FP64 products for the gap (contributions)
+  double* pub = nullptr;         // [T][ld] contributions of the public egt_grad / egt_grad_f64
   double* partials = nullptr;    // per-CTA value partials
   unsigned int* counter = nullptr;
   double* vals = nullptr;        // device value slots
@@ -108,6 +111,7 @@ struct egt_game {
 namespace {
 
 size_t vec_elems(const egt_game* G, int p) { return (size_t)G->comp.tpx[p].S * G->ld; }
+size_t contrib_elems(const egt_game* G) { return std::max<size_t>(G->comp.term.size(), 1) * G->ld; }
 
 egt_status check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
@@ -390,6 +394,7 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
     dt.beta = (const double*)put(T.beta.data(), T.J * 8);
     dt.log_n = (const float*)put(th[p].log_n.data(), T.J * 4);
     DevTerms& tm = g.terms[p];
+    tm.n = (int)C.term.size();
     tm.ptr = (const int*)put(tptr[p].data(), tptr[p].size() * 4);
     tm.opp_seq = (const int*)put(topp[p].data(), topp[p].size() * 4);
     tm.kind = (const int*)put(tkind[p].data(), tkind[p].size() * 4);
@@ -405,9 +410,9 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
 }
 
 egt_status alloc_state(egt_game* G) {
-  const size_t n0 = vec_elems(G, 0), n1 = vec_elems(G, 1);
-  // x[2], gy[2]... sized by their player: x, gx, tx are player 0; y, gy, ty are player 1
-  const size_t total = 5 * (n0 + 64) + 5 * (n1 + 64);   // each vector rounded up to 64 floats
+  const size_t n0 = vec_elems(G, 0), n1 = vec_elems(G, 1), nc = contrib_elems(G);
+  const size_t t0 = std::max(n0, nc), t1 = std::max(n1, nc);
+  const size_t total = 2 * n0 + 2 * n1 + 4 * nc + t0 + t1 + 10 * 64;   // each rounded up to 64 floats
   CUDA_TRY(cudaMalloc(&G->vec, total * sizeof(float)));
   CUDA_TRY(cudaMemset(G->vec, 0, total * sizeof(float)));
   float* p = G->vec;
@@ -418,14 +423,15 @@ egt_status alloc_state(egt_game* G) {
   };
   for (int i = 0; i < 2; ++i) {
     G->x[i] = take(n0);
-    G->gx[i] = take(n0);
+    G->gx[i] = take(nc);
     G->y[i] = take(n1);
-    G->gy[i] = take(n1);
+    G->gy[i] = take(nc);
   }
-  G->tx = take(n0);
-  G->ty = take(n1);
-  CUDA_TRY(cudaMalloc(&G->g64[0], n0 * sizeof(double)));
-  CUDA_TRY(cudaMalloc(&G->g64[1], n1 * sizeof(double)));
+  G->tx = take(t0);
+  G->ty = take(t1);
+  CUDA_TRY(cudaMalloc(&G->g64[0], nc * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&G->g64[1], nc * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&G->pub, nc * sizeof(double)));
   CUDA_TRY(cudaMalloc(&G->partials, 1024 * sizeof(double)));
   CUDA_TRY(cudaMalloc(&G->counter, 16 * sizeof(unsigned int)));
   CUDA_TRY(cudaMemset(G->counter, 0, 16 * sizeof(unsigned int)));
@@ -450,6 +456,7 @@ void free_game(egt_game* G) {
   cudaFree(G->vec);
   cudaFree(G->g64[0]);
   cudaFree(G->g64[1]);
+  cudaFree(G->pub);
   cudaFree(G->partials);
   cudaFree(G->counter);
   cudaFree(G->vals);
@@ -529,17 +536,20 @@ egt_status timed(egt_game* G, int kind, cudaStream_t st, const char* what, F&& l
 
 // ---- internal launches (no argument checks) ----
 
+// Player's product of `in` in terminal-contribution form (out [T][ld]).
 egt_status grad32(egt_game* G, int player, const float* in, float* out, cudaStream_t st) {
   G->products++;
   return timed(G, EGT_KERNEL_GRAD_F32, st, "grad kernel",
-               [&] { launch_grad<float, float>(G->dg, player, in, out, st); });
+               [&] { launch_terms<float>(G->dg, player, in, out, nullptr, st); });
 }
 
-// SBR of player p with loss gradient sign * g (player 1 receives A^T x and negates).
+// SBR of player p with loss gradient sign * g (player 1 receives A^T x and negates);
+// g holds contributions (grad32) unless dense.
 egt_status sbr(egt_game* G, int p, const float* g, double mu, const float* old, double tau,
-               float* out, int value_slot, cudaStream_t st) {
+               float* out, int value_slot, cudaStream_t st, bool dense = false) {
   SbrArgs a{};
   a.g = g;
+  a.contrib = !dense;
   a.sign = p == 0 ? 1.f : -1.f;
   a.mu = mu;
   a.old = old;
@@ -564,14 +574,14 @@ egt_status read_vals(egt_game* G, int first, int n, cudaStream_t st) {
 
 egt_status gap_internal(egt_game* G, const float* x, const float* y, double* gap_mbb, cudaStream_t st) {
   EGT_TRY(timed(G, EGT_KERNEL_GRAD_F64, st, "grad f64 kernel",               // A y
-                [&] { launch_grad<float, double>(G->dg, 0, y, G->g64[0], st); }));
+                [&] { launch_terms<float>(G->dg, 0, y, nullptr, G->g64[0], st); }));
   EGT_TRY(timed(G, EGT_KERNEL_GRAD_F64, st, "grad f64 kernel",               // A^T x
-                [&] { launch_grad<float, double>(G->dg, 1, x, G->g64[1], st); }));
+                [&] { launch_terms<float>(G->dg, 1, x, nullptr, G->g64[1], st); }));
   EGT_TRY(timed(G, EGT_KERNEL_BR_F64, st, "br kernel", [&] {                // min_x <x, Ay>
-    launch_br64(G->dg, 0, G->g64[0], 1.0, G->vals + 8, G->partials, G->counter, st);
+    launch_br64(G->dg, 0, G->g64[0], true, 1.0, G->vals + 8, G->partials, G->counter, st);
   }));
   EGT_TRY(timed(G, EGT_KERNEL_BR_F64, st, "br kernel", [&] {                // max_y <y, A^T x>
-    launch_br64(G->dg, 1, G->g64[1], -1.0, G->vals + 9, G->partials, G->counter, st);
+    launch_br64(G->dg, 1, G->g64[1], true, -1.0, G->vals + 9, G->partials, G->counter, st);
   }));
   CUDA_TRY(cudaMemcpyAsync(G->pinned + 8, G->vals + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -719,8 +729,8 @@ int engine_grid(egt_game* G) {
   if (G->eng_grid == -2) {
     const int maxg = engine_max_grid(G->dg);
     const int NB = G->ld / kSbrHands;
-    const int S0 = G->comp.tpx[0].S, S1 = G->comp.tpx[1].S;
-    const int items = std::max(2 * NB, S0 + S1);
+    // widest phase: the EGV SBR with the residual's two best responses, or a product
+    const int items = std::max(3 * NB, (int)G->comp.term.size());
     G->eng_grid = maxg <= 0 ? 0 : std::min(maxg, items);
   }
   return G->eng_grid;
@@ -870,7 +880,7 @@ egt_status egt_create_game(const egt_game_desc* desc, int32_t device, void* stre
     for (int p = 0; p < 2 && st == EGT_OK; ++p)
       if (sbr_smem_bytes(G->dg, p) > room || br_smem_bytes(G->dg, p) > room)
         st = fail(EGT_ERR_INVALID_ARG, "betting tree too large for the shared-memory SBR tile");
-    if (st == EGT_OK && grad_smem_bytes(G->dg, true) > room)
+    if (st == EGT_OK && grad_smem_bytes(G->dg) > room)
       st = fail(EGT_ERR_INVALID_ARG, "hand count too large for the shared-memory gradient tile");
   }
   if (st != EGT_OK) {
@@ -956,7 +966,11 @@ egt_status egt_grad(egt_game* G, int32_t player, const float* in, float* out, vo
   EGT_TRY(check_ptr(out, "out"));
   if (in == out) return fail(EGT_ERR_INVALID_ARG, "in and out must differ");
   DeviceGuard guard(G->device);
-  return grad32(G, player, in, out, S(stream));
+  cudaStream_t st = S(stream);
+  float* c = reinterpret_cast<float*>(G->pub);
+  EGT_TRY(grad32(G, player, in, c, st));
+  return timed(G, EGT_KERNEL_GRAD_F32, st, "combine kernel",
+               [&] { launch_combine<float>(G->dg, player, c, out, st); });
 }
 
 egt_status egt_grad_f64(egt_game* G, int32_t player, const double* in, double* out, void* stream) {
@@ -968,8 +982,10 @@ egt_status egt_grad_f64(egt_game* G, int32_t player, const double* in, double* o
   if ((const void*)in == (const void*)out) return fail(EGT_ERR_INVALID_ARG, "in and out must differ");
   DeviceGuard guard(G->device);
   cudaStream_t st = S(stream);
-  return timed(G, EGT_KERNEL_GRAD_F64, st, "grad f64 kernel",
-               [&] { launch_grad<double, double>(G->dg, player, in, out, st); });
+  EGT_TRY(timed(G, EGT_KERNEL_GRAD_F64, st, "grad f64 kernel",
+                [&] { launch_terms<double>(G->dg, player, in, nullptr, G->pub, st); }));
+  return timed(G, EGT_KERNEL_GRAD_F64, st, "combine kernel",
+               [&] { launch_combine<double>(G->dg, player, G->pub, out, st); });
 }
 
 egt_status egt_smoothed_br(egt_game* G, int32_t player, const float* g, double mu, float* q_out,
@@ -981,7 +997,7 @@ egt_status egt_smoothed_br(egt_game* G, int32_t player, const float* g, double m
   if (q_out) EGT_TRY(check_ptr(q_out, "q_out"));
   if (!(mu > 0) || !std::isfinite(mu)) return fail(EGT_ERR_INVALID_ARG, "mu must be finite and > 0");
   DeviceGuard guard(G->device);
-  EGT_TRY(sbr(G, player, g, mu, nullptr, 0, q_out, value_out ? 4 : -1, S(stream)));
+  EGT_TRY(sbr(G, player, g, mu, nullptr, 0, q_out, value_out ? 4 : -1, S(stream), true));
   if (value_out) {
     EGT_TRY(read_vals(G, 4, 1, S(stream)));
     // player 1's kernel solved min <y, -g> + mu d(y); its own maximum is the negation
@@ -1000,7 +1016,7 @@ egt_status egt_best_response_f64(egt_game* G, int32_t player, const double* g, d
   DeviceGuard guard(G->device);
   cudaStream_t st = S(stream);
   EGT_TRY(timed(G, EGT_KERNEL_BR_F64, st, "br kernel", [&] {
-    launch_br64(G->dg, player, g, player == 0 ? 1.0 : -1.0, G->vals + 10, G->partials, G->counter, st);
+    launch_br64(G->dg, player, g, false, player == 0 ? 1.0 : -1.0, G->vals + 10, G->partials, G->counter, st);
   }));
   CUDA_TRY(cudaMemcpyAsync(G->pinned + 10, G->vals + 10, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
   CUDA_TRY(cudaStreamSynchronize(S(stream)));

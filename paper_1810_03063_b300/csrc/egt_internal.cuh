@@ -25,6 +25,7 @@ struct DevTpx {
 
 // Terminals grouped by the sequence of the output player (CSR over that player's sequences).
 struct DevTerms {
+  int n;                   // terminals
   const int* ptr;          // [S_p + 1]
   const int* opp_seq;      // [n] opponent sequence of the terminal
   const int* kind;         // [n] 0 fold, 1 showdown
@@ -71,22 +72,28 @@ void set_last_error(const std::string& msg);
 int opt_in_dynamic_smem(const void* kernel);
 
 // ---- kernels ----
-template <typename TIn, typename T>
-void launch_grad(const DevGame& g, int player, const TIn* in, T* out, cudaStream_t st);
+// Terminal contributions of player `player`'s product (A y for player 0, A^T x for
+// player 1): c32 / c64 (either may be NULL) [terms[player].n][ld], row e = coef_e x the
+// exact payoff sum of terminal e, without the r / Z factor (grad_impl.cuh).
+template <typename TIn>
+void launch_terms(const DevGame& g, int player, const TIn* in, float* c32, double* c64, cudaStream_t st);
 
-size_t grad_smem_bytes(const DevGame& g, bool f64);
+// Product rows from contributions: out[s][h] = rz[h] x (sum of the contributions of the
+// terminals of sequence s, in terminal order); 0 on padding hands.
+template <typename T>
+void launch_combine(const DevGame& g, int player, const T* c, T* out, cudaStream_t st);
 
-// One product with both results: out32 (FP32) and out64 (FP64) from the same exact sums.
-void launch_grad_dual(const DevGame& g, int player, const float* in, float* out32, double* out64,
-                      cudaStream_t st);
+size_t grad_smem_bytes(const DevGame& g);
 
 // SBR of player p on g (sign: +1 player 0, -1 player 1), temperature mu * beta_j.
-// g may be NULL (treated as 0: the uniform behavioural strategy).  If out is
+// g may be NULL (treated as 0: the uniform behavioural strategy); with contrib it
+// holds player p's terminal contributions (launch_terms), else a dense [S][ld] row set.  If out is
 // non-NULL writes q, or (1 - tau) old + tau q when old is non-NULL.  If
 // value_dev is non-NULL writes sum over hands and root simplexes of the value
 // (FP64) to *value_dev, reducing per-CTA partials (partials[grid], counter).
 struct SbrArgs {
   const float* g;
+  bool contrib;
   float sign;
   double mu;
   const float* old;
@@ -100,8 +107,9 @@ struct SbrArgs {
 void launch_sbr(const DevGame& g, int player, const SbrArgs& a, cudaStream_t st);
 size_t sbr_smem_bytes(const DevGame& g, int player);
 
-// Plain best response value in FP64: sign * (min over the treeplex of <q, sign * g>).
-void launch_br64(const DevGame& g, int player, const double* gv, double sign, double* value_dev,
+// Plain best response value in FP64: sign * (min over the treeplex of <q, sign * g>);
+// g as in SbrArgs (contributions or dense rows).
+void launch_br64(const DevGame& g, int player, const double* gv, bool contrib, double sign, double* value_dev,
                  double* partials, unsigned int* counter, cudaStream_t st);
 size_t br_smem_bytes(const DevGame& g, int player);
 

@@ -4,7 +4,9 @@
 // bookkeeping and the FP64 stopping residual -- with no host round trip.
 //
 // Phases are separated by a grid barrier; the work of a phase (32-hand SBR
-// items, one output sequence per gradient item) is spread over the CTAs.
+// items, one terminal per product item) is spread over the CTAs.  Products stay
+// in terminal-contribution form; the SBR items add a sequence's contributions
+// while they load their tile.
 // Every CTA keeps its own copy of the solver state (t, mu, tau, buffer index)
 // and takes every decision (EGV sign, tau back-off, gap target) itself from
 // the same per-item FP64 partials, summed in the same fixed order as the
@@ -131,7 +133,8 @@ __device__ __forceinline__ TpxTab pick(const Tabs& tb, int p) {
   return t;
 }
 
-// One SBR phase: all 32-hand items of `player`, spread over the CTAs.
+// One SBR phase: all 32-hand items of `player`, spread over the CTAs; gv holds the
+// player's terminal contributions (or is NULL).
 __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int player, const float* gv,
                                         double mu, const float* old, double tau, float* out,
                                         double* partials, unsigned char* sm) {
@@ -140,6 +143,8 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int pl
   for (int item = blockIdx.x; item < NB; item += gridDim.x) {
     SbrItemArgs a;
     a.g = gv;
+    a.gptr = player ? g.terms[1].ptr : g.terms[0].ptr;
+    a.grz = player ? g.rz[1] : g.rz[0];
     a.sign = player == 0 ? 1.f : -1.f;
     a.mu = mu;
     a.old = old;
@@ -150,13 +155,13 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int pl
   }
 }
 
-// One product phase: every output sequence of `player`; out64 (FP64 copy for the
-// residual) may be NULL.
+// One product phase: every terminal of `player`'s grouping; c64 (FP64 contributions
+// for the residual) may be NULL.
 __device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, int player, const float* in,
-                                         float* out, double* out64, unsigned char* sm) {
-  const int S = player ? g.tpx[1].S : g.tpx[0].S;
-  for (int item = blockIdx.x; item < S; item += gridDim.x)
-    grad_item<float>(g, tb.grad, player, item, in, out, out64, sm);
+                                         float* c32, double* c64, unsigned char* sm) {
+  const int T = player ? g.terms[1].n : g.terms[0].n;
+  for (int item = blockIdx.x; item < T; item += gridDim.x)
+    term_item<float>(g, tb.grad, player, item, in, c32, c64, sm);
 }
 
 // The residual's two FP64 best responses as items [first, first + 2 NB) of a phase
@@ -165,9 +170,11 @@ __device__ __forceinline__ void run_br_items(const DevGame& g, const Tabs& tb, i
                                              const EngineBufs& b, double* partBR0, double* partBR1,
                                              unsigned char* sm) {
   if (item < NB)
-    br64_item(g, tb.tpx[0], item, b.g64[0], 1.0, partBR0 + item, reinterpret_cast<double*>(sm));
+    br64_item(g, tb.tpx[0], item, b.g64[0], g.terms[0].ptr, g.rz64[0], 1.0, partBR0 + item,
+              reinterpret_cast<double*>(sm));
   else
-    br64_item(g, tb.tpx[1], item - NB, b.g64[1], -1.0, partBR1 + item - NB, reinterpret_cast<double*>(sm));
+    br64_item(g, tb.tpx[1], item - NB, b.g64[1], g.terms[1].ptr, g.rz64[1], -1.0, partBR1 + item - NB,
+              reinterpret_cast<double*>(sm));
 }
 
 // Two fixed-order sums of per-item partials, computed by warp 0 of every CTA
@@ -299,6 +306,8 @@ __global__ void __launch_bounds__(kItemThreads, 1)
           if (item < NB) {
             SbrItemArgs a;
             a.g = g_ot_n;
+            a.gptr = ot ? g.terms[1].ptr : g.terms[0].ptr;
+            a.grz = ot ? g.rz[1] : g.rz[0];
             a.sign = ot == 0 ? 1.f : -1.f;
             a.mu = mu_ot;
             a.old = nullptr;

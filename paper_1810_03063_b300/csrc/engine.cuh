@@ -38,11 +38,11 @@ struct EngineCtl {
 struct EngineBufs {
   float* x[2];
   float* y[2];
-  float* gx[2];     // A y of the matching y buffer
-  float* gy[2];     // A^T x of the matching x buffer
-  float* tx;
-  float* ty;
-  double* g64[2];   // FP64 products of the residual
+  float* gx[2];     // A y of the matching y buffer (terminal contributions, [T][ld])
+  float* gy[2];     // A^T x of the matching x buffer (terminal contributions)
+  float* tx;        // [max(S0, T)][ld] scratch
+  float* ty;        // [max(S1, T)][ld] scratch
+  double* g64[2];   // FP64 products of the residual (terminal contributions)
   double* partials; // 4 x (ld / 32) per-item values
   egt_iter_log* log;
   int log_cap;

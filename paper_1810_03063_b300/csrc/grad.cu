@@ -1,7 +1,10 @@
-// Standalone gradient-product kernel: one CTA per output sequence running the
-// shared body grad_item (grad_impl.cuh: Sec. 3 products over the poker river
-// payoff structure, exact fixed-point sums).  The per-game tables are staged
-// in shared memory first.
+// Standalone gradient-product kernels.  The terminal kernel runs one CTA per
+// terminal of the output player's grouping on the shared body term_item
+// (grad_impl.cuh: Sec. 3 products over the poker river payoff structure, exact
+// fixed-point sums), after staging the per-game tables in shared memory.  The
+// combine kernel turns those contributions into dense product rows (the public
+// egt_grad / egt_grad_f64); the solver's own kernels read the contributions
+// directly.
 #include "egt_internal.cuh"
 #include "grad_impl.cuh"
 
@@ -10,46 +13,70 @@ namespace {
 
 template <typename TIn>
 __global__ void __launch_bounds__(kItemThreads)
-    grad_kernel(DevGame g, int player, const TIn* __restrict__ in, float* __restrict__ out32,
-                double* __restrict__ out64) {
+    term_kernel(DevGame g, int player, const TIn* __restrict__ in, float* __restrict__ c32,
+                double* __restrict__ c64) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const GradTab tb = stage_grad_tab(g, smem_raw);
   __syncthreads();
-  grad_item<TIn>(g, tb, player, blockIdx.x, in, out32, out64, smem_raw + grad_tab_bytes(g));
+  term_item<TIn>(g, tb, player, blockIdx.x, in, c32, c64, smem_raw + grad_tab_bytes(g));
+}
+
+__device__ __forceinline__ float combine_one(const float* c, const int* ptr, int s, int ld, int h,
+                                             const DevGame& g, int player) {
+  return product32(c, ptr, s, ld, h, (player ? g.rz[1] : g.rz[0])[h]);
+}
+
+__device__ __forceinline__ double combine_one(const double* c, const int* ptr, int s, int ld, int h,
+                                              const DevGame& g, int player) {
+  return product64(c, ptr, s, ld, h, (player ? g.rz64[1] : g.rz64[0])[h]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) combine_kernel(DevGame g, int player, const T* __restrict__ c,
+                                                      T* __restrict__ out) {
+  const int S = player ? g.tpx[1].S : g.tpx[0].S;
+  const int* ptr = player ? g.terms[1].ptr : g.terms[0].ptr;
+  const size_t n = (size_t)S * g.ld;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / g.ld), h = (int)(i % g.ld);
+    out[i] = h < g.H ? combine_one(c, ptr, s, g.ld, h, g, player) : T(0);
+  }
 }
 
 template <typename TIn>
-void launch(const DevGame& g, int player, const TIn* in, float* out32, double* out64, cudaStream_t st) {
+void launch_t(const DevGame& g, int player, const TIn* in, float* c32, double* c64, cudaStream_t st) {
   static int limit = 0;   // one process-wide opt-in per instantiation
-  if (limit == 0) limit = opt_in_dynamic_smem((const void*)grad_kernel<TIn>);
-  grad_kernel<TIn><<<g.tpx[player].S, kItemThreads, grad_smem_bytes(g, true), st>>>(g, player, in,
-                                                                                    out32, out64);
+  if (limit == 0) limit = opt_in_dynamic_smem((const void*)term_kernel<TIn>);
+  const int T = player ? g.terms[1].n : g.terms[0].n;
+  if (T == 0) return;
+  term_kernel<TIn><<<T, kItemThreads, grad_smem_bytes(g), st>>>(g, player, in, c32, c64);
 }
 
 }  // namespace
 
-size_t grad_smem_bytes(const DevGame& g, bool) { return grad_tab_bytes(g) + grad_item_smem(g); }
+size_t grad_smem_bytes(const DevGame& g) { return grad_tab_bytes(g) + grad_item_smem(g); }
 
 template <>
-void launch_grad<float, float>(const DevGame& g, int player, const float* in, float* out, cudaStream_t st) {
-  launch<float>(g, player, in, out, nullptr, st);
-}
-
-template <>
-void launch_grad<double, double>(const DevGame& g, int player, const double* in, double* out,
-                                 cudaStream_t st) {
-  launch<double>(g, player, in, nullptr, out, st);
+void launch_terms<float>(const DevGame& g, int player, const float* in, float* c32, double* c64,
+                         cudaStream_t st) {
+  launch_t<float>(g, player, in, c32, c64, st);
 }
 
 template <>
-void launch_grad<float, double>(const DevGame& g, int player, const float* in, double* out,
-                                cudaStream_t st) {
-  launch<float>(g, player, in, nullptr, out, st);
+void launch_terms<double>(const DevGame& g, int player, const double* in, float* c32, double* c64,
+                          cudaStream_t st) {
+  launch_t<double>(g, player, in, c32, c64, st);
 }
 
-void launch_grad_dual(const DevGame& g, int player, const float* in, float* out32, double* out64,
-                      cudaStream_t st) {
-  launch<float>(g, player, in, out32, out64, st);
+template <typename T>
+void launch_combine(const DevGame& g, int player, const T* c, T* out, cudaStream_t st) {
+  const int S = player ? g.tpx[1].S : g.tpx[0].S;
+  const size_t n = (size_t)S * g.ld;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, 148 * 8);
+  if (grid > 0) combine_kernel<T><<<grid, 256, 0, st>>>(g, player, c, out);
 }
+
+template void launch_combine<float>(const DevGame&, int, const float*, float*, cudaStream_t);
+template void launch_combine<double>(const DevGame&, int, const double*, double*, cudaStream_t);
 
 }  // namespace egt

@@ -12,18 +12,20 @@
 // prefix sums over the hands in ascending strength, up to h's tie group start /
 // from its end, minus the same prefix over each of h's cards' hand lists.
 //
-// One CTA (512 threads) per output sequence; its two halves take the
-// sequence's terminals in pairs (every sequence of the river games has one or
-// two).  All sums are exact: each w is put in fixed point with two int64 limbs
+// One CTA (512 threads) per terminal writes that terminal's contribution column
+// coef_b x (sum) for every hand; the consumer of the product (the smoothed best
+// response, the FP64 best response, or the combine kernel of egt_grad) adds the
+// one or two contributions of a sequence in terminal order and multiplies by
+// r_me / Z while it loads them.  All sums are exact: each w is put in fixed point with two int64 limbs
 // (integer part at a per-terminal power-of-two scale leaving 2^59 headroom,
 // then 40 more fraction bits), so prefix sums, per-card corrections and the
 // tie-aware differences are integer operations, deterministic in any order and
 // on the full-rate integer pipes.  For FP32 inputs w = r (FP64 range) x y is
 // formed exactly as the 77-bit product of the two mantissas, with integer
 // operations only (B300's FP64 pipe is a small fraction of the integer rate).
-// From the same exact sums the CTA can emit an FP32 result (float-float
-// accumulation over terminals, the path of every EGT step) and an FP64 result
-// (the stopping residual); asking for the FP64 one does not change the FP32 one.
+// From the same exact sums the CTA can emit an FP32 contribution (the path of
+// every EGT step) and an FP64 one (the stopping residual); asking for the FP64
+// one does not change the FP32 one.
 #pragma once
 #include <climits>
 
@@ -32,28 +34,8 @@
 namespace egt {
 
 constexpr int kItemThreads = 512;     // threads of a CTA of the engine and of the kernels
-constexpr int kHalfThreads = 256;     // one terminal per half CTA
 
 namespace gradimpl {
-
-struct FF {
-  float hi, lo;
-};
-
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-  const float s = __fadd_rn(a.hi, b.hi);
-  const float bb = __fsub_rn(s, a.hi);
-  float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-  err = __fadd_rn(err, __fadd_rn(a.lo, b.lo));
-  const float hi = __fadd_rn(s, err);
-  return {hi, __fsub_rn(err, __fsub_rn(hi, s))};
-}
-
-// c * v with the product's rounding error kept (TwoProd by fma)
-__device__ __forceinline__ FF ff_prod(float c, float v) {
-  const float p = __fmul_rn(c, v);
-  return {p, __fmaf_rn(c, v, -p)};
-}
 
 // fixed point: v0 = integer part, v1 = the next 40 fraction bits (both carry the sign)
 struct Fx {
@@ -204,31 +186,23 @@ __device__ __forceinline__ double fx_to_f64(Fx a, int ex) {
   return s * pow2d(-e1) * pow2d(e1 - ex);
 }
 
-__device__ __forceinline__ void half_sync(int half) {
-  asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(kHalfThreads) : "memory");
-}
-
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-// shared memory of one half: input cache / combine area, F (w in fixed point), P, PC,
-// warp maxima, warp totals
-__host__ __device__ inline size_t half_bytes(int ld, int n_slots, int lmax) {
-  const size_t fx = sizeof(Fx);
-  size_t b = align16((size_t)ld * 16);
-  b += align16((size_t)ld * fx);
-  b += align16((size_t)(ld + 1) * fx);
-  b += align16((size_t)n_slots * (lmax + 1) * fx);
-  b += 8 * sizeof(int) + 8 * fx + 16;
-  return align16(b);
-}
-
-constexpr int kMaxHandsPerThread = 6;   // ld <= 1536 with 256 threads per half
+constexpr int kMaxHandsPerThread = 3;   // ld <= 1536 with 512 threads
 
 }  // namespace gradimpl
 
-// Shared memory of one gradient CTA (without the staged tables).
+// Shared memory of one terminal item: input cache, F (w in fixed point), P, PC,
+// warp maxima, warp totals (without the staged tables).
 __host__ __device__ inline size_t grad_item_smem(const DevGame& g) {
-  return 2 * gradimpl::half_bytes(g.ld, g.n_slots, g.lmax);
+  using gradimpl::align16;
+  const size_t fx = sizeof(gradimpl::Fx);
+  size_t b = align16((size_t)g.ld * 8);
+  b += align16((size_t)g.ld * fx);
+  b += align16((size_t)(g.ld + 1) * fx);
+  b += align16((size_t)g.n_slots * (g.lmax + 1) * fx);
+  b += 16 * sizeof(int) + 16 * fx + 16;
+  return align16(b);
 }
 
 // Per-game tables the product reads for every terminal, staged once in shared memory.
@@ -272,158 +246,127 @@ __device__ inline GradTab stage_grad_tab(const DevGame& g, unsigned char* dst) {
   return t;
 }
 
-// Output column s of player `player`: (A in)[s] for player 0, (A^T in)[s] for player 1,
-// written to out32 (FP32) and / or out64 (FP64), either may be NULL; computed by one CTA
-// of kItemThreads threads.  `in` is read through L2 (it may have been written earlier in
-// the same launch by other CTAs).
+// Contribution of terminal e (index in player `player`'s grouping, DevTerms) to that
+// player's product: c32[e][h] and / or c64[e][h] (either may be NULL) = coef_b x the
+// card-removal / strength sum of w = r_opp (.) in[sigma_opp(b)], without the r_me / Z
+// factor.  One CTA of kItemThreads threads.  `in` is read through L2 (it may have
+// been written earlier in the same launch by other CTAs).
 template <typename TIn>
-__device__ inline void grad_item(const DevGame& g, const GradTab& tb, int player, int s,
-                                 const TIn* __restrict__ in, float* __restrict__ out32,
-                                 double* __restrict__ out64, unsigned char* smem) {
+__device__ inline void term_item(const DevGame& g, const GradTab& tb, int player, int e,
+                                 const TIn* __restrict__ in, float* __restrict__ c32,
+                                 double* __restrict__ c64, unsigned char* smem) {
   using namespace gradimpl;
   const int ld = g.ld, H = g.H, opp = 1 - player;
-  const int tid = threadIdx.x, half = tid / kHalfThreads, th = tid % kHalfThreads;
-  const int lane = tid & 31, hw = th >> 5;
-  constexpr int kHalfWarps = kHalfThreads / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kItemThreads / 32;
   const int lstride = g.lmax + 1;
-  const size_t hb = half_bytes(ld, g.n_slots, g.lmax);
 
-  unsigned char* hs = smem + half * hb;
-  TIn* cache = reinterpret_cast<TIn*>(hs);                                 // [ld] input column
-  Fx* F = reinterpret_cast<Fx*>(hs + align16((size_t)ld * 16));
+  TIn* cache = reinterpret_cast<TIn*>(smem);                               // [ld] input column
+  Fx* F = reinterpret_cast<Fx*>(smem + align16((size_t)ld * 8));
   Fx* P = F + ld;                                                          // [ld + 1]
   Fx* PC = reinterpret_cast<Fx*>(reinterpret_cast<unsigned char*>(P) + align16((size_t)(ld + 1) * sizeof(Fx)));
   int* wmax = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(PC) +
                                      align16((size_t)g.n_slots * lstride * sizeof(Fx)));
-  Fx* wtot = reinterpret_cast<Fx*>(wmax + 8);
+  Fx* wtot = reinterpret_cast<Fx*>(wmax + 16);
 
   // (selects instead of runtime indices into struct arrays, which would go to local memory)
   const DevTerms tm = player ? g.terms[1] : g.terms[0];
-  const int e0 = tm.ptr[s], e1 = tm.ptr[s + 1];
   const double* __restrict__ r_opp = opp ? tb.r64[1] : tb.r64[0];
-  const float* __restrict__ rz = player ? g.rz[1] : g.rz[0];
-  const double* __restrict__ rz64 = player ? g.rz64[1] : g.rz64[0];
+  const int os = tm.opp_seq[e];
+  const int kind = tm.kind[e];
+  const float coef32 = tm.coef[e];
+  const double coef64 = tm.coef64[e];
+  const TIn* col = in + (size_t)os * ld;
 
-  FF acc32[kMaxHandsPerThread];
-  double acc64[kMaxHandsPerThread];
+  // pass 1: input cached, largest exponent of |w|
+  int mlg = INT_MIN;
+  for (int h = tid; h < ld; h += kItemThreads) {
+    const TIn y = h < H ? __ldcg(col + h) : TIn(0);
+    cache[h] = y;
+    mlg = max(mlg, wprod(r_opp[h], y).lg);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) mlg = max(mlg, __shfl_xor_sync(0xffffffffu, mlg, d));
+  if (lane == 0) wmax[warp] = mlg;
+  __syncthreads();
+  int M = INT_MIN;
+#pragma unroll
+  for (int q = 0; q < kWarps; ++q) M = max(M, wmax[q]);
+  const int ex = scale_of(M);
+  // pass 2: exact fixed point
+  for (int h = tid; h < ld; h += kItemThreads) F[h] = to_fx(wprod(r_opp[h], cache[h]), ex);
+  __syncthreads();
+
+  // exclusive prefix over ascending strength: P[i] = sum_{k < i} w[k], P[ld] = total
+  const int K = (ld + kItemThreads - 1) / kItemThreads;   // raking chunk
+  const int k0 = min(tid * K, ld), k1 = min(k0 + K, ld);
+  Fx loc = fx_zero();
+  for (int i = k0; i < k1; ++i) loc = fx_add(loc, F[i]);
+  const Fx inc = fx_scan(loc, lane);
+  if (lane == 31) wtot[warp] = inc;
+  Fx run = fx_shfl_up(inc, 1);
+  if (lane == 0) run = fx_zero();
+  __syncthreads();
+  for (int q = 0; q < warp; ++q) run = fx_add(run, wtot[q]);
+  for (int i = k0; i < k1; ++i) {
+    P[i] = run;
+    run = fx_add(run, F[i]);
+  }
+  if (k0 < ld && k1 == ld) P[ld] = run;
+
+  // per-card exclusive prefixes, one warp per card slot
+  for (int c = warp; c < g.n_slots; c += kWarps) {
+    const int len = tb.card_len[c];
+    const uint16_t* lst = tb.card_hands + (size_t)c * g.lmax;
+    const Fx v0 = lane < len ? F[lst[lane]] : fx_zero();
+    const Fx v1 = lane + 32 < len ? F[lst[lane + 32]] : fx_zero();
+    const Fx a0 = fx_scan(v0, lane);
+    const Fx a1 = fx_add(fx_scan(v1, lane), fx_shfl(a0, 31));
+    Fx* pc = PC + (size_t)c * lstride;
+    if (lane == 0) pc[0] = fx_zero();
+    if (lane < len) pc[lane + 1] = a0;
+    if (lane + 32 < len) pc[lane + 33] = a1;
+  }
+  __syncthreads();
+
+  const Fx W = P[ld];
 #pragma unroll
   for (int k = 0; k < kMaxHandsPerThread; ++k) {
-    acc32[k] = {0.f, 0.f};
-    acc64[k] = 0.0;
-  }
-
-  const int K = (ld + kHalfThreads - 1) / kHalfThreads;   // raking chunk
-  const int k0 = min(th * K, ld), k1 = min(k0 + K, ld);
-
-  for (int base = e0; base < e1; base += 2) {
-    const int e = base + half;
-    if (e >= e1) continue;                                   // uniform within a half
-    const int os = tm.opp_seq[e];
-    const int kind = tm.kind[e];
-    const float coef32 = tm.coef[e];
-    const double coef64 = tm.coef64[e];
-    const TIn* col = in + (size_t)os * ld;
-
-    // pass 1: input cached, largest exponent of |w|
-    int mlg = INT_MIN;
-    for (int h = th; h < ld; h += kHalfThreads) {
-      const TIn y = h < H ? __ldcg(col + h) : TIn(0);
-      cache[h] = y;
-      mlg = max(mlg, wprod(r_opp[h], y).lg);
+    const int h = tid + k * kItemThreads;
+    if (h >= ld) break;
+    const uint4 hi = tb.hinfo[h];
+    const Fx C0 = PC[hi.z & 0xffffu];
+    const Fx C1 = PC[hi.w >> 16];
+    Fx val;
+    if (kind == 0) {
+      val = fx_sub(fx_sub(W, C0), C1);
+      if (g.hand_size == 2) val = fx_add(val, F[h]);
+    } else {
+      const Fx lt = fx_sub(fx_sub(P[hi.x & 0xffffu], PC[hi.y & 0xffffu]), PC[hi.z >> 16]);
+      const Fx gt = fx_sub(fx_sub(fx_sub(W, P[hi.x >> 16]), fx_sub(C0, PC[hi.y >> 16])),
+                           fx_sub(C1, PC[hi.w & 0xffffu]));
+      val = fx_sub(gt, lt);
     }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) mlg = max(mlg, __shfl_xor_sync(0xffffffffu, mlg, d));
-    if (lane == 0) wmax[hw] = mlg;
-    half_sync(half);
-    int M = INT_MIN;
-#pragma unroll
-    for (int q = 0; q < kHalfWarps; ++q) M = max(M, wmax[q]);
-    const int ex = scale_of(M);
-    // pass 2: exact fixed point
-    for (int h = th; h < ld; h += kHalfThreads) F[h] = to_fx(wprod(r_opp[h], cache[h]), ex);
-    half_sync(half);
-
-    // exclusive prefix over ascending strength: P[i] = sum_{k < i} w[k], P[ld] = total
-    Fx loc = fx_zero();
-    for (int i = k0; i < k1; ++i) loc = fx_add(loc, F[i]);
-    const Fx inc = fx_scan(loc, lane);
-    if (lane == 31) wtot[hw] = inc;
-    Fx run = fx_shfl_up(inc, 1);
-    if (lane == 0) run = fx_zero();
-    half_sync(half);
-    for (int q = 0; q < hw; ++q) run = fx_add(run, wtot[q]);
-    for (int i = k0; i < k1; ++i) {
-      P[i] = run;
-      run = fx_add(run, F[i]);
-    }
-    if (k0 < ld && k1 == ld) P[ld] = run;
-
-    // per-card exclusive prefixes, one warp per card slot
-    for (int c = hw; c < g.n_slots; c += kHalfWarps) {
-      const int len = tb.card_len[c];
-      const uint16_t* lst = tb.card_hands + (size_t)c * g.lmax;
-      const Fx v0 = lane < len ? F[lst[lane]] : fx_zero();
-      const Fx v1 = lane + 32 < len ? F[lst[lane + 32]] : fx_zero();
-      const Fx a0 = fx_scan(v0, lane);
-      const Fx a1 = fx_add(fx_scan(v1, lane), fx_shfl(a0, 31));
-      Fx* pc = PC + (size_t)c * lstride;
-      if (lane == 0) pc[0] = fx_zero();
-      if (lane < len) pc[lane + 1] = a0;
-      if (lane + 32 < len) pc[lane + 33] = a1;
-    }
-    half_sync(half);
-
-    const Fx W = P[ld];
-#pragma unroll
-    for (int k = 0; k < kMaxHandsPerThread; ++k) {
-      const int h = th + k * kHalfThreads;
-      if (h >= ld) break;
-      const uint4 hi = tb.hinfo[h];
-      const Fx C0 = PC[hi.z & 0xffffu];
-      const Fx C1 = PC[hi.w >> 16];
-      Fx val;
-      if (kind == 0) {
-        val = fx_sub(fx_sub(W, C0), C1);
-        if (g.hand_size == 2) val = fx_add(val, F[h]);
-      } else {
-        const Fx lt = fx_sub(fx_sub(P[hi.x & 0xffffu], PC[hi.y & 0xffffu]), PC[hi.z >> 16]);
-        const Fx gt = fx_sub(fx_sub(fx_sub(W, P[hi.x >> 16]), fx_sub(C0, PC[hi.y >> 16])),
-                             fx_sub(C1, PC[hi.w & 0xffffu]));
-        val = fx_sub(gt, lt);
-      }
-      if (out32 != nullptr) acc32[k] = ff_add(acc32[k], ff_prod(coef32, fx_to_f32(val, ex)));
-      if (out64 != nullptr) acc64[k] += coef64 * fx_to_f64(val, ex);
-    }
-    half_sync(half);   // the cache / F / P / PC are rewritten by the next terminal of this half
-  }
-
-  // combine the halves: half 1 leaves its per-hand sums in its cache area
-  __syncthreads();
-  float* other32 = reinterpret_cast<float*>(smem + hb);
-  double* other64 = reinterpret_cast<double*>(smem + hb + align16((size_t)ld * 4));
-  if (half == 1) {
-#pragma unroll
-    for (int k = 0; k < kMaxHandsPerThread; ++k) {
-      const int h = th + k * kHalfThreads;
-      if (h >= ld) break;
-      other32[h] = __fadd_rn(acc32[k].hi, acc32[k].lo);
-      other64[h] = acc64[k];
-    }
-  }
-  __syncthreads();
-  if (half == 0) {
-#pragma unroll
-    for (int k = 0; k < kMaxHandsPerThread; ++k) {
-      const int h = th + k * kHalfThreads;
-      if (h >= ld) break;
-      const bool live = h < H;
-      if (out32 != nullptr)
-        out32[(size_t)s * ld + h] = live ? rz[h] * (__fadd_rn(acc32[k].hi, acc32[k].lo) + other32[h]) : 0.f;
-      if (out64 != nullptr)
-        out64[(size_t)s * ld + h] = live ? rz64[h] * (acc64[k] + other64[h]) : 0.0;
-    }
+    const bool live = h < H;
+    if (c32 != nullptr) c32[(size_t)e * ld + h] = live ? coef32 * fx_to_f32(val, ex) : 0.f;
+    if (c64 != nullptr) c64[(size_t)e * ld + h] = live ? coef64 * fx_to_f64(val, ex) : 0.0;
   }
   __syncthreads();   // shared memory is reused by the caller's next item
+}
+
+// Product row s of a player at hand h from the terminal contributions: the
+// contributions of its terminals [ptr[s], ptr[s+1]) added in order, times r / Z.
+__device__ __forceinline__ float product32(const float* c, const int* ptr, int s, int ld, int h, float rz) {
+  float acc = 0.f;
+  for (int e = ptr[s]; e < ptr[s + 1]; ++e) acc += __ldcg(c + (size_t)e * ld + h);
+  return rz * acc;
+}
+
+__device__ __forceinline__ double product64(const double* c, const int* ptr, int s, int ld, int h,
+                                            double rz) {
+  double acc = 0.0;
+  for (int e = ptr[s]; e < ptr[s + 1]; ++e) acc += __ldcg(c + (size_t)e * ld + h);
+  return rz * acc;
 }
 
 }  // namespace egt

@@ -36,6 +36,7 @@ constexpr size_t kCounterOff = 256;            // arrival counter of the value r
 constexpr size_t kZeroBytes = 512;             // values + counter: cleared by every call
 constexpr size_t kPartialsOff = 512;           // per-CTA partial values, <= 1024 CTAs
 constexpr size_t kProdOff = kPartialsOff + 1024 * sizeof(double);   // FP64 A y, then A^T x
+                                                                    // (terminal contributions [T][ld])
 
 constexpr int kMaxDevices = 64;
 std::mutex g_addr_mu;
@@ -74,7 +75,7 @@ extern "C" egt_status egt_gap_noalloc(const egt_game* game, const float* x, cons
   if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
     return fail(EGT_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
   const egt::DevGame& dg = *v.dg;
-  const size_t n0 = (size_t)dg.tpx[0].S * dg.ld, n1 = (size_t)dg.tpx[1].S * dg.ld;
+  const size_t n0 = (size_t)dg.terms[0].n * dg.ld, n1 = (size_t)dg.terms[1].n * dg.ld;
   const size_t need = kProdOff + round256(n0 * sizeof(double)) + n1 * sizeof(double);
   if (need > kNoAllocScratchBytes)
     return fail(EGT_ERR_INVALID_ARG, "the game needs " + std::to_string(need) +
@@ -104,10 +105,10 @@ extern "C" egt_status egt_gap_noalloc(const egt_game* game, const float* x, cons
 
   cudaError_t e = cudaMemsetAsync(base, 0, kZeroBytes, st);
   if (e != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-  egt::launch_grad<float, double>(dg, 0, y, ay, st);                              // A y
-  egt::launch_grad<float, double>(dg, 1, x, atx, st);                             // A^T x
-  egt::launch_br64(dg, 0, ay, 1.0, vals + 0, partials, counter, st);              // min_x <x, Ay>
-  egt::launch_br64(dg, 1, atx, -1.0, vals + 1, partials, counter, st);            // max_y <y, A^T x>
+  egt::launch_terms<float>(dg, 0, y, nullptr, ay, st);                            // A y
+  egt::launch_terms<float>(dg, 1, x, nullptr, atx, st);                           // A^T x
+  egt::launch_br64(dg, 0, ay, true, 1.0, vals + 0, partials, counter, st);        // min_x <x, Ay>
+  egt::launch_br64(dg, 1, atx, true, -1.0, vals + 1, partials, counter, st);      // max_y <y, A^T x>
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
   double host_vals[2] = {0.0, 0.0};

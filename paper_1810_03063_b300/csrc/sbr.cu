@@ -34,6 +34,8 @@ __global__ void __launch_bounds__(kItemThreads) sbr_kernel(DevGame g, int player
   extern __shared__ __align__(16) float sm[];
   SbrItemArgs ia;
   ia.g = a.g;
+  ia.gptr = a.contrib ? (player ? g.terms[1].ptr : g.terms[0].ptr) : nullptr;
+  ia.grz = player ? g.rz[1] : g.rz[0];
   ia.sign = a.sign;
   ia.mu = a.mu;
   ia.old = a.old;
@@ -48,13 +50,15 @@ __global__ void __launch_bounds__(kItemThreads) sbr_kernel(DevGame g, int player
 }
 
 __global__ void __launch_bounds__(kItemThreads)
-    br64_kernel(DevGame g, int player, const double* __restrict__ gv, double sign,
+    br64_kernel(DevGame g, int player, const double* __restrict__ gv, bool contrib, double sign,
                 double* value_dev, double* partials, unsigned int* counter) {
   extern __shared__ __align__(16) double smd[];
   unsigned char* raw = reinterpret_cast<unsigned char*>(smd);
   const TpxTab tt = stage_tpx_tab(g, player, raw);
   __syncthreads();
-  br64_item(g, tt, blockIdx.x, gv, sign, partials + blockIdx.x,
+  const int* gptr = contrib ? (player ? g.terms[1].ptr : g.terms[0].ptr) : nullptr;
+  const double* grz = player ? g.rz64[1] : g.rz64[0];
+  br64_item(g, tt, blockIdx.x, gv, gptr, grz, sign, partials + blockIdx.x,
             reinterpret_cast<double*>(raw + tpx_tab_bytes(g, player)));
   finish_value(partials, counter, value_dev, nullptr);
 }
@@ -89,13 +93,13 @@ void launch_sbr(const DevGame& g, int player, const SbrArgs& a, cudaStream_t st)
   sbr_kernel<<<grid, kItemThreads, sbr_smem_bytes(g, player), st>>>(g, player, a);
 }
 
-void launch_br64(const DevGame& g, int player, const double* gv, double sign, double* value_dev,
+void launch_br64(const DevGame& g, int player, const double* gv, bool contrib, double sign, double* value_dev,
                  double* partials, unsigned int* counter, cudaStream_t st) {
   static int limit = 0;
   if (limit == 0) limit = opt_in_dynamic_smem((const void*)br64_kernel);
   const int grid = g.ld / kSbrHands;
-  br64_kernel<<<grid, kItemThreads, br_smem_bytes(g, player), st>>>(g, player, gv, sign, value_dev,
-                                                                     partials, counter);
+  br64_kernel<<<grid, kItemThreads, br_smem_bytes(g, player), st>>>(g, player, gv, contrib, sign,
+                                                                     value_dev, partials, counter);
 }
 
 }  // namespace egt

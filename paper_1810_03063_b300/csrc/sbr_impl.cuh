@@ -25,7 +25,9 @@
 namespace egt {
 
 struct SbrItemArgs {
-  const float* g;          // [S][ld] gradient of the player's own loss up to `sign`; NULL = 0
+  const float* g;          // gradient of the player's own loss up to `sign`; NULL = 0
+  const int* gptr;         // NULL: g is dense [S][ld]; else g holds terminal contributions
+  const float* grz;        //   [T][ld] and row s is grz[h] x sum_{e in [gptr[s], gptr[s+1])} g[e][h]
   float sign;              // +1 player 0 (g = A y), -1 player 1 (g = A^T x)
   double mu;
   const float* old;        // if non-NULL the output is (1 - tau) old + tau q
@@ -123,9 +125,12 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
   const bool live = h < g.H;
 
   for (int idx = tid; idx < S * kSbrHands; idx += kItemThreads) {
-    const int s = idx / kSbrHands, l = idx % kSbrHands;
-    const size_t gi = (size_t)s * ld + h0 + l;
-    G[idx] = (a.g != nullptr && h0 + l < g.H) ? a.sign * __ldcg(a.g + gi) : 0.f;
+    const int s = idx / kSbrHands, l = idx % kSbrHands, hh = h0 + l;
+    const size_t gi = (size_t)s * ld + hh;
+    float v = 0.f;
+    if (a.g != nullptr && hh < g.H)
+      v = a.gptr != nullptr ? product32(a.g, a.gptr, s, ld, hh, a.grz[hh]) : __ldcg(a.g + gi);
+    G[idx] = a.sign * v;
     if (a.old != nullptr) O[idx] = __ldcg(a.old + gi);
   }
   for (int j = tid; j < J; j += kItemThreads) {
@@ -199,8 +204,10 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
 
 // One item of the FP64 best-response value: sign * min over the treeplex of
 // <q, sign * g> summed over the item's live hands, written to *value_partial.
+// gv as in SbrItemArgs: dense [S][ld] (gptr NULL) or terminal contributions.
 __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, const double* gv,
-                                 double sign, double* value_partial, double* sm) {
+                                 const int* gptr, const double* grz, double sign,
+                                 double* value_partial, double* sm) {
   const int S = tp.S, ld = g.ld;
   constexpr int kWarps = kItemThreads / 32;
   double* G = sm;                                  // [S][32]
@@ -210,7 +217,10 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
   const bool live = h < g.H;
   for (int idx = tid; idx < S * kSbrHands; idx += kItemThreads) {
     const int s = idx / kSbrHands, l = idx % kSbrHands;
-    G[idx] = h0 + l < g.H ? sign * __ldcg(gv + (size_t)s * ld + h0 + l) : 0.0;
+    const int hh = h0 + l;
+    double v = 0.0;
+    if (hh < g.H) v = gptr != nullptr ? product64(gv, gptr, s, ld, hh, grz[hh]) : __ldcg(gv + (size_t)s * ld + hh);
+    G[idx] = sign * v;
   }
   __syncthreads();
   for (int l = tp.L - 1; l >= 0; --l) {

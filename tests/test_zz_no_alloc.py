@@ -61,7 +61,7 @@ def test_gap_noalloc_after_another_game(egtlib):
 
 def test_gap_noalloc_rejects_games_beyond_its_scratch(egtlib):
     from paper_1810_03063_b300 import synth
-    g = egtlib.Game(synth.large(), device=0)       # (508 + 508) * 1088 * 8 bytes > 2 MiB
+    g = egtlib.Game(synth.large(), device=0)       # 2 * 677 terminals * 1088 * 8 bytes > 2 MiB
     x, y = random_pair(g, np.random.default_rng(1))
     with pytest.raises(egtlib.EGTError) as e:
         g.gap_noalloc(x, y)
