@@ -4,11 +4,15 @@
 Workload: 52-card river endgame, fixed board, 1081 hands per player, bets
 {0.5, 1} x pot + all-in, raise cap 3, stack 10, pot 1, Dirichlet(0.5) ranges
 (seeded synthetic stand-in for the paper's Libratus endgames).  One step is one
-EGT/as iteration through the C-ABI: a Decr (Step = 3 FP32 products + 3 smoothed
-best responses, the EGV check, and any tau back-offs) plus the FP64 stopping gap
-of Alg. 3 (2 FP64 products + 2 best responses).  The game's state is ~1 MB, so
-L2 is flushed (256 MB write) before every timed iteration and each iteration is
-timed alone with CUDA events on the library's stream.
+egt_iterate call through the C-ABI running --iters-per-step EGT/as iterations in
+one device-resident launch, as a solve runs them; every iteration is a Decr
+(Step = 3 FP32 products + 3 smoothed best responses, the EGV check, any tau
+back-offs) plus the FP64 stopping gap of Alg. 3 (FP64 products and best
+responses).  The game's state is ~2 MB, so L2 is flushed (256 MB write) before
+every timed step; each step is timed with CUDA events on the library's stream.
+The solver is re-initialised (untimed) every --reinit-every iterations so that
+every timed iteration is one of a solve's first iterations.  The same loop with
+one iteration per launch is reported beside it (config.one_iteration_per_launch).
 
 Under torchrun (--gpus N > 1) every rank solves its own game (seed + rank) as an
 independent replica: the method has no exchange step, so no collective is used
@@ -39,14 +43,16 @@ WORKLOAD = "full-deck river endgame: 52 cards, 1081 hands/player, bets {0.5,1}xp
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--iters-per-step", type=int, default=100)
+    ap.add_argument("--reinit-every", type=int, default=8000)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample (cpu_baseline)")
     ap.add_argument("--ttg-max-iters", type=int, default=20000)
     ap.add_argument("--no-ttg", action="store_true")
     ap.add_argument("--engine", default="device", choices=["device", "host"],
-                    help="device: each step is one egt_iterate launch; host: egt_step + egt_state_gap")
+                    help="device: each step is one egt_iterate launch; host: egt_step + egt_state_gap per iteration")
     return ap.parse_args()
 
 
@@ -192,61 +198,83 @@ def run_ours(args, world, rank, local):
     g = egt.Game(spec, device=local)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def one_step(tau):
+    ips = max(1, args.iters_per_step)
+    done = [0]
+
+    def one_step(n):
         if args.engine == "device":
-            r = g.iterate(1, variant=egt.EGT_AS, gap_every=1)
-            return dict(tau=r["tau"], backoffs=r["backoffs"]), r["gap_mbb"]
-        info = g.step(-1, tau, mode=egt.STEP_DECR)
-        return info, g.state_gap()
+            r = g.iterate(n, variant=egt.EGT_AS, gap_every=1)
+            return r["backoffs"], r["gap_mbb"]
+        backoffs, gap = 0, None
+        for _ in range(n):
+            info = g.step(-1, tau_h[0], mode=egt.STEP_DECR)
+            tau_h[0] = info["tau"]
+            backoffs += info["backoffs"]
+            gap = g.state_gap()
+        return backoffs, gap
+
+    tau_h = [0.5]                         # EGT/as tau carried by the host-driven loop
+
+    def maybe_reinit(n):
+        if done[0] + n > args.reinit_every:
+            g.solver_init(variant=egt.EGT_AS, alpha=0.01)
+            done[0] = 0
+            tau_h[0] = 0.5
+        done[0] += n
 
     g.solver_init(variant=egt.EGT_AS, alpha=0.01)
-    tau = 0.5
     for _ in range(args.warmup):
-        info, _ = one_step(tau)
-        tau = info["tau"]
+        maybe_reinit(ips)
+        one_step(ips)
 
-    def timed_pass(k, tau):
+    def timed_pass(k, n):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
         backoffs = 0
         gap = None
         for i in range(k):
+            maybe_reinit(n)
             flush.fill_(float(i))
             evs[i][0].record(stream)
-            info, gap = one_step(tau)
+            b, gap = one_step(n)
             evs[i][1].record(stream)
-            tau = info["tau"]
-            backoffs += info["backoffs"]
+            backoffs += b
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in evs)
-        return ms, tau, backoffs, gap
+        return ms, backoffs, gap
 
     g.profile(0)                          # restart launch counts
     clk = ClockSampler(local).__enter__()  # sampled over every GPU-busy phase below
     barrier(world)
     torch.cuda.synchronize()
-    ms, tau, backoffs, gap = timed_pass(args.steps, tau)
+    ms, backoffs, gap = timed_pass(args.steps, ips)
     torch.cuda.synchronize()
     barrier(world)
     launches = g.profile_read()
     gpu_launches = sum(v["launches"] for v in launches.values())
     ms_max = allreduce_max(world, ms)
-    total_iters = allreduce_sum(world, float(args.steps))
+    total_iters = allreduce_sum(world, float(args.steps * ips))
 
     # per-kernel device time over the same kind of steps (events around every launch)
     g.profile(1)
-    timed_pass(args.steps, tau)
+    timed_pass(args.steps, ips)
     prof = g.profile_read()
     g.profile(0)
     ab = algorithmic_bytes(g)
+    per_launch = dict(ab)
+    per_launch["engine"] = ab["engine"] * ips
     dom = max(prof, key=lambda k: prof[k]["ms"])
     avg_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
-    achieved = ab[dom] / (avg_ms * 1e-3) / 1e9
+    achieved = per_launch[dom] / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     kernels = {k: dict(launches=v["launches"], ms=round(v["ms"], 4),
                        avg_us=round(1e3 * v["ms"] / max(1, v["launches"]), 3),
-                       alg_bytes=int(ab[k]),
-                       gbs=round(ab[k] / (v["ms"] / max(1, v["launches"]) * 1e-3) / 1e9, 2) if v["ms"] else None)
+                       alg_bytes=int(per_launch[k]),
+                       gbs=round(per_launch[k] / (v["ms"] / max(1, v["launches"]) * 1e-3) / 1e9, 2) if v["ms"] else None)
                for k, v in prof.items()}
+
+    # the same iterations with one launch each (each timed alone after an L2 flush)
+    one_ms, _, _ = timed_pass(min(args.steps * ips, 200), 1)
+    one_per_launch = round(min(args.steps * ips, 200) / (one_ms * 1e-3), 2)
 
     # time to gap and end-to-end: create from host arrays, solve to 1 mbb, copy x, y to host
     ttg = e2e = None
@@ -278,7 +306,8 @@ def run_ours(args, world, rank, local):
     clk.__exit__(None, None, None)
     return dict(ms=ms_max, total_iters=total_iters, backoffs=backoffs, gap=gap, clocks=clk.summary(),
                 gpu_launches=gpu_launches, kernels=kernels, dom=dom, achieved=achieved, peak=peak,
-                peak_kind=peak_kind, avg_ms=avg_ms, ttg=ttg, e2e=e2e, g=g)
+                peak_kind=peak_kind, avg_ms=avg_ms, ttg=ttg, e2e=e2e, g=g, ips=ips,
+                per_launch=per_launch, one_per_launch=one_per_launch)
 
 
 def oracle_iterations(seconds, max_iters=None, seed=None):
@@ -375,14 +404,17 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "hands": g.H, "seq_per_player": g.S[0],
                    "terminals": g.T, "variant": "EGT/as (Alg. 3 + 4)", "gap_every": 1,
-                   "engine": args.engine,
+                   "engine": args.engine, "iterations_per_step": r["ips"],
+                   "reinit_every": args.reinit_every,
+                   "one_iteration_per_launch": {"value": r["one_per_launch"], "unit": UNIT},
                    "precision": "products and smoothed BR in f32 (compensated sums); gap, EGV sums, mu in f64",
-                   "l2": "flushed (256 MB write) before every timed iteration",
+                   "l2": "flushed (256 MB write) before every timed step (one launch of iterations_per_step "
+                         "iterations; the ~2 MB state stays L2-resident inside the launch, as in a solve)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": r["dom"], "achieved": round(r["achieved"], 2),
                      "peak": r["peak"], "unit": "GB/s", "frac": round(r["achieved"] / r["peak"], 5),
                      "peak_source": r["peak_kind"], "traffic": None,
-                     "alg_bytes_per_launch": int(algorithmic_bytes(g)[r["dom"]]),
+                     "alg_bytes_per_launch": int(r["per_launch"][r["dom"]]),
                      "avg_launch_us": round(r["avg_ms"] * 1e3, 3)},
         "kernels": r["kernels"],
         "cpu_baseline": cpu,

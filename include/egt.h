@@ -312,14 +312,18 @@ EGT_API egt_status egt_profile(egt_game* game, int32_t enable);
 EGT_API egt_status egt_profile_read(egt_game* game, double* ms, int64_t* launches);
 
 /* Device time of the device-resident driver (egt_iterate / egt_solve) by phase,
- * measured by CTA 0 between consecutive grid-barrier exits (so a phase includes
- * the wait for its slowest CTA and the barrier), summed since the last reset:
- * 0-6 the Step's SBR / product / SBR / product / SBR / product phases and the
- * EGV smoothed best response, 7 the EGV decision, 8 the accept barrier of an
- * iteration without residual, 9 the residual's FP64 products, 10 its FP64 best
- * responses and decision.  Host arrays of 11 entries (microseconds, counts),
- * either may be NULL; reset != 0 clears the sums after reading. */
-EGT_API egt_status egt_engine_trace(egt_game* game, int32_t reset, double* phase_us,
+ * measured by CTA 0 and summed since the last reset.  Phases: 0-5 the Step's
+ * SBR / product / SBR / product / SBR / product phases (phase 0 is skipped when
+ * the previous iteration computed this v_hat ahead; phase 5 then may carry the
+ * next iteration's v_hat), 6 the phase after the Step (the other player's EGV
+ * part, the residual's FP64 best responses, the next v_hat), 7 the sums
+ * behind the EGV and residual decisions (fixed-order sums of the per-item
+ * partials that every CTA reads after phase 6; no barrier).  phase_us: from
+ * one mark to the next (for 0-6, barrier exits: the phase's slowest CTA and the
+ * barrier included); work_us: for 0-6, from that exit to CTA 0's arrival at the
+ * next barrier (its own items); phase_count: phases timed.  Host arrays of 8
+ * entries, any may be NULL; reset != 0 clears the sums after reading. */
+EGT_API egt_status egt_engine_trace(egt_game* game, int32_t reset, double* phase_us, double* work_us,
                                     int64_t* phase_count);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -91,6 +91,7 @@ struct egt_game {
   double* eng_partials = nullptr;
   int eng_grid = -2;             // -2: not queried yet, <= 0: engine unavailable
   double eng_phase_ns[kEnginePhases] = {0};
+  double eng_phase_work_ns[kEnginePhases] = {0};
   long long eng_phase_n[kEnginePhases] = {0};
   bool host_only = false;        // compiled tables only (device = -1): queries work, kernels do not
   long long products = 0;
@@ -729,8 +730,9 @@ int engine_grid(egt_game* G) {
   if (G->eng_grid == -2) {
     const int maxg = engine_max_grid(G->dg);
     const int NB = G->ld / kSbrHands;
-    // widest phase: the EGV SBR with the residual's two best responses, or a product
-    const int items = std::max(3 * NB, (int)G->comp.term.size());
+    // widest phase: the last product with the next v_hat, or the EGV SBR with the
+    // residual's two best responses
+    const int items = std::max(3 * NB, (int)G->comp.term.size() + NB);
     G->eng_grid = maxg <= 0 ? 0 : std::min(maxg, items);
   }
   return G->eng_grid;
@@ -797,6 +799,7 @@ egt_status engine_run(egt_game* G, int variant, double eps_mbb, int gap_every, i
   G->products += c.products;
   for (int k = 0; k < kEnginePhases; ++k) {
     G->eng_phase_ns[k] += (double)c.phase_ns[k];
+    G->eng_phase_work_ns[k] += (double)c.phase_work_ns[k];
     G->eng_phase_n[k] += (long long)c.phase_n[k];
   }
   if (rep) {
@@ -1241,13 +1244,16 @@ egt_status egt_profile(egt_game* G, int32_t enable) {
   return EGT_OK;
 }
 
-egt_status egt_engine_trace(egt_game* G, int32_t reset, double* phase_us, int64_t* phase_count) {
+egt_status egt_engine_trace(egt_game* G, int32_t reset, double* phase_us, double* work_us,
+                            int64_t* phase_count) {
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   for (int k = 0; k < kEnginePhases; ++k) {
     if (phase_us) phase_us[k] = G->eng_phase_ns[k] * 1e-3;
+    if (work_us) work_us[k] = G->eng_phase_work_ns[k] * 1e-3;
     if (phase_count) phase_count[k] = G->eng_phase_n[k];
     if (reset) {
       G->eng_phase_ns[k] = 0;
+      G->eng_phase_work_ns[k] = 0;
       G->eng_phase_n[k] = 0;
     }
   }

@@ -51,13 +51,24 @@ struct GridBar {
   unsigned long long limit_ns;
 };
 
+// Phase clock of CTA 0 (thread 0), kept in shared memory and written to the
+// control block at exit: per phase, the time from the previous barrier exit to
+// this CTA's arrival at the next barrier (its own work) and to the exit.
+struct PhaseClock {
+  unsigned long long last, arrive;
+  unsigned long long ns[kEnginePhases];
+  unsigned long long work[kEnginePhases];
+  unsigned int n[kEnginePhases];
+};
+
 // All CTAs meet here; k counts this CTA's barriers.  Returns false (in every
 // thread) if the wait ran out or an error status was recorded.
-__device__ bool grid_sync(const GridBar& b, unsigned long long& k) {
+__device__ bool grid_sync(const GridBar& b, unsigned long long& k, PhaseClock* clk) {
   __shared__ int ok_s;
   __syncthreads();
   ++k;
   if (threadIdx.x == 0) {
+    if (blockIdx.x == 0) clk->arrive = global_ns();
     int ok = 1;
     __threadfence();                       // release this CTA's writes of the phase
     atomicAdd(b.arrive, 1ull);
@@ -87,21 +98,28 @@ __device__ bool grid_sync(const GridBar& b, unsigned long long& k) {
   return ok_s != 0;
 }
 
-// Phase clock of CTA 0 (thread 0): time since the previous barrier exit, kept in
-// shared memory and written to the control block at exit.
-struct PhaseClock {
-  unsigned long long last;
-  unsigned long long ns[kEnginePhases];
-  unsigned int n[kEnginePhases];
-};
-
-__device__ __forceinline__ void phase_mark(PhaseClock* c, int phase) {
+// CTA 0 books the time since the last mark to `phase` (work done without a barrier).
+__device__ __forceinline__ void phase_cut(PhaseClock* c, int phase) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const unsigned long long now = global_ns();
     c->ns[phase] += now - c->last;
+    c->work[phase] += now - c->last;
     c->n[phase] += 1;
     c->last = now;
   }
+}
+
+// End of a phase: grid barrier, then CTA 0 books the phase's time.
+__device__ __forceinline__ bool phase_end(const GridBar& b, unsigned long long& k, PhaseClock* c, int phase) {
+  if (!grid_sync(b, k, c)) return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long now = global_ns();
+    c->ns[phase] += now - c->last;
+    c->work[phase] += c->arrive - c->last;
+    c->n[phase] += 1;
+    c->last = now;
+  }
+  return true;
 }
 
 // Tables staged once per launch at the start of shared memory.
@@ -177,22 +195,35 @@ __device__ __forceinline__ void run_br_items(const DevGame& g, const Tabs& tb, i
               reinterpret_cast<double*>(sm));
 }
 
-// Two fixed-order sums of per-item partials, computed by warp 0 of every CTA
-// and shared with the CTA.
-__device__ __forceinline__ void reduce_pair(const double* p, const double* q, int n, double& a, double& c) {
-  __shared__ double s[2];
-  if (threadIdx.x < 32) {
-    const double va = reduce_partials(p, n, threadIdx.x);
-    const double vc = reduce_partials(q, n, threadIdx.x);
-    if (threadIdx.x == 0) {
-      s[0] = va;
-      s[1] = vc;
-    }
+// Fixed-order sums of the per-item partial arrays [first, last) (each of n
+// values, consecutive in p): warp k of every CTA sums array first + k, the CTA
+// shares the results in red[first .. last).
+__device__ __forceinline__ void reduce_arrays(const double* p, int n, int first, int last, double* red) {
+  __shared__ double s[4];
+  const int w = threadIdx.x >> 5;
+  if (w < last - first) {
+    const double v = reduce_partials(p + (size_t)(first + w) * n, n, threadIdx.x & 31);
+    if ((threadIdx.x & 31) == 0) s[first + w] = v;
   }
   __syncthreads();
-  a = s[0];
-  c = s[1];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (k >= first && k < last) red[k] = s[k];
   __syncthreads();
+}
+
+// Player to step and tau of iteration t (Alg. 1: alternate by parity, tau_t = 2/(t+3);
+// practical EGT: the player with the larger mu, same tau; EGT/as: that player, the
+// carried tau).
+__device__ __forceinline__ void choose(int variant, int t, double mu0, double mu1, double tau_as, int& me,
+                                       double& tau) {
+  if (variant == EGT_THEORY) {
+    me = t % 2 == 0 ? 0 : 1;
+    tau = 2.0 / (t + 3);
+  } else {
+    me = mu0 > mu1 ? 0 : 1;
+    tau = variant == EGT_PRACTICAL ? 2.0 / (t + 3) : tau_as;
+  }
 }
 
 __global__ void __launch_bounds__(kItemThreads, 1)
@@ -211,13 +242,16 @@ __global__ void __launch_bounds__(kItemThreads, 1)
   PhaseClock* clk = &clk_s;
   if (threadIdx.x == 0) {
     clk->last = global_ns();
+    clk->arrive = clk->last;
     for (int k = 0; k < kEnginePhases; ++k) {
       clk->ns[k] = 0;
+      clk->work[k] = 0;
       clk->n[k] = 0;
     }
   }
   const bool writer = blockIdx.x == 0 && threadIdx.x == 0;
   const int NB = g.ld / kSbrHands;
+  const int T = g.terms[0].n;
   double* partA = b.partials;
   double* partB = b.partials + NB;
   double* partBR0 = b.partials + 2 * NB;
@@ -232,21 +266,19 @@ __global__ void __launch_bounds__(kItemThreads, 1)
   int done = 0, backoffs_total = 0, products = 0, gap_checks = 0, reached = 0, status = 0;
   int last_player = -1, last_backoffs = 0;
   double last_tau = 0.0 / 0.0, last_egv = 0.0 / 0.0;
+  // v_hat of the coming iteration already computed (speculatively, in the previous
+  // iteration's last phases, on the assumption that its step is accepted)
+  bool pre = false;
 
   for (int it = 0; it < n_iters && status == 0; ++it) {
     const int nxt = 1 - cur;
     int me;
     double tau;
-    if (variant == EGT_THEORY) {
-      me = t % 2 == 0 ? 0 : 1;
-      tau = 2.0 / (t + 3);
-    } else {
-      me = mu0 > mu1 ? 0 : 1;
-      tau = variant == EGT_PRACTICAL ? 2.0 / (t + 3) : tau_as;
-    }
+    choose(variant, t, mu0, mu1, tau_as, me, tau);
     const bool check = variant == EGT_AS;
-    int backoffs = 0;
+    int backoffs = 0, spec = 0;
     double egv = 0.0 / 0.0;
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
     // Alg. 2 Step focused on `me` (the y-focused step swaps roles, A -> -A^T)
     const int ot = 1 - me;
     const bool xs = me == 0;
@@ -269,62 +301,89 @@ __global__ void __launch_bounds__(kItemThreads, 1)
     float* t_ot = xs ? b.ty : b.tx;
     const double mu_me = xs ? mu0 : mu1, mu_ot = xs ? mu1 : mu0;
     // the residual of the new point is due: the Step's products of y_+ and x_+ also
-    // write their FP64 copies, and the best responses run with the EGV phase
+    // write their FP64 copies, and the best responses run in the last phase
     const bool gap_due = (t + 1) % gap_every == 0 || t + 1 >= max_t;
+    const bool tail = check || gap_due;              // a phase after the Step's last product
     double* g64_me = gap_due ? (xs ? b.g64[0] : b.g64[1]) : nullptr;
     double* g64_ot = gap_due ? (xs ? b.g64[1] : b.g64[0]) : nullptr;
     for (;;) {
       // v_hat = (1 - tau) v + tau v_mu(other)
-      run_sbr(g, tb, me, g_me, mu_me, v_me, tau, t_me, nullptr, sm);
-      if (!grid_sync(bar, bk)) return;
-      phase_mark(clk, 0);
+      if (!pre) {
+        run_sbr(g, tb, me, g_me, mu_me, v_me, tau, t_me, nullptr, sm);
+        if (!phase_end(bar, bk, clk, 0)) return;
+      }
+      pre = false;
       run_grad(g, tb, ot, t_me, t_ot, nullptr, sm);         // the other's loss gradient at v_hat
-      if (!grid_sync(bar, bk)) return;
-      phase_mark(clk, 1);
+      if (!phase_end(bar, bk, clk, 1)) return;
       // other_+ = (1 - tau) other + tau other_mu(v_hat)
       run_sbr(g, tb, ot, t_ot, mu_ot, v_ot, tau, v_ot_n, nullptr, sm);
-      if (!grid_sync(bar, bk)) return;
-      phase_mark(clk, 2);
+      if (!phase_end(bar, bk, clk, 2)) return;
       run_grad(g, tb, me, v_ot_n, g_me_n, g64_me, sm);      // my loss gradient at other_+
-      if (!grid_sync(bar, bk)) return;
-      phase_mark(clk, 3);
+      if (!phase_end(bar, bk, clk, 3)) return;
       // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part
       run_sbr(g, tb, me, g_me_n, (1 - tau) * mu_me, v_me, tau, v_me_n, partA, sm);
-      if (!grid_sync(bar, bk)) return;
-      phase_mark(clk, 4);
-      run_grad(g, tb, ot, v_me_n, g_ot_n, g64_ot, sm);      // the other's loss gradient at v_+
-      if (!grid_sync(bar, bk)) return;
-      phase_mark(clk, 5);
-      products += 3;
-      if (!check) break;
+      if (!phase_end(bar, bk, clk, 4)) return;
+      // The next iteration's choice if this step is accepted, and its v_hat computed
+      // ahead: with the last product when the same player steps again (its gradient
+      // and iterate are final here), else in the last phase, from the same smoothed
+      // best response as the other's EGV part (same gradient, same mu).
+      int me2;
+      double tau2;
+      choose(variant, t + 1, xs ? (1 - tau) * mu0 : mu0, xs ? mu1 : (1 - tau) * mu1, tau, me2, tau2);
+      spec = me2 == me ? 1 : (tail ? 2 : 0);
       {
-        // the other's EGV part (items [0, NB)) and, when due, the residual's best
-        // responses (items [NB, 3 NB)) in one phase
-        const TpxTab tp = pick(tb, ot);
-        const int n_items = gap_due ? 3 * NB : NB;
+        const int n_items = T + (spec == 1 ? NB : 0);
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-          if (item < NB) {
+          if (item < T) {
+            term_item<float>(g, tb.grad, ot, item, v_me_n, g_ot_n, g64_ot, sm);   // the other's at v_+
+          } else {
+            SbrItemArgs a;
+            a.g = g_me_n;
+            a.gptr = me ? g.terms[1].ptr : g.terms[0].ptr;
+            a.grz = me ? g.rz[1] : g.rz[0];
+            a.sign = me == 0 ? 1.f : -1.f;
+            a.mu = (1 - tau) * mu_me;
+            a.old = v_me_n;
+            a.tau = (float)tau2;
+            a.out = t_me;
+            a.value_partial = nullptr;
+            sbr_item(g, pick(tb, me), item - T, a, reinterpret_cast<float*>(sm));
+          }
+        }
+      }
+      if (!phase_end(bar, bk, clk, 5)) return;
+      products += 3;
+      if (!tail) break;
+      {
+        // the other's EGV part and / or the next v_hat (items [0, NB)), the residual's
+        // best responses when due (the following 2 NB items)
+        const int n_sbr = check || spec == 2 ? NB : 0;
+        const int n_items = n_sbr + (gap_due ? 2 * NB : 0);
+        const TpxTab tp = pick(tb, ot);
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+          if (item < n_sbr) {
             SbrItemArgs a;
             a.g = g_ot_n;
             a.gptr = ot ? g.terms[1].ptr : g.terms[0].ptr;
             a.grz = ot ? g.rz[1] : g.rz[0];
             a.sign = ot == 0 ? 1.f : -1.f;
             a.mu = mu_ot;
-            a.old = nullptr;
-            a.tau = 0.f;
-            a.out = nullptr;
-            a.value_partial = partB + item;
+            a.old = spec == 2 ? v_ot_n : nullptr;
+            a.tau = spec == 2 ? (float)tau2 : 0.f;
+            a.out = spec == 2 ? t_ot : nullptr;
+            a.value_partial = check ? partB + item : nullptr;
             sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
           } else {
-            run_br_items(g, tb, item - NB, NB, b, partBR0, partBR1, sm);
+            run_br_items(g, tb, item - n_sbr, NB, b, partBR0, partBR1, sm);
           }
         }
       }
-      if (!grid_sync(bar, bk)) return;
-      phase_mark(clk, 6);
-      double a, c;
-      reduce_pair(partA, partB, NB, a, c);
-      const double phi = xs ? a : c, negf = xs ? c : a;
+      if (!phase_end(bar, bk, clk, 6)) return;
+      // the EGV parts (partA, partB) and the residual's values (partBR0, partBR1) in one pass
+      reduce_arrays(b.partials, NB, check ? 0 : 2, gap_due ? 4 : 2, red);
+      phase_cut(clk, 7);
+      if (!check) break;
+      const double phi = xs ? red[0] : red[1], negf = xs ? red[1] : red[0];
       egv = phi + negf;
       if (!isfinite(egv)) {
         status = EGT_ERR_NUMERIC;
@@ -362,19 +421,11 @@ __global__ void __launch_bounds__(kItemThreads, 1)
     last_backoffs = backoffs;
     last_tau = tau;
     last_egv = egv;
+    pre = spec != 0;
     if (gap_due) {
-      // eps_sad of the new iterates from the FP64 products of the Step; the best
-      // responses already ran with the EGV phase under EGT/as, otherwise here
-      if (!check) {
-        for (int item = blockIdx.x; item < 2 * NB; item += gridDim.x)
-          run_br_items(g, tb, item, NB, b, partBR0, partBR1, sm);
-        if (!grid_sync(bar, bk)) return;
-      }
-      double vmin, vmax;
-      reduce_pair(partBR0, partBR1, NB, vmin, vmax);
-      gap = (vmax - vmin) / bb * 1000.0;
+      // eps_sad of the new iterates from the FP64 products of the Step
+      gap = (red[3] - red[2]) / bb * 1000.0;   // max_y <y, A^T x> - min_x <x, A y>
       gap_checks += 1;
-      phase_mark(clk, 10);
       if (!isfinite(gap)) {
         status = EGT_ERR_NUMERIC;
         break;
@@ -404,6 +455,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
 #pragma unroll
     for (int k = 0; k < kEnginePhases; ++k) {
       ctl->phase_ns[k] = clk->ns[k];
+      ctl->phase_work_ns[k] = clk->work[k];
       ctl->phase_n[k] = clk->n[k];
     }
   }

@@ -8,10 +8,11 @@
 namespace egt {
 
 // Phases of an iteration timed by the engine (egt_engine_trace): the Step's
-// three SBR and three product phases, the EGV SBR (with the EGV decision), two
-// slots kept for compatibility (0 now: those barriers are gone), the residual's
-// FP64 products, its FP64 best responses (with the gap decision).
-constexpr int kEnginePhases = 11;
+// three SBR and three product phases (the last one may carry the next v_hat), and
+// the last phase (the other's EGV part, the residual's FP64 best responses, the
+// next v_hat when the other player steps next), then CTA 0's time on the sums
+// behind the EGV and residual decisions (no barrier).
+constexpr int kEnginePhases = 8;
 
 // Control block in device memory, one per game.  The host writes the
 // configuration and the solver state before a launch and reads everything back
@@ -32,6 +33,7 @@ struct EngineCtl {
   unsigned long long bar_arrive;
   // device time per phase (CTA 0, between consecutive barrier exits), ns
   unsigned long long phase_ns[kEnginePhases];
+  unsigned long long phase_work_ns[kEnginePhases];   // CTA 0's own work (to its barrier arrival)
   unsigned long long phase_n[kEnginePhases];
 };
 

@@ -98,7 +98,7 @@ _SIGS = {
     "egt_state_gap": [_vp, C.POINTER(_f64), _vp],
     "egt_gap_noalloc": [_vp, _vp, _vp, C.POINTER(_f64), _vp],
     "egt_iterate": [_vp, C.POINTER(SolveOpts), _i32, C.POINTER(SolveReport), _vp],
-    "egt_engine_trace": [_vp, _i32, _vp, _vp],
+    "egt_engine_trace": [_vp, _i32, _vp, _vp, _vp],
     "egt_profile": [_vp, _i32],
     "egt_profile_read": [_vp, _vp, _vp],
 }
@@ -307,15 +307,21 @@ class Game:
         m = (C.c_double * 2)(*mu)
         _check(lib.egt_state_set(self._h, _ptr(x), _ptr(y), C.cast(m, C.c_void_p), _stream(stream)))
 
-    ENGINE_PHASES = ("sbr_hat", "grad_1", "sbr_other", "grad_2", "sbr_tilde", "grad_3",
-                     "sbr_egv", "egv_decision", "accept", "gap_grad_f64", "gap_br_f64")
+    ENGINE_PHASES = ("sbr_hat", "grad_1", "sbr_other", "grad_2", "sbr_tilde", "grad_3", "tail",
+                     "decisions")
 
     def engine_trace(self, reset=True):
-        us = np.zeros(len(self.ENGINE_PHASES), np.float64)
-        n = np.zeros(len(self.ENGINE_PHASES), np.int64)
-        _check(lib.egt_engine_trace(self._h, int(reset), us.ctypes.data, n.ctypes.data))
-        return {k: dict(us=float(us[i]), n=int(n[i]), avg_us=float(us[i] / n[i]) if n[i] else 0.0)
-                for i, k in enumerate(self.ENGINE_PHASES)}
+        """Per-phase device time of the device-resident driver: total (us), CTA 0's
+        own work (work_us), phases timed (n), average per phase (avg_us)."""
+        k = len(self.ENGINE_PHASES)
+        us = np.zeros(k, np.float64)
+        work = np.zeros(k, np.float64)
+        n = np.zeros(k, np.int64)
+        _check(lib.egt_engine_trace(self._h, int(reset), us.ctypes.data, work.ctypes.data, n.ctypes.data))
+        return {name: dict(us=float(us[i]), work_us=float(work[i]), n=int(n[i]),
+                           avg_us=float(us[i] / n[i]) if n[i] else 0.0,
+                           avg_work_us=float(work[i] / n[i]) if n[i] else 0.0)
+                for i, name in enumerate(self.ENGINE_PHASES)}
 
     def profile(self, enable):
         _check(lib.egt_profile(self._h, int(enable)))
