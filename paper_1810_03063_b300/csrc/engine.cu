@@ -154,7 +154,7 @@ __device__ __forceinline__ TpxTab pick(const Tabs& tb, int p) {
 // One SBR phase: all 32-hand items of `player`, spread over the CTAs; gv holds the
 // player's terminal contributions (or is NULL).
 __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int player, const float* gv,
-                                        double mu, const float* old, double tau, float* out,
+                                        double mu, const float* old, float tau, float* out,
                                         double* partials, unsigned char* sm) {
   const int NB = g.ld / kSbrHands;
   const TpxTab tp = pick(tb, player);
@@ -166,7 +166,7 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int pl
     a.sign = player == 0 ? 1.f : -1.f;
     a.mu = mu;
     a.old = old;
-    a.tau = (float)tau;
+    a.tau = tau;
     a.out = out;
     a.value_partial = partials ? partials + item : nullptr;
     sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
@@ -226,6 +226,18 @@ __device__ __forceinline__ void choose(int variant, int t, double mu0, double mu
   }
 }
 
+// Decisions of the current attempt, written by thread 0 of the CTA (the only
+// thread that runs the solver's FP64 bookkeeping: FP64 is a narrow pipe on this
+// part, and 512 redundant copies of it cost microseconds per iteration) and read
+// by all threads after a CTA barrier.
+struct Sched {
+  int stop;             // leave the iteration loop
+  int cur, me, gap_due, spec, pre;
+  float tau, tau2;      // this attempt's tau, the next iteration's (FP32, for the mixing)
+  double mu_me, mu_ot;  // mu of the stepping player and of the other
+  double mu_tilde;      // (1 - tau) mu_me
+};
+
 __global__ void __launch_bounds__(kItemThreads, 1)
     engine_kernel(DevGame g, EngineBufs b, EngineCtl* ctl, unsigned long long expected,
                   unsigned long long limit_ns) {
@@ -234,13 +246,15 @@ __global__ void __launch_bounds__(kItemThreads, 1)
   tb.grad = stage_grad_tab(g, smem_all);
   tb.tpx[0] = stage_tpx_tab(g, 0, smem_all + grad_tab_bytes(g));
   tb.tpx[1] = stage_tpx_tab(g, 1, smem_all + grad_tab_bytes(g) + tpx_tab_bytes(g, 0));
-  __syncthreads();
+  // (the tables are first read after the CTA barrier at the top of the iteration loop)
   unsigned char* sm = smem_all + tabs_bytes(g);   // per-phase working area
   const GridBar bar{&ctl->bar_arrive, &ctl->status, expected, limit_ns};
   unsigned long long bk = 0;                      // barriers passed by this CTA
   __shared__ PhaseClock clk_s;
+  __shared__ Sched sc;
   PhaseClock* clk = &clk_s;
-  if (threadIdx.x == 0) {
+  const bool lead = threadIdx.x == 0;
+  if (lead) {
     clk->last = global_ns();
     clk->arrive = clk->last;
     for (int k = 0; k < kEnginePhases; ++k) {
@@ -249,7 +263,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
       clk->n[k] = 0;
     }
   }
-  const bool writer = blockIdx.x == 0 && threadIdx.x == 0;
+  const bool writer = blockIdx.x == 0 && lead;
   const int NB = g.ld / kSbrHands;
   const int T = g.terms[0].n;
   double* partA = b.partials;
@@ -258,38 +272,77 @@ __global__ void __launch_bounds__(kItemThreads, 1)
   double* partBR1 = b.partials + 3 * NB;
   const int variant = ctl->variant, n_iters = ctl->n_iters, gap_every = ctl->gap_every;
   const int max_t = ctl->max_t;
-  const double eps_mbb = ctl->eps_mbb, bb = ctl->bb;
+  const bool check = variant == EGT_AS;
 
-  // solver state, identical in every CTA
-  int t = ctl->t, cur = ctl->cur;
-  double mu0 = ctl->mu[0], mu1 = ctl->mu[1], tau_as = ctl->tau, gap = ctl->gap_mbb;
-  int done = 0, backoffs_total = 0, products = 0, gap_checks = 0, reached = 0, status = 0;
-  int last_player = -1, last_backoffs = 0;
-  double last_tau = 0.0 / 0.0, last_egv = 0.0 / 0.0;
-  // v_hat of the coming iteration already computed (speculatively, in the previous
-  // iteration's last phases, on the assumption that its step is accepted)
-  bool pre = false;
+  // solver state: meaningful in thread 0 only (identical in every CTA)
+  int t = 0, cur = 0, done = 0, backoffs_total = 0, products = 0, gap_checks = 0, reached = 0;
+  int status = 0, last_player = -1, last_backoffs = 0, it = 0, me = 0, backoffs = 0, spec = 0;
+  double mu0 = 0, mu1 = 0, tau_as = 0, gap = 0, tau = 0, eps_mbb = 0, bb = 1;
+  double last_tau = 0.0 / 0.0, last_egv = 0.0 / 0.0, egv = 0.0 / 0.0;
+  bool pre = false;        // v_hat of this iteration already computed (ahead, by the previous one)
+  bool new_iter = true;    // the next attempt starts an iteration (else it retries with tau / 2)
+  if (lead) {
+    t = ctl->t;
+    cur = ctl->cur;
+    mu0 = ctl->mu[0];
+    mu1 = ctl->mu[1];
+    tau_as = ctl->tau;
+    gap = ctl->gap_mbb;
+    eps_mbb = ctl->eps_mbb;
+    bb = ctl->bb;
+  }
 
-  for (int it = 0; it < n_iters && status == 0; ++it) {
-    const int nxt = 1 - cur;
-    int me;
-    double tau;
-    choose(variant, t, mu0, mu1, tau_as, me, tau);
-    const bool check = variant == EGT_AS;
-    int backoffs = 0, spec = 0;
-    double egv = 0.0 / 0.0;
-    double red[4] = {0.0, 0.0, 0.0, 0.0};
-    // Alg. 2 Step focused on `me` (the y-focused step swaps roles, A -> -A^T)
-    const int ot = 1 - me;
-    const bool xs = me == 0;
-    float* xc = cur ? b.x[1] : b.x[0];
-    float* xn = cur ? b.x[0] : b.x[1];
-    float* yc = cur ? b.y[1] : b.y[0];
-    float* yn = cur ? b.y[0] : b.y[1];
-    float* gxc = cur ? b.gx[1] : b.gx[0];
-    float* gxn = cur ? b.gx[0] : b.gx[1];
-    float* gyc = cur ? b.gy[1] : b.gy[0];
-    float* gyn = cur ? b.gy[0] : b.gy[1];
+  for (;;) {
+    if (lead) {
+      int stop = !(it < n_iters && status == 0) || (it > 0 && new_iter && (reached || t >= max_t));
+      if (!stop) {
+        if (new_iter) {
+          choose(variant, t, mu0, mu1, tau_as, me, tau);
+          backoffs = 0;
+          egv = 0.0 / 0.0;
+        }
+        const bool xs = me == 0;
+        const int gap_due = (t + 1) % gap_every == 0 || t + 1 >= max_t;
+        // The next iteration's choice if this attempt is accepted, and its v_hat computed
+        // ahead: with the last product when the same player steps again (its gradient and
+        // iterate are final there), else in the last phase, from the same smoothed best
+        // response as the other's EGV part (same gradient, same mu).
+        int me2;
+        double tau2;
+        choose(variant, t + 1, xs ? (1 - tau) * mu0 : mu0, xs ? mu1 : (1 - tau) * mu1, tau, me2, tau2);
+        spec = me2 == me ? 1 : (check || gap_due ? 2 : 0);
+        sc.cur = cur;
+        sc.me = me;
+        sc.gap_due = gap_due;
+        sc.spec = spec;
+        sc.pre = pre;
+        sc.tau = (float)tau;
+        sc.tau2 = (float)tau2;
+        sc.mu_me = xs ? mu0 : mu1;
+        sc.mu_ot = xs ? mu1 : mu0;
+        sc.mu_tilde = (1 - tau) * (xs ? mu0 : mu1);
+      }
+      sc.stop = stop;
+    }
+    __syncthreads();
+    if (sc.stop) break;
+    const int c = sc.cur, m = sc.me, gap_due = sc.gap_due, sp = sc.spec;
+    const bool have_hat = sc.pre != 0;
+    const float tau_f = sc.tau, tau2_f = sc.tau2;
+    const double mu_me = sc.mu_me, mu_ot = sc.mu_ot, mu_tilde = sc.mu_tilde;
+    const bool tail = check || gap_due;              // a phase after the Step's last product
+
+    // Alg. 2 Step focused on m (the y-focused step swaps roles, A -> -A^T)
+    const int ot = 1 - m;
+    const bool xs = m == 0;
+    float* xc = c ? b.x[1] : b.x[0];
+    float* xn = c ? b.x[0] : b.x[1];
+    float* yc = c ? b.y[1] : b.y[0];
+    float* yn = c ? b.y[0] : b.y[1];
+    float* gxc = c ? b.gx[1] : b.gx[0];
+    float* gxn = c ? b.gx[0] : b.gx[1];
+    float* gyc = c ? b.gy[1] : b.gy[0];
+    float* gyn = c ? b.gy[0] : b.gy[1];
     float* v_me = xs ? xc : yc;                      // my iterate
     float* v_ot = xs ? yc : xc;                      // the other's iterate
     float* v_me_n = xs ? xn : yn;
@@ -299,140 +352,135 @@ __global__ void __launch_bounds__(kItemThreads, 1)
     float* g_ot_n = xs ? gyn : gxn;
     float* t_me = xs ? b.tx : b.ty;
     float* t_ot = xs ? b.ty : b.tx;
-    const double mu_me = xs ? mu0 : mu1, mu_ot = xs ? mu1 : mu0;
     // the residual of the new point is due: the Step's products of y_+ and x_+ also
     // write their FP64 copies, and the best responses run in the last phase
-    const bool gap_due = (t + 1) % gap_every == 0 || t + 1 >= max_t;
-    const bool tail = check || gap_due;              // a phase after the Step's last product
     double* g64_me = gap_due ? (xs ? b.g64[0] : b.g64[1]) : nullptr;
     double* g64_ot = gap_due ? (xs ? b.g64[1] : b.g64[0]) : nullptr;
-    for (;;) {
-      // v_hat = (1 - tau) v + tau v_mu(other)
-      if (!pre) {
-        run_sbr(g, tb, me, g_me, mu_me, v_me, tau, t_me, nullptr, sm);
-        if (!phase_end(bar, bk, clk, 0)) return;
-      }
-      pre = false;
-      run_grad(g, tb, ot, t_me, t_ot, nullptr, sm);         // the other's loss gradient at v_hat
-      if (!phase_end(bar, bk, clk, 1)) return;
-      // other_+ = (1 - tau) other + tau other_mu(v_hat)
-      run_sbr(g, tb, ot, t_ot, mu_ot, v_ot, tau, v_ot_n, nullptr, sm);
-      if (!phase_end(bar, bk, clk, 2)) return;
-      run_grad(g, tb, me, v_ot_n, g_me_n, g64_me, sm);      // my loss gradient at other_+
-      if (!phase_end(bar, bk, clk, 3)) return;
-      // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part
-      run_sbr(g, tb, me, g_me_n, (1 - tau) * mu_me, v_me, tau, v_me_n, partA, sm);
-      if (!phase_end(bar, bk, clk, 4)) return;
-      // The next iteration's choice if this step is accepted, and its v_hat computed
-      // ahead: with the last product when the same player steps again (its gradient
-      // and iterate are final here), else in the last phase, from the same smoothed
-      // best response as the other's EGV part (same gradient, same mu).
-      int me2;
-      double tau2;
-      choose(variant, t + 1, xs ? (1 - tau) * mu0 : mu0, xs ? mu1 : (1 - tau) * mu1, tau, me2, tau2);
-      spec = me2 == me ? 1 : (tail ? 2 : 0);
-      {
-        const int n_items = T + (spec == 1 ? NB : 0);
-        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-          if (item < T) {
-            term_item<float>(g, tb.grad, ot, item, v_me_n, g_ot_n, g64_ot, sm);   // the other's at v_+
-          } else {
-            SbrItemArgs a;
-            a.g = g_me_n;
-            a.gptr = me ? g.terms[1].ptr : g.terms[0].ptr;
-            a.grz = me ? g.rz[1] : g.rz[0];
-            a.sign = me == 0 ? 1.f : -1.f;
-            a.mu = (1 - tau) * mu_me;
-            a.old = v_me_n;
-            a.tau = (float)tau2;
-            a.out = t_me;
-            a.value_partial = nullptr;
-            sbr_item(g, pick(tb, me), item - T, a, reinterpret_cast<float*>(sm));
-          }
+
+    // v_hat = (1 - tau) v + tau v_mu(other)
+    if (!have_hat) {
+      run_sbr(g, tb, m, g_me, mu_me, v_me, tau_f, t_me, nullptr, sm);
+      if (!phase_end(bar, bk, clk, 0)) return;
+    }
+    phase_cut(clk, 8);
+    run_grad(g, tb, ot, t_me, t_ot, nullptr, sm);           // the other's loss gradient at v_hat
+    if (!phase_end(bar, bk, clk, 1)) return;
+    // other_+ = (1 - tau) other + tau other_mu(v_hat)
+    run_sbr(g, tb, ot, t_ot, mu_ot, v_ot, tau_f, v_ot_n, nullptr, sm);
+    if (!phase_end(bar, bk, clk, 2)) return;
+    run_grad(g, tb, m, v_ot_n, g_me_n, g64_me, sm);         // my loss gradient at other_+
+    if (!phase_end(bar, bk, clk, 3)) return;
+    // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part
+    run_sbr(g, tb, m, g_me_n, mu_tilde, v_me, tau_f, v_me_n, partA, sm);
+    if (!phase_end(bar, bk, clk, 4)) return;
+    {
+      // the other's loss gradient at v_+, and the next v_hat when the same player steps
+      const int n_items = T + (sp == 1 ? NB : 0);
+      for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        if (item < T) {
+          term_item<float>(g, tb.grad, ot, item, v_me_n, g_ot_n, g64_ot, sm);
+        } else {
+          SbrItemArgs a;
+          a.g = g_me_n;
+          a.gptr = m ? g.terms[1].ptr : g.terms[0].ptr;
+          a.grz = m ? g.rz[1] : g.rz[0];
+          a.sign = m == 0 ? 1.f : -1.f;
+          a.mu = mu_tilde;
+          a.old = v_me_n;
+          a.tau = tau2_f;
+          a.out = t_me;
+          a.value_partial = nullptr;
+          sbr_item(g, pick(tb, m), item - T, a, reinterpret_cast<float*>(sm));
         }
       }
-      if (!phase_end(bar, bk, clk, 5)) return;
-      products += 3;
-      if (!tail) break;
-      {
-        // the other's EGV part and / or the next v_hat (items [0, NB)), the residual's
-        // best responses when due (the following 2 NB items)
-        const int n_sbr = check || spec == 2 ? NB : 0;
-        const int n_items = n_sbr + (gap_due ? 2 * NB : 0);
-        const TpxTab tp = pick(tb, ot);
-        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-          if (item < n_sbr) {
-            SbrItemArgs a;
-            a.g = g_ot_n;
-            a.gptr = ot ? g.terms[1].ptr : g.terms[0].ptr;
-            a.grz = ot ? g.rz[1] : g.rz[0];
-            a.sign = ot == 0 ? 1.f : -1.f;
-            a.mu = mu_ot;
-            a.old = spec == 2 ? v_ot_n : nullptr;
-            a.tau = spec == 2 ? (float)tau2 : 0.f;
-            a.out = spec == 2 ? t_ot : nullptr;
-            a.value_partial = check ? partB + item : nullptr;
-            sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
-          } else {
-            run_br_items(g, tb, item - n_sbr, NB, b, partBR0, partBR1, sm);
-          }
+    }
+    if (!phase_end(bar, bk, clk, 5)) return;
+    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    if (tail) {
+      // the other's EGV part and / or the next v_hat (items [0, NB)), the residual's
+      // best responses when due (the following 2 NB items)
+      const int n_sbr = check || sp == 2 ? NB : 0;
+      const int n_items = n_sbr + (gap_due ? 2 * NB : 0);
+      const TpxTab tp = pick(tb, ot);
+      for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        if (item < n_sbr) {
+          SbrItemArgs a;
+          a.g = g_ot_n;
+          a.gptr = ot ? g.terms[1].ptr : g.terms[0].ptr;
+          a.grz = ot ? g.rz[1] : g.rz[0];
+          a.sign = ot == 0 ? 1.f : -1.f;
+          a.mu = mu_ot;
+          a.old = sp == 2 ? v_ot_n : nullptr;
+          a.tau = sp == 2 ? tau2_f : 0.f;
+          a.out = sp == 2 ? t_ot : nullptr;
+          a.value_partial = check ? partB + item : nullptr;
+          sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
+        } else {
+          run_br_items(g, tb, item - n_sbr, NB, b, partBR0, partBR1, sm);
         }
       }
       if (!phase_end(bar, bk, clk, 6)) return;
       // the EGV parts (partA, partB) and the residual's values (partBR0, partBR1) in one pass
       reduce_arrays(b.partials, NB, check ? 0 : 2, gap_due ? 4 : 2, red);
       phase_cut(clk, 7);
-      if (!check) break;
-      const double phi = xs ? red[0] : red[1], negf = xs ? red[1] : red[0];
-      egv = phi + negf;
-      if (!isfinite(egv)) {
-        status = EGT_ERR_NUMERIC;
-        break;
-      }
-      if (egv >= 0) break;
-      tau *= 0.5;
-      if (tau < 1.0 / (1u << 30)) {
-        status = EGT_ERR_TAU_UNDERFLOW;
-        break;
-      }
-      ++backoffs;
     }
-    if (status != 0) break;
-    // accept (Alg. 2 last lines): mu_me^+ = (1 - tau) mu_me, swap the iterate buffers
-    if (xs) mu0 *= (1.0 - tau);
-    else mu1 *= (1.0 - tau);
-    if (variant == EGT_AS) tau_as = tau;
-    if (writer && b.log != nullptr && it < b.log_cap) {
-      egt_iter_log& L = b.log[it];
-      L.t = t;
-      L.player = me;
-      L.backoffs = backoffs;
-      L.tau = tau;
-      L.mu[0] = mu0;
-      L.mu[1] = mu1;
-      L.egv = check ? egv : 0.0 / 0.0;
-      L.gap_mbb = gap;
-    }
-    cur = nxt;
-    t += 1;
-    backoffs_total += backoffs;
-    done += 1;
-    last_player = me;
-    last_backoffs = backoffs;
-    last_tau = tau;
-    last_egv = egv;
-    pre = spec != 0;
-    if (gap_due) {
-      // eps_sad of the new iterates from the FP64 products of the Step
-      gap = (red[3] - red[2]) / bb * 1000.0;   // max_y <y, A^T x> - min_x <x, A y>
-      gap_checks += 1;
-      if (!isfinite(gap)) {
-        status = EGT_ERR_NUMERIC;
-        break;
+
+    if (lead) {
+      products += 3;
+      bool accept = true;
+      if (check) {
+        const double phi = xs ? red[0] : red[1], negf = xs ? red[1] : red[0];
+        egv = phi + negf;
+        if (!isfinite(egv)) {
+          status = EGT_ERR_NUMERIC;
+          accept = false;
+        } else if (egv < 0) {
+          accept = false;
+          tau *= 0.5;
+          if (tau < 1.0 / (1u << 30)) status = EGT_ERR_TAU_UNDERFLOW;
+          else ++backoffs;
+        }
       }
-      reached = eps_mbb > 0 && gap <= eps_mbb ? 1 : 0;
+      if (accept) {
+        // accept (Alg. 2 last lines): mu_me^+ = (1 - tau) mu_me, swap the iterate buffers
+        if (xs) mu0 *= (1.0 - tau);
+        else mu1 *= (1.0 - tau);
+        if (variant == EGT_AS) tau_as = tau;
+        if (writer && b.log != nullptr && it < b.log_cap) {
+          egt_iter_log& L = b.log[it];
+          L.t = t;
+          L.player = me;
+          L.backoffs = backoffs;
+          L.tau = tau;
+          L.mu[0] = mu0;
+          L.mu[1] = mu1;
+          L.egv = check ? egv : 0.0 / 0.0;
+          L.gap_mbb = gap;
+        }
+        cur = 1 - cur;
+        t += 1;
+        backoffs_total += backoffs;
+        done += 1;
+        last_player = me;
+        last_backoffs = backoffs;
+        last_tau = tau;
+        last_egv = egv;
+        pre = spec != 0;
+        if (gap_due) {
+          // eps_sad of the new iterates from the FP64 products of the Step:
+          // max_y <y, A^T x> - min_x <x, A y>
+          gap = (red[3] - red[2]) / bb * 1000.0;
+          gap_checks += 1;
+          if (!isfinite(gap)) status = EGT_ERR_NUMERIC;
+          else reached = eps_mbb > 0 && gap <= eps_mbb ? 1 : 0;
+        }
+        it += 1;
+        new_iter = true;
+      } else {
+        pre = false;
+        new_iter = false;
+      }
     }
-    if (reached || t >= max_t) break;
   }
 
   if (writer) {

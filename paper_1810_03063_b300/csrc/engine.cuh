@@ -12,7 +12,7 @@ namespace egt {
 // the last phase (the other's EGV part, the residual's FP64 best responses, the
 // next v_hat when the other player steps next), then CTA 0's time on the sums
 // behind the EGV and residual decisions (no barrier).
-constexpr int kEnginePhases = 8;
+constexpr int kEnginePhases = 9;
 
 // Control block in device memory, one per game.  The host writes the
 // configuration and the solver state before a launch and reads everything back

@@ -66,28 +66,6 @@ __device__ __forceinline__ double pow2d(int e) {
   return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// int64 -> float rounded to nearest even (leading-zero count and shifts)
-__device__ __forceinline__ float i64_to_f32(long long v) {
-  if (v == 0) return 0.f;
-  const unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-  const int nb = 64 - __clzll(u);
-  float f;
-  if (nb <= 24) {
-    f = __uint2float_rn((unsigned)u);
-  } else {
-    int sh = nb - 24;
-    unsigned long long mant = u >> sh;
-    const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
-    if (mant == (1ull << 24)) {
-      mant >>= 1;
-      ++sh;
-    }
-    f = __int_as_float(((127 + 23 + sh) << 23) | (int)(mant & 0x7fffffull));
-  }
-  return v < 0 ? -f : f;
-}
-
 // floor(P / 2^k) of the 128-bit P = hi:lo, low 64 bits
 __device__ __forceinline__ unsigned long long shr128(unsigned long long hi, unsigned long long lo, int k) {
   if (k <= 0) return lo;
@@ -173,17 +151,90 @@ __device__ __forceinline__ Fx to_fx(const WBits& w, int ex) {
 // scale so that |w| 2^ex < 2^48 for the largest |w| (sums of 2048 terms < 2^59)
 __device__ __forceinline__ int scale_of(int maxlg) { return maxlg == INT_MIN ? 0 : 47 - maxlg; }
 
-// FP32 value of a fixed-point sum (fraction rounded into the integer part)
-__device__ __forceinline__ float fx_to_f32(Fx a, int ex) {
-  const long long v = a.v0 + ((a.v1 + (1ll << 39)) >> 40);
-  const int e1 = ex >> 1;
-  return i64_to_f32(v) * pow2f(-e1) * pow2f(e1 - ex);
+// |N| of a fixed-point sum, N = v0 2^40 + v1 as a signed 128-bit integer
+// (uh:ul), its sign and bit length (0 when N = 0).
+struct Wide {
+  unsigned long long uh, ul;
+  int nb, neg;
+};
+
+__device__ __forceinline__ Wide fx_wide(Fx a) {
+  unsigned long long lo = (unsigned long long)a.v0 << 40;
+  long long hi = a.v0 >> 24;
+  const unsigned long long lo2 = lo + (unsigned long long)a.v1;
+  hi += (a.v1 < 0 ? -1 : 0) + (lo2 < lo ? 1 : 0);
+  lo = lo2;
+  Wide w;
+  w.neg = hi < 0;
+  w.uh = (unsigned long long)hi;
+  w.ul = lo;
+  if (w.neg) {
+    w.ul = ~w.ul + 1ull;
+    w.uh = ~w.uh + (w.ul == 0 ? 1ull : 0ull);
+  }
+  w.nb = w.uh ? 128 - __clzll(w.uh) : (w.ul ? 64 - __clzll(w.ul) : 0);
+  return w;
 }
 
+// The leading P bits of |N| (nb >= 1, 1 <= P <= 53) rounded to nearest even:
+// the mantissa in [2^(P-1), 2^P]; a carry to 2^P is left to the caller.
+__device__ __forceinline__ unsigned long long round_top(const Wide& w, int P) {
+  if (w.nb <= P) return w.ul << (P - w.nb);
+  const int sh = w.nb - P;
+  const unsigned long long mant = shr128(w.uh, w.ul, sh);
+  const int rb = sh - 1;                                     // position of the rounding bit
+  const unsigned long long round = rb < 64 ? (w.ul >> rb) & 1ull : (w.uh >> (rb - 64)) & 1ull;
+  bool sticky;
+  if (rb == 0) sticky = false;
+  else if (rb < 64) sticky = (w.ul & ((1ull << rb) - 1ull)) != 0;
+  else if (rb == 64) sticky = w.ul != 0;
+  else sticky = w.ul != 0 || (w.uh & ((1ull << (rb - 64)) - 1ull)) != 0;
+  return mant + ((round && (sticky || (mant & 1ull))) ? 1ull : 0ull);
+}
+
+// |N| 2^s (N from fx_wide) correctly rounded to a binary format with P-bit
+// significands, minimum normal exponent emin and bias `bias`: the magnitude's
+// bit pattern (exponent field << (P - 1) | fraction), or the all-ones exponent
+// field (infinity) on overflow.
+__device__ __forceinline__ unsigned long long fx_round(const Wide& w, int s, int P, int emin, int emax) {
+  const int e0 = w.nb - 1 + s;                                // exponent of the leading bit
+  if (e0 > emax) return (unsigned long long)(emax - emin + 2) << (P - 1);
+  if (e0 >= emin) {
+    unsigned long long mant = round_top(w, P);
+    int e = e0;
+    if (mant >> P) {
+      mant >>= 1;
+      ++e;
+    }
+    if (e > emax) return (unsigned long long)(emax - emin + 2) << (P - 1);
+    return ((unsigned long long)(e - emin + 1) << (P - 1)) | (mant & ((1ull << (P - 1)) - 1ull));
+  }
+  // subnormal: P - (emin - e0) significant bits remain
+  const int q = P - (emin - e0);
+  if (q < 0) return 0;
+  if (q == 0) {   // |value| in [min subnormal / 2, min subnormal): rounds up unless exactly half
+    const bool above = w.nb >= 2 && (w.nb - 1 >= 64 ? (w.ul != 0 || (w.uh & ((1ull << (w.nb - 65)) - 1ull)) != 0)
+                                                    : (w.ul & ((1ull << (w.nb - 1)) - 1ull)) != 0);
+    return above ? 1ull : 0ull;
+  }
+  return round_top(w, q);   // a carry to 2^q lands on the smallest normal, as it should
+}
+
+// FP32 value of a fixed-point sum, a x 2^-ex correctly rounded (all 87 bits of
+// the sum count, not only its integer part), with integer operations.
+__device__ __forceinline__ float fx_to_f32(Fx a, int ex) {
+  const Wide w = fx_wide(a);
+  if (w.nb == 0) return 0.f;
+  const unsigned bits = (unsigned)fx_round(w, -40 - ex, 24, -126, 127);
+  return __uint_as_float(((unsigned)w.neg << 31) | bits);
+}
+
+// FP64 value of a fixed-point sum, a x 2^-ex correctly rounded, with integer operations.
 __device__ __forceinline__ double fx_to_f64(Fx a, int ex) {
-  const double s = (double)a.v0 + (double)a.v1 * (1.0 / 1099511627776.0);
-  const int e1 = ex >> 1;
-  return s * pow2d(-e1) * pow2d(e1 - ex);
+  const Wide w = fx_wide(a);
+  if (w.nb == 0) return 0.0;
+  const unsigned long long bits = fx_round(w, -40 - ex, 53, -1022, 1023);
+  return __longlong_as_double((long long)(((unsigned long long)w.neg << 63) | bits));
 }
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -367,6 +418,14 @@ __device__ __forceinline__ double product64(const double* c, const int* ptr, int
   double acc = 0.0;
   for (int e = ptr[s]; e < ptr[s + 1]; ++e) acc += __ldcg(c + (size_t)e * ld + h);
   return rz * acc;
+}
+
+// -product64 (the negation folds into the multiply)
+__device__ __forceinline__ double neg_product64(const double* c, const int* ptr, int s, int ld, int h,
+                                                double rz) {
+  double acc = 0.0;
+  for (int e = ptr[s]; e < ptr[s + 1]; ++e) acc += __ldcg(c + (size_t)e * ld + h);
+  return (-rz) * acc;
 }
 
 }  // namespace egt

@@ -219,8 +219,13 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
     const int s = idx / kSbrHands, l = idx % kSbrHands;
     const int hh = h0 + l;
     double v = 0.0;
-    if (hh < g.H) v = gptr != nullptr ? product64(gv, gptr, s, ld, hh, grz[hh]) : __ldcg(gv + (size_t)s * ld + hh);
-    G[idx] = sign * v;
+    if (hh < g.H) {
+      if (gptr != nullptr)
+        v = sign < 0 ? neg_product64(gv, gptr, s, ld, hh, grz[hh]) : product64(gv, gptr, s, ld, hh, grz[hh]);
+      else
+        v = sign < 0 ? -__ldcg(gv + (size_t)s * ld + hh) : __ldcg(gv + (size_t)s * ld + hh);
+    }
+    G[idx] = v;
   }
   __syncthreads();
   for (int l = tp.L - 1; l >= 0; --l) {

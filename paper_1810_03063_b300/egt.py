@@ -308,7 +308,7 @@ class Game:
         _check(lib.egt_state_set(self._h, _ptr(x), _ptr(y), C.cast(m, C.c_void_p), _stream(stream)))
 
     ENGINE_PHASES = ("sbr_hat", "grad_1", "sbr_other", "grad_2", "sbr_tilde", "grad_3", "tail",
-                     "decisions")
+                     "decisions", "top")
 
     def engine_trace(self, reset=True):
         """Per-phase device time of the device-resident driver: total (us), CTA 0's
