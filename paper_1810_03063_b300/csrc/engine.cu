@@ -148,6 +148,7 @@ __device__ __forceinline__ TpxTab pick(const Tabs& tb, int p) {
   t.inf_parent = p ? c.inf_parent : a.inf_parent;
   t.child_ptr = p ? c.child_ptr : a.child_ptr;
   t.child_idx = p ? c.child_idx : a.child_idx;
+  t.tptr = p ? c.tptr : a.tptr;
   return t;
 }
 
@@ -161,7 +162,7 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int pl
   for (int item = blockIdx.x; item < NB; item += gridDim.x) {
     SbrItemArgs a;
     a.g = gv;
-    a.gptr = player ? g.terms[1].ptr : g.terms[0].ptr;
+    a.contrib = true;
     a.grz = player ? g.rz[1] : g.rz[0];
     a.sign = player == 0 ? 1.f : -1.f;
     a.mu = mu;
@@ -188,10 +189,10 @@ __device__ __forceinline__ void run_br_items(const DevGame& g, const Tabs& tb, i
                                              const EngineBufs& b, double* partBR0, double* partBR1,
                                              unsigned char* sm) {
   if (item < NB)
-    br64_item(g, tb.tpx[0], item, b.g64[0], g.terms[0].ptr, g.rz64[0], 1.0, partBR0 + item,
+    br64_item(g, tb.tpx[0], item, b.g64[0], true, g.rz64[0], 1.0, partBR0 + item,
               reinterpret_cast<double*>(sm));
   else
-    br64_item(g, tb.tpx[1], item - NB, b.g64[1], g.terms[1].ptr, g.rz64[1], -1.0, partBR1 + item - NB,
+    br64_item(g, tb.tpx[1], item - NB, b.g64[1], true, g.rz64[1], -1.0, partBR1 + item - NB,
               reinterpret_cast<double*>(sm));
 }
 
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
         } else {
           SbrItemArgs a;
           a.g = g_me_n;
-          a.gptr = m ? g.terms[1].ptr : g.terms[0].ptr;
+          a.contrib = true;
           a.grz = m ? g.rz[1] : g.rz[0];
           a.sign = m == 0 ? 1.f : -1.f;
           a.mu = mu_tilde;
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
         if (item < n_sbr) {
           SbrItemArgs a;
           a.g = g_ot_n;
-          a.gptr = ot ? g.terms[1].ptr : g.terms[0].ptr;
+          a.contrib = true;
           a.grz = ot ? g.rz[1] : g.rz[0];
           a.sign = ot == 0 ? 1.f : -1.f;
           a.mu = mu_ot;

@@ -243,13 +243,12 @@ constexpr int kMaxHandsPerThread = 3;   // ld <= 1536 with 512 threads
 
 }  // namespace gradimpl
 
-// Shared memory of one terminal item: input cache, F (w in fixed point), P, PC,
-// warp maxima, warp totals (without the staged tables).
+// Shared memory of one terminal item: F (w in fixed point), P, PC, warp maxima,
+// warp totals (without the staged tables).
 __host__ __device__ inline size_t grad_item_smem(const DevGame& g) {
   using gradimpl::align16;
   const size_t fx = sizeof(gradimpl::Fx);
-  size_t b = align16((size_t)g.ld * 8);
-  b += align16((size_t)g.ld * fx);
+  size_t b = align16((size_t)g.ld * fx);
   b += align16((size_t)(g.ld + 1) * fx);
   b += align16((size_t)g.n_slots * (g.lmax + 1) * fx);
   b += 16 * sizeof(int) + 16 * fx + 16;
@@ -312,8 +311,7 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
   constexpr int kWarps = kItemThreads / 32;
   const int lstride = g.lmax + 1;
 
-  TIn* cache = reinterpret_cast<TIn*>(smem);                               // [ld] input column
-  Fx* F = reinterpret_cast<Fx*>(smem + align16((size_t)ld * 8));
+  Fx* F = reinterpret_cast<Fx*>(smem);
   Fx* P = F + ld;                                                          // [ld + 1]
   Fx* PC = reinterpret_cast<Fx*>(reinterpret_cast<unsigned char*>(P) + align16((size_t)(ld + 1) * sizeof(Fx)));
   int* wmax = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(PC) +
@@ -329,12 +327,18 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
   const double coef64 = tm.coef64[e];
   const TIn* col = in + (size_t)os * ld;
 
-  // pass 1: input cached, largest exponent of |w|
+  // pass 1: all of this thread's inputs loaded at once, largest exponent of |w| (w exact)
+  TIn y[kMaxHandsPerThread];
+#pragma unroll
+  for (int k = 0; k < kMaxHandsPerThread; ++k) {
+    const int h = tid + k * kItemThreads;
+    y[k] = h < H ? __ldcg(col + h) : TIn(0);
+  }
   int mlg = INT_MIN;
-  for (int h = tid; h < ld; h += kItemThreads) {
-    const TIn y = h < H ? __ldcg(col + h) : TIn(0);
-    cache[h] = y;
-    mlg = max(mlg, wprod(r_opp[h], y).lg);
+#pragma unroll
+  for (int k = 0; k < kMaxHandsPerThread; ++k) {
+    const int h = tid + k * kItemThreads;
+    if (h < ld) mlg = max(mlg, wprod(r_opp[h], y[k]).lg);
   }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) mlg = max(mlg, __shfl_xor_sync(0xffffffffu, mlg, d));
@@ -345,7 +349,11 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
   for (int q = 0; q < kWarps; ++q) M = max(M, wmax[q]);
   const int ex = scale_of(M);
   // pass 2: exact fixed point
-  for (int h = tid; h < ld; h += kItemThreads) F[h] = to_fx(wprod(r_opp[h], cache[h]), ex);
+#pragma unroll
+  for (int k = 0; k < kMaxHandsPerThread; ++k) {
+    const int h = tid + k * kItemThreads;
+    if (h < ld) F[h] = to_fx(wprod(r_opp[h], y[k]), ex);
+  }
   __syncthreads();
 
   // exclusive prefix over ascending strength: P[i] = sum_{k < i} w[k], P[ld] = total

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kItemThreads) sbr_kernel(DevGame g, int player
   extern __shared__ __align__(16) float sm[];
   SbrItemArgs ia;
   ia.g = a.g;
-  ia.gptr = a.contrib ? (player ? g.terms[1].ptr : g.terms[0].ptr) : nullptr;
+  ia.contrib = a.contrib;
   ia.grz = player ? g.rz[1] : g.rz[0];
   ia.sign = a.sign;
   ia.mu = a.mu;
@@ -56,9 +56,8 @@ __global__ void __launch_bounds__(kItemThreads)
   unsigned char* raw = reinterpret_cast<unsigned char*>(smd);
   const TpxTab tt = stage_tpx_tab(g, player, raw);
   __syncthreads();
-  const int* gptr = contrib ? (player ? g.terms[1].ptr : g.terms[0].ptr) : nullptr;
   const double* grz = player ? g.rz64[1] : g.rz64[0];
-  br64_item(g, tt, blockIdx.x, gv, gptr, grz, sign, partials + blockIdx.x,
+  br64_item(g, tt, blockIdx.x, gv, contrib, grz, sign, partials + blockIdx.x,
             reinterpret_cast<double*>(raw + tpx_tab_bytes(g, player)));
   finish_value(partials, counter, value_dev, nullptr);
 }

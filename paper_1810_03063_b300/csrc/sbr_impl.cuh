@@ -26,8 +26,9 @@ namespace egt {
 
 struct SbrItemArgs {
   const float* g;          // gradient of the player's own loss up to `sign`; NULL = 0
-  const int* gptr;         // NULL: g is dense [S][ld]; else g holds terminal contributions
-  const float* grz;        //   [T][ld] and row s is grz[h] x sum_{e in [gptr[s], gptr[s+1])} g[e][h]
+  bool contrib;            // false: g is dense [S][ld]; true: g holds the player's terminal
+  const float* grz;        //   contributions [T][ld] and row s is grz[h] x (sum over the
+                           //   terminals [tptr[s], tptr[s+1]) of g[e][h], in order)
   float sign;              // +1 player 0 (g = A y), -1 player 1 (g = A^T x)
   double mu;
   const float* old;        // if non-NULL the output is (1 - tau) old + tau q
@@ -50,6 +51,7 @@ inline size_t br_item_smem(const DevGame& g, int player) {
 // One player's treeplex tables (Sec. 4 notation), staged once in shared memory.
 struct TpxTab {
   int S, J, L;
+  const int* tptr;         // [S+1] the player's terminals grouped by sequence (DevTerms::ptr)
   const double* beta;      // [J]
   const int* level_ptr;    // [L+1]
   const int* inf_first;    // [J]
@@ -62,7 +64,7 @@ struct TpxTab {
 __host__ __device__ inline size_t tpx_tab_bytes(const DevGame& g, int player) {
   const DevTpx& tp = g.tpx[player];
   return gradimpl::align16((size_t)tp.J * sizeof(double)) +
-         gradimpl::align16((size_t)(tp.L + 1 + 4 * tp.J + tp.S + 1) * sizeof(int));
+         gradimpl::align16((size_t)(tp.L + 1 + 4 * tp.J + 2 * (tp.S + 1)) * sizeof(int));
 }
 
 // Copy player's tables into dst (all threads; the caller synchronises before use).
@@ -81,6 +83,9 @@ __device__ inline TpxTab stage_tpx_tab(const DevGame& g, int player, unsigned ch
   int* cp = pa + tp.J;
   int* ci = cp + tp.S + 1;
   const int nchild = tp.child_ptr[tp.S];
+  int* tq = ci + nchild;
+  const int* tsrc = player ? g.terms[1].ptr : g.terms[0].ptr;
+  for (int i = threadIdx.x; i <= tp.S; i += blockDim.x) tq[i] = tsrc[i];
   for (int i = threadIdx.x; i < tp.J; i += blockDim.x) {
     beta[i] = tp.beta[i];
     fi[i] = tp.inf_first[i];
@@ -97,6 +102,7 @@ __device__ inline TpxTab stage_tpx_tab(const DevGame& g, int player, unsigned ch
   t.inf_parent = pa;
   t.child_ptr = cp;
   t.child_idx = ci;
+  t.tptr = tq;
   return t;
 }
 
@@ -124,14 +130,51 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
   const int h0 = blk * kSbrHands, h = h0 + lane;
   const bool live = h < g.H;
 
-  for (int idx = tid; idx < S * kSbrHands; idx += kItemThreads) {
-    const int s = idx / kSbrHands, l = idx % kSbrHands, hh = h0 + l;
-    const size_t gi = (size_t)s * ld + hh;
-    float v = 0.f;
-    if (a.g != nullptr && hh < g.H)
-      v = a.gptr != nullptr ? product32(a.g, a.gptr, s, ld, hh, a.grz[hh]) : __ldcg(a.g + gi);
-    G[idx] = a.sign * v;
-    if (a.old != nullptr) O[idx] = __ldcg(a.old + gi);
+  // the [S][32] tile of sign * g (and of the previous iterate): each warp takes rows
+  // warp, warp + 16, ...; the loads of kU rows are issued before any is used
+  {
+    constexpr int kU = 4;
+    const float rz = (a.g != nullptr && a.contrib && live) ? a.grz[h] : 0.f;
+    for (int s0 = warp; s0 < S; s0 += kWarps * kU) {
+      float c0[kU], c1[kU], o[kU];
+      int e0[kU], e1[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int s = s0 + u * kWarps;
+        c0[u] = c1[u] = o[u] = 0.f;
+        e0[u] = e1[u] = 0;
+        if (s < S) {
+          if (a.g != nullptr && live) {
+            if (a.contrib) {
+              e0[u] = tp.tptr[s];
+              e1[u] = tp.tptr[s + 1];
+              if (e0[u] < e1[u]) c0[u] = __ldcg(a.g + (size_t)e0[u] * ld + h);
+              if (e0[u] + 1 < e1[u]) c1[u] = __ldcg(a.g + (size_t)(e0[u] + 1) * ld + h);
+            } else {
+              c0[u] = __ldcg(a.g + (size_t)s * ld + h);
+            }
+          }
+          if (a.old != nullptr) o[u] = __ldcg(a.old + (size_t)s * ld + h);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int s = s0 + u * kWarps;
+        if (s < S) {
+          float v = c0[u];
+          if (a.contrib) {
+            // rz x (sum of the sequence's contributions in terminal order)
+            float acc = 0.f;
+            if (e0[u] < e1[u]) acc += c0[u];
+            if (e0[u] + 1 < e1[u]) acc += c1[u];
+            for (int e = e0[u] + 2; e < e1[u]; ++e) acc += __ldcg(a.g + (size_t)e * ld + h);
+            v = rz * acc;
+          }
+          G[s * kSbrHands + lane] = a.sign * v;
+          if (a.old != nullptr) O[s * kSbrHands + lane] = o[u];
+        }
+      }
+    }
   }
   for (int j = tid; j < J; j += kItemThreads) {
     const float t = (float)(a.mu * tp.beta[j]);
@@ -204,9 +247,9 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
 
 // One item of the FP64 best-response value: sign * min over the treeplex of
 // <q, sign * g> summed over the item's live hands, written to *value_partial.
-// gv as in SbrItemArgs: dense [S][ld] (gptr NULL) or terminal contributions.
+// gv as in SbrItemArgs: dense [S][ld] or (contrib) terminal contributions.
 __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, const double* gv,
-                                 const int* gptr, const double* grz, double sign,
+                                 bool contrib, const double* grz, double sign,
                                  double* value_partial, double* sm) {
   const int S = tp.S, ld = g.ld;
   constexpr int kWarps = kItemThreads / 32;
@@ -215,17 +258,47 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int h0 = blk * kSbrHands, h = h0 + lane;
   const bool live = h < g.H;
-  for (int idx = tid; idx < S * kSbrHands; idx += kItemThreads) {
-    const int s = idx / kSbrHands, l = idx % kSbrHands;
-    const int hh = h0 + l;
-    double v = 0.0;
-    if (hh < g.H) {
-      if (gptr != nullptr)
-        v = sign < 0 ? neg_product64(gv, gptr, s, ld, hh, grz[hh]) : product64(gv, gptr, s, ld, hh, grz[hh]);
-      else
-        v = sign < 0 ? -__ldcg(gv + (size_t)s * ld + hh) : __ldcg(gv + (size_t)s * ld + hh);
+  {
+    constexpr int kU = 4;
+    const bool neg = sign < 0;
+    const double rz = (contrib && live) ? grz[h] : 0.0;
+    for (int s0 = warp; s0 < S; s0 += kWarps * kU) {
+      double c0[kU], c1[kU];
+      int e0[kU], e1[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int s = s0 + u * kWarps;
+        c0[u] = c1[u] = 0.0;
+        e0[u] = e1[u] = 0;
+        if (s < S && live) {
+          if (contrib) {
+            e0[u] = tp.tptr[s];
+            e1[u] = tp.tptr[s + 1];
+            if (e0[u] < e1[u]) c0[u] = __ldcg(gv + (size_t)e0[u] * ld + h);
+            if (e0[u] + 1 < e1[u]) c1[u] = __ldcg(gv + (size_t)(e0[u] + 1) * ld + h);
+          } else {
+            c0[u] = __ldcg(gv + (size_t)s * ld + h);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int s = s0 + u * kWarps;
+        if (s < S) {
+          double v = c0[u];
+          if (contrib) {
+            double acc = 0.0;
+            if (e0[u] < e1[u]) acc += c0[u];
+            if (e0[u] + 1 < e1[u]) acc += c1[u];
+            for (int e = e0[u] + 2; e < e1[u]; ++e) acc += __ldcg(gv + (size_t)e * ld + h);
+            v = neg ? (-rz) * acc : rz * acc;
+          } else if (neg) {
+            v = -v;
+          }
+          G[s * kSbrHands + lane] = v;
+        }
+      }
     }
-    G[idx] = v;
   }
   __syncthreads();
   for (int l = tp.L - 1; l >= 0; --l) {
