@@ -287,6 +287,52 @@ EGT_API egt_status egt_iterate(egt_game* game, const egt_solve_opts* opts, int32
 EGT_API egt_status egt_solve(egt_game* game, const egt_solve_opts* opts, float* x_out, float* y_out,
                      egt_solve_report* rep, void* stream);
 
+/* ---- batches: many games in one device-resident launch --------------------
+ * A batch schedules games that the caller created and initialised
+ * (egt_solver_init): each egt_batch_step is one cooperative launch whose CTAs
+ * are split into groups; every group runs its members (games) in turn, each
+ * for up to n_iters iterations of its own variant, stopping early at its own
+ * eps_mbb target or max_iters (Alg. 1 / 3 loop test, residual every gap_every
+ * iterations and at its last one).  A member's iterates are bit for bit those
+ * egt_iterate gives it alone: its decisions come from fixed-order sums that do
+ * not depend on the group size or on the other members.  The batch only reads
+ * and advances its members' solver state; the games must outlive their
+ * membership and must not be used by other calls while a step runs. */
+typedef struct egt_batch egt_batch;
+
+/* An empty batch on `device`. */
+EGT_API egt_status egt_batch_create(int32_t device, egt_batch** out);
+EGT_API egt_status egt_batch_destroy(egt_batch* batch);
+
+/* Add an initialised game with opts->variant, eps_mbb, gap_every, max_iters
+ * (max_iters counted from now; replay and log are not accepted).  *slot (host):
+ * its index, stable until egt_batch_remove; freed slots are reused. */
+EGT_API egt_status egt_batch_add(egt_batch* batch, egt_game* game, const egt_solve_opts* opts,
+                                 int32_t* slot);
+EGT_API egt_status egt_batch_remove(egt_batch* batch, int32_t slot);
+
+/* One launch advancing every active member by up to n_iters iterations.
+ * group: CTAs per member (0: the co-resident CTAs split evenly over the active
+ * members, at most the widest phase of the largest one).  *n_active (host, may
+ * be NULL): members still active afterwards.  A member stops being active when
+ * it reaches its target (status OK), runs out of iterations (OK, or
+ * NOT_CONVERGED if it had a target) or fails (its status). */
+EGT_API egt_status egt_batch_step(egt_batch* batch, int32_t n_iters, int32_t group, int32_t* n_active,
+                                  void* stream);
+
+typedef struct {
+  int32_t active;            /* 1 while the member still runs */
+  int32_t status;            /* egt_status of the member */
+  egt_solve_report rep;      /* since it was added: iterations, products, back-offs, residual
+                                checks; the last residual, mu, tau; seconds = wall time of the
+                                launches it took part in */
+} egt_batch_member_info;
+
+EGT_API egt_status egt_batch_member(const egt_batch* batch, int32_t slot, egt_batch_member_info* out);
+
+/* Launch shape of the last egt_batch_step: CTAs per member and grid (host, either may be NULL). */
+EGT_API egt_status egt_batch_launch_shape(const egt_batch* batch, int32_t* group, int32_t* grid);
+
 /* ---- per-kernel device time accounting -------------------------------------- */
 
 /* Kernel kinds of the accounting: FP32 product, FP64 product, smoothed best

@@ -52,7 +52,7 @@ struct DeviceGuard {
   }
 };
 
-constexpr int kMaxLd = 1536;   // 6 hands per thread of a 256-thread half in the product kernels
+constexpr int kMaxLd = 1536;   // 3 hands per thread of a 512-thread CTA in the product kernels
 constexpr double kTauMin = 1.0 / (1u << 30);
 
 }  // namespace
@@ -728,29 +728,32 @@ egt_status solver_init(egt_game* G, const egt_solve_opts* o, cudaStream_t st) {
 // Grid of the device-resident driver for this game (0: not available here).
 int engine_grid(egt_game* G) {
   if (G->eng_grid == -2) {
-    const int maxg = engine_max_grid(G->dg);
-    const int NB = G->ld / kSbrHands;
-    // widest phase: the last product with the next v_hat, or the EGV SBR with the
-    // residual's two best responses
-    const int items = std::max(3 * NB, (int)G->comp.term.size() + NB);
-    G->eng_grid = maxg <= 0 ? 0 : std::min(maxg, items);
+    const int maxg = engine_max_grid(engine_smem_bytes(G->dg), false);
+    G->eng_grid = maxg <= 0 ? 0 : std::min(maxg, engine_items(G->dg));
   }
   return G->eng_grid;
 }
 
-int env_int(const char* name, int dflt) {
-  const char* v = std::getenv(name);
-  return v && *v ? std::atoi(v) : dflt;
+// The game's buffers as the device-resident driver sees them.
+EngineBufs engine_bufs(const egt_game* G, egt_iter_log* log_dev, int log_cap) {
+  EngineBufs b{};
+  for (int i = 0; i < 2; ++i) {
+    b.x[i] = G->x[i];
+    b.y[i] = G->y[i];
+    b.gx[i] = G->gx[i];
+    b.gy[i] = G->gy[i];
+    b.g64[i] = G->g64[i];
+  }
+  b.tx = G->tx;
+  b.ty = G->ty;
+  b.partials = G->eng_partials;
+  b.log = log_dev;
+  b.log_cap = log_cap;
+  return b;
 }
 
-// Run up to n iterations of `variant` from the solver state on the device (one
-// cooperative launch), as the host loop of egt_solve would: Step (with the
-// EGT/as back-off), then the residual every gap_every iterations and at the end.
-egt_status engine_run(egt_game* G, int variant, double eps_mbb, int gap_every, int n,
-                      egt_iter_log* log_dev, int log_cap, egt_solve_report* rep, cudaStream_t st) {
-  const int grid = engine_grid(G);
-  if (grid <= 0) return fail(EGT_ERR_CUDA, "the device-resident driver cannot run on this device");
-  EngineCtl& c = *G->ctl_host;
+// Control block of a launch of n iterations from the game's solver state.
+void engine_ctl_init(const egt_game* G, EngineCtl& c, int variant, double eps_mbb, int gap_every, int n) {
   std::memset(&c, 0, sizeof(c));
   c.variant = variant;
   c.n_iters = n;
@@ -765,31 +768,10 @@ egt_status engine_run(egt_game* G, int variant, double eps_mbb, int gap_every, i
   c.t = G->t;
   c.gap_mbb = G->last_gap;
   c.egv = c.last_tau = c.last_egv = NAN;
-  EngineBufs b{};
-  for (int i = 0; i < 2; ++i) {
-    b.x[i] = G->x[i];
-    b.y[i] = G->y[i];
-    b.gx[i] = G->gx[i];
-    b.gy[i] = G->gy[i];
-    b.g64[i] = G->g64[i];
-  }
-  b.tx = G->tx;
-  b.ty = G->ty;
-  b.partials = G->eng_partials;
-  b.log = log_dev;
-  b.log_cap = log_cap;
-  // fault-injection hooks for tests: phantom arrivals make every grid barrier wait run
-  // out after the time limit instead of completing
-  const unsigned expected = (unsigned)(grid + std::max(0, env_int("EGT_TEST_BARRIER_EXTRA", 0)));
-  const unsigned long long limit_ns =
-      1000000ull * (unsigned long long)std::max(1, env_int("EGT_BARRIER_TIMEOUT_MS", 2000));
-  CUDA_TRY(cudaMemcpyAsync(G->ctl_dev, &c, sizeof(c), cudaMemcpyHostToDevice, st));
-  cudaError_t le = cudaSuccess;
-  EGT_TRY(timed(G, EGT_KERNEL_ENGINE, st, "engine kernel",
-                [&] { le = engine_launch(G->dg, b, G->ctl_dev, grid, expected, limit_ns, st); }));
-  if (le != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("engine launch: ") + cudaGetErrorString(le));
-  CUDA_TRY(cudaMemcpyAsync(&c, G->ctl_dev, sizeof(c), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+// The game's solver state after a launch (from its control block).
+void engine_ctl_apply(egt_game* G, const EngineCtl& c, egt_solve_report* rep) {
   G->mu[0] = c.mu[0];
   G->mu[1] = c.mu[1];
   G->cur = c.cur;
@@ -812,12 +794,50 @@ egt_status engine_run(egt_game* G, int variant, double eps_mbb, int gap_every, i
     rep->mu[1] = c.mu[1];
     rep->tau = c.tau;
   }
+}
+
+egt_status engine_status(const EngineCtl& c) {
   if (c.status == EGT_ERR_TIMEOUT)
-    return fail(EGT_ERR_TIMEOUT, "a grid barrier of the device-resident driver ran out of time; "
+    return fail(EGT_ERR_TIMEOUT, "a group barrier of the device-resident driver ran out of time; "
                                  "the solver state is undefined until egt_solver_init");
   if (c.status == EGT_ERR_TAU_UNDERFLOW) return fail(EGT_ERR_TAU_UNDERFLOW, "Decr halved tau below 2^-30");
   if (c.status != 0) return fail((egt_status)c.status, "non-finite value in the device-resident driver");
   return EGT_OK;
+}
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+
+// Run up to n iterations of `variant` from the solver state on the device (one
+// cooperative launch), as the host loop of egt_solve would: Step (with the
+// EGT/as back-off), then the residual every gap_every iterations and at the end.
+egt_status engine_run(egt_game* G, int variant, double eps_mbb, int gap_every, int n,
+                      egt_iter_log* log_dev, int log_cap, egt_solve_report* rep, cudaStream_t st) {
+  const int grid = engine_grid(G);
+  if (grid <= 0) return fail(EGT_ERR_CUDA, "the device-resident driver cannot run on this device");
+  EngineCtl& c = *G->ctl_host;
+  engine_ctl_init(G, c, variant, eps_mbb, gap_every, n);
+  EngineJob job{};
+  job.g = G->dg;
+  job.b = engine_bufs(G, log_dev, log_cap);
+  job.ctl = G->ctl_dev;
+  // fault-injection hooks for tests: phantom arrivals make every group barrier wait run
+  // out after the time limit instead of completing
+  const unsigned extra = (unsigned)std::max(0, env_int("EGT_TEST_BARRIER_EXTRA", 0));
+  const unsigned long long limit_ns =
+      1000000ull * (unsigned long long)std::max(1, env_int("EGT_BARRIER_TIMEOUT_MS", 2000));
+  CUDA_TRY(cudaMemcpyAsync(G->ctl_dev, &c, sizeof(c), cudaMemcpyHostToDevice, st));
+  cudaError_t le = cudaSuccess;
+  EGT_TRY(timed(G, EGT_KERNEL_ENGINE, st, "engine kernel", [&] {
+    le = engine_launch_one(job, grid, engine_smem_bytes(G->dg), extra, limit_ns, st);
+  }));
+  if (le != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("engine launch: ") + cudaGetErrorString(le));
+  CUDA_TRY(cudaMemcpyAsync(&c, G->ctl_dev, sizeof(c), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  engine_ctl_apply(G, c, rep);
+  return engine_status(c);
 }
 
 }  // namespace
@@ -834,6 +854,61 @@ bool game_view(const egt_game* G, GameView* out) {
   return true;
 }
 }  // namespace egt
+
+// ---- batches ------------------------------------------------------------------
+
+struct egt_batch {
+  int device = 0;
+  struct Member {
+    egt_game* G = nullptr;     // NULL: free slot
+    int variant = EGT_AS, gap_every = 1, max_iters = 0;
+    double eps_mbb = 0.0;
+    int active = 0, status = EGT_OK, iters = 0, products = 0, backoffs = 0, gap_checks = 0;
+    double seconds = 0.0;
+  };
+  std::vector<Member> members;
+  EngineCtl* ctl_dev = nullptr;
+  EngineCtl* ctl_host = nullptr;
+  EngineJob* jobs_dev = nullptr;
+  EngineJob* jobs_host = nullptr;
+  int cap = 0;
+  int last_group = 0, last_grid = 0;
+};
+
+namespace {
+
+void batch_free_arrays(egt_batch* B) {
+  cudaFree(B->ctl_dev);
+  cudaFree(B->jobs_dev);
+  if (B->ctl_host) cudaFreeHost(B->ctl_host);
+  if (B->jobs_host) cudaFreeHost(B->jobs_host);
+  B->ctl_dev = nullptr;
+  B->jobs_dev = nullptr;
+  B->ctl_host = nullptr;
+  B->jobs_host = nullptr;
+  B->cap = 0;
+}
+
+egt_status batch_reserve(egt_batch* B, int n) {
+  if (n <= B->cap) return EGT_OK;
+  const int cap = std::max(n, 2 * B->cap);
+  batch_free_arrays(B);
+  CUDA_TRY(cudaMalloc(&B->ctl_dev, (size_t)cap * sizeof(EngineCtl)));
+  CUDA_TRY(cudaMalloc(&B->jobs_dev, (size_t)cap * sizeof(EngineJob)));
+  CUDA_TRY(cudaHostAlloc(&B->ctl_host, (size_t)cap * sizeof(EngineCtl), cudaHostAllocDefault));
+  CUDA_TRY(cudaHostAlloc(&B->jobs_host, (size_t)cap * sizeof(EngineJob), cudaHostAllocDefault));
+  B->cap = cap;
+  return EGT_OK;
+}
+
+egt_status check_slot(const egt_batch* B, int32_t slot) {
+  if (!B) return fail(EGT_ERR_INVALID_ARG, "batch is NULL");
+  if (slot < 0 || slot >= (int)B->members.size() || !B->members[slot].G)
+    return fail(EGT_ERR_INVALID_ARG, "no such batch member");
+  return EGT_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1269,6 +1344,162 @@ egt_status egt_profile_read(egt_game* G, double* ms, int64_t* launches) {
     if (ms) ms[k] = G->prof_ms[k];
     if (launches) launches[k] = G->launches[k];
   }
+  return EGT_OK;
+}
+
+
+egt_status egt_batch_create(int32_t device, egt_batch** out) {
+  if (!out) return fail(EGT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(EGT_ERR_INVALID_ARG, "no such device");
+  egt_batch* B = new (std::nothrow) egt_batch();
+  if (!B) return fail(EGT_ERR_OOM, "host allocation failed");
+  B->device = device;
+  *out = B;
+  return EGT_OK;
+}
+
+egt_status egt_batch_destroy(egt_batch* B) {
+  if (!B) return EGT_OK;
+  DeviceGuard guard(B->device);
+  cudaDeviceSynchronize();
+  batch_free_arrays(B);
+  delete B;
+  return EGT_OK;
+}
+
+egt_status egt_batch_add(egt_batch* B, egt_game* G, const egt_solve_opts* o, int32_t* slot) {
+  if (!B || !G || !o || !slot) return fail(EGT_ERR_INVALID_ARG, "NULL argument");
+  if (G->host_only || G->device != B->device)
+    return fail(EGT_ERR_INVALID_ARG, "the game is not on the batch's device");
+  if (!G->initialised) return fail(EGT_ERR_INVALID_ARG, "egt_solver_init has not been called");
+  if (o->variant < EGT_THEORY || o->variant > EGT_AS) return fail(EGT_ERR_INVALID_ARG, "unknown variant");
+  if (o->max_iters <= 0) return fail(EGT_ERR_INVALID_ARG, "max_iters must be > 0");
+  if (o->replay_n > 0 || o->log) return fail(EGT_ERR_INVALID_ARG, "replay and log are not accepted in a batch");
+  for (const auto& m : B->members)
+    if (m.G == G) return fail(EGT_ERR_INVALID_ARG, "the game is already a member");
+  egt_batch::Member m;
+  m.G = G;
+  m.variant = o->variant;
+  m.gap_every = std::max(1, o->gap_every);
+  m.max_iters = o->max_iters;
+  m.eps_mbb = o->eps_mbb;
+  m.active = 1;
+  int k = 0;
+  while (k < (int)B->members.size() && B->members[k].G) ++k;
+  if (k == (int)B->members.size()) B->members.push_back(m);
+  else B->members[k] = m;
+  *slot = k;
+  return EGT_OK;
+}
+
+egt_status egt_batch_remove(egt_batch* B, int32_t slot) {
+  EGT_TRY(check_slot(B, slot));
+  B->members[slot] = egt_batch::Member();
+  return EGT_OK;
+}
+
+egt_status egt_batch_step(egt_batch* B, int32_t n_iters, int32_t group, int32_t* n_active, void* stream) {
+  if (!B) return fail(EGT_ERR_INVALID_ARG, "batch is NULL");
+  if (n_iters <= 0) return fail(EGT_ERR_INVALID_ARG, "n_iters must be > 0");
+  if (group < 0) return fail(EGT_ERR_INVALID_ARG, "group must be >= 0");
+  DeviceGuard guard(B->device);
+  cudaStream_t st = S(stream);
+  std::vector<int> act;
+  for (int k = 0; k < (int)B->members.size(); ++k)
+    if (B->members[k].G && B->members[k].active) act.push_back(k);
+  const int n = (int)act.size();
+  if (n_active) *n_active = n;
+  if (n == 0) return EGT_OK;
+  EGT_TRY(batch_reserve(B, n));
+  size_t smem = 0;
+  int items = 1;
+  for (int k : act) {
+    smem = std::max(smem, engine_smem_bytes(B->members[k].G->dg));
+    items = std::max(items, engine_items(B->members[k].G->dg));
+  }
+  const int maxg = engine_max_grid(smem, true);
+  if (maxg <= 0) return fail(EGT_ERR_CUDA, "the device-resident driver cannot run on this device");
+  // CTAs per game: what the device holds split over the members, at most the widest
+  // phase of the largest member
+  int gsize = group > 0 ? group : std::max(1, std::min(maxg / n, items));
+  gsize = std::min(gsize, maxg);
+  const int grid = gsize * std::min(n, maxg / gsize);
+  B->last_group = gsize;
+  B->last_grid = grid;
+  for (int i = 0; i < n; ++i) {
+    egt_batch::Member& m = B->members[act[i]];
+    const int left = m.max_iters - m.iters;
+    engine_ctl_init(m.G, B->ctl_host[i], m.variant, m.eps_mbb, m.gap_every, std::min(n_iters, left));
+    // the residual at the member's last iteration, as egt_solve does
+    B->ctl_host[i].max_t = m.G->t + left;
+    EngineJob& j = B->jobs_host[i];
+    std::memset(&j, 0, sizeof(j));
+    j.g = m.G->dg;
+    j.b = engine_bufs(m.G, nullptr, 0);
+    j.ctl = B->ctl_dev + i;
+  }
+  const unsigned extra = (unsigned)std::max(0, env_int("EGT_TEST_BARRIER_EXTRA", 0));
+  const unsigned long long limit_ns =
+      1000000ull * (unsigned long long)std::max(1, env_int("EGT_BARRIER_TIMEOUT_MS", 2000));
+  const auto t0 = std::chrono::steady_clock::now();
+  CUDA_TRY(cudaMemcpyAsync(B->ctl_dev, B->ctl_host, (size_t)n * sizeof(EngineCtl), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(B->jobs_dev, B->jobs_host, (size_t)n * sizeof(EngineJob), cudaMemcpyHostToDevice, st));
+  const cudaError_t le = engine_launch(B->jobs_dev, n, gsize, grid, smem, extra, limit_ns, st);
+  if (le != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("engine launch: ") + cudaGetErrorString(le));
+  CUDA_TRY(cudaMemcpyAsync(B->ctl_host, B->ctl_dev, (size_t)n * sizeof(EngineCtl), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int still = 0;
+  for (int i = 0; i < n; ++i) {
+    egt_batch::Member& m = B->members[act[i]];
+    const EngineCtl& c = B->ctl_host[i];
+    engine_ctl_apply(m.G, c, nullptr);
+    m.iters += c.done_iters;
+    m.products += c.products;
+    m.backoffs += c.backoffs;
+    m.gap_checks += c.gap_checks;
+    m.seconds += sec;
+    if (c.status != 0) {
+      m.active = 0;
+      m.status = c.status;
+    } else if (c.reached) {
+      m.active = 0;
+      m.status = EGT_OK;
+    } else if (m.iters >= m.max_iters) {
+      m.active = 0;
+      m.status = m.eps_mbb > 0 ? EGT_ERR_NOT_CONVERGED : EGT_OK;
+    }
+    still += m.active;
+  }
+  if (n_active) *n_active = still;
+  return EGT_OK;
+}
+
+egt_status egt_batch_member(const egt_batch* B, int32_t slot, egt_batch_member_info* out) {
+  EGT_TRY(check_slot(B, slot));
+  if (!out) return fail(EGT_ERR_INVALID_ARG, "out is NULL");
+  const egt_batch::Member& m = B->members[slot];
+  out->active = m.active;
+  out->status = m.status;
+  out->rep.iters = m.iters;
+  out->rep.products = m.products;
+  out->rep.backoffs = m.backoffs;
+  out->rep.gap_checks = m.gap_checks;
+  out->rep.gap_mbb = m.G->last_gap;
+  out->rep.mu[0] = m.G->mu[0];
+  out->rep.mu[1] = m.G->mu[1];
+  out->rep.tau = m.G->tau;
+  out->rep.seconds = m.seconds;
+  return EGT_OK;
+}
+
+egt_status egt_batch_launch_shape(const egt_batch* B, int32_t* group, int32_t* grid) {
+  if (!B) return fail(EGT_ERR_INVALID_ARG, "batch is NULL");
+  if (group) *group = B->last_group;
+  if (grid) *grid = B->last_grid;
   return EGT_OK;
 }
 

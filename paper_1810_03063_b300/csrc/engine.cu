@@ -3,18 +3,21 @@
 // of Alg. 2's Step, the excessive-gap check with its tau back-off, the mu / tau
 // bookkeeping and the FP64 stopping residual -- with no host round trip.
 //
-// Phases are separated by a grid barrier; the work of a phase (32-hand SBR
-// items, one terminal per product item) is spread over the CTAs.  Products stay
+// The CTAs of a launch are split into groups; each group runs the jobs (games)
+// assigned to it one after the other.  Phases are separated by a group barrier;
+// the work of a phase (32-hand SBR items, one terminal per product item) is
+// spread over the group's CTAs.  Products stay
 // in terminal-contribution form; the SBR items add a sequence's contributions
 // while they load their tile.
 // Every CTA keeps its own copy of the solver state (t, mu, tau, buffer index)
 // and takes every decision (EGV sign, tau back-off, gap target) itself from
 // the same per-item FP64 partials, summed in the same fixed order as the
-// standalone kernels: all CTAs agree without a broadcast, and a run here
-// reproduces the host-driven loop of api.cu bit for bit.
+// standalone kernels: all CTAs of a group agree without a broadcast, a run here
+// reproduces the host-driven loop of api.cu bit for bit, and a game's iterates
+// do not depend on the group size or on the other games of the launch.
 //
-// The grid barrier is a monotone 64-bit arrival counter: barrier k completes
-// when it reaches k x (number of CTAs).  Waits are bounded in time: if one runs
+// The group barrier is a monotone 64-bit arrival counter in the job's control
+// block: barrier k completes when it reaches k x (CTAs of the group).  Waits are bounded in time: if one runs
 // out (a CTA that never arrives), the kernel records EGT_ERR_TIMEOUT and every
 // CTA returns; the host reads the status and the context stays usable.
 #include <algorithm>
@@ -63,12 +66,16 @@ struct PhaseClock {
 
 // All CTAs meet here; k counts this CTA's barriers.  Returns false (in every
 // thread) if the wait ran out or an error status was recorded.
-__device__ bool grid_sync(const GridBar& b, unsigned long long& k, PhaseClock* clk) {
+__device__ bool grid_sync(const GridBar& b, unsigned long long& k, PhaseClock* clk, bool clock_cta) {
   __shared__ int ok_s;
   __syncthreads();
   ++k;
+  if (b.expected == 1) {   // a one-CTA group: the CTA barrier is the group barrier
+    if (clock_cta && threadIdx.x == 0) clk->arrive = global_ns();
+    return true;
+  }
   if (threadIdx.x == 0) {
-    if (blockIdx.x == 0) clk->arrive = global_ns();
+    if (clock_cta) clk->arrive = global_ns();
     int ok = 1;
     __threadfence();                       // release this CTA's writes of the phase
     atomicAdd(b.arrive, 1ull);
@@ -99,8 +106,8 @@ __device__ bool grid_sync(const GridBar& b, unsigned long long& k, PhaseClock* c
 }
 
 // CTA 0 books the time since the last mark to `phase` (work done without a barrier).
-__device__ __forceinline__ void phase_cut(PhaseClock* c, int phase) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+__device__ __forceinline__ void phase_cut(PhaseClock* c, int phase, bool clock_cta) {
+  if (clock_cta && threadIdx.x == 0) {
     const unsigned long long now = global_ns();
     c->ns[phase] += now - c->last;
     c->work[phase] += now - c->last;
@@ -110,9 +117,10 @@ __device__ __forceinline__ void phase_cut(PhaseClock* c, int phase) {
 }
 
 // End of a phase: grid barrier, then CTA 0 books the phase's time.
-__device__ __forceinline__ bool phase_end(const GridBar& b, unsigned long long& k, PhaseClock* c, int phase) {
-  if (!grid_sync(b, k, c)) return false;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+__device__ __forceinline__ bool phase_end(const GridBar& b, unsigned long long& k, PhaseClock* c, int phase,
+                                          bool clock_cta) {
+  if (!grid_sync(b, k, c, clock_cta)) return false;
+  if (clock_cta && threadIdx.x == 0) {
     const unsigned long long now = global_ns();
     c->ns[phase] += now - c->last;
     c->work[phase] += c->arrive - c->last;
@@ -122,7 +130,12 @@ __device__ __forceinline__ bool phase_end(const GridBar& b, unsigned long long& 
   return true;
 }
 
-// Tables staged once per launch at the start of shared memory.
+// A group of CTAs running one job: this CTA's rank in it and its size.
+struct Grp {
+  int rank, size;
+};
+
+// Tables staged once per job at the start of shared memory.
 struct Tabs {
   GradTab grad;
   TpxTab tpx[2];
@@ -154,12 +167,12 @@ __device__ __forceinline__ TpxTab pick(const Tabs& tb, int p) {
 
 // One SBR phase: all 32-hand items of `player`, spread over the CTAs; gv holds the
 // player's terminal contributions (or is NULL).
-__device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int player, const float* gv,
+__device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, Grp gr, int player, const float* gv,
                                         double mu, const float* old, float tau, float* out,
                                         double* partials, unsigned char* sm) {
   const int NB = g.ld / kSbrHands;
   const TpxTab tp = pick(tb, player);
-  for (int item = blockIdx.x; item < NB; item += gridDim.x) {
+  for (int item = gr.rank; item < NB; item += gr.size) {
     SbrItemArgs a;
     a.g = gv;
     a.contrib = true;
@@ -176,10 +189,10 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, int pl
 
 // One product phase: every terminal of `player`'s grouping; c64 (FP64 contributions
 // for the residual) may be NULL.
-__device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, int player, const float* in,
+__device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, Grp gr, int player, const float* in,
                                          float* c32, double* c64, unsigned char* sm) {
   const int T = player ? g.terms[1].n : g.terms[0].n;
-  for (int item = blockIdx.x; item < T; item += gridDim.x)
+  for (int item = gr.rank; item < T; item += gr.size)
     term_item<float>(g, tb.grad, player, item, in, c32, c64, sm);
 }
 
@@ -239,10 +252,11 @@ struct Sched {
   double mu_tilde;      // (1 - tau) mu_me
 };
 
-__global__ void __launch_bounds__(kItemThreads, 1)
-    engine_kernel(DevGame g, EngineBufs b, EngineCtl* ctl, unsigned long long expected,
-                  unsigned long long limit_ns) {
-  extern __shared__ __align__(16) unsigned char smem_all[];
+// One job (game) run by the group `gr`: its tables staged in smem_all, then up to
+// ctl->n_iters iterations.  Returns when the job stops or fails (status recorded).
+__device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b, EngineCtl* ctl, Grp gr,
+                                        unsigned long long expected, unsigned long long limit_ns,
+                                        unsigned char* smem_all) {
   Tabs tb;
   tb.grad = stage_grad_tab(g, smem_all);
   tb.tpx[0] = stage_tpx_tab(g, 0, smem_all + grad_tab_bytes(g));
@@ -264,7 +278,8 @@ __global__ void __launch_bounds__(kItemThreads, 1)
       clk->n[k] = 0;
     }
   }
-  const bool writer = blockIdx.x == 0 && lead;
+  const bool clock_cta = gr.rank == 0;
+  const bool writer = clock_cta && lead;
   const int NB = g.ld / kSbrHands;
   const int T = g.terms[0].n;
   double* partA = b.partials;
@@ -360,24 +375,24 @@ __global__ void __launch_bounds__(kItemThreads, 1)
 
     // v_hat = (1 - tau) v + tau v_mu(other)
     if (!have_hat) {
-      run_sbr(g, tb, m, g_me, mu_me, v_me, tau_f, t_me, nullptr, sm);
-      if (!phase_end(bar, bk, clk, 0)) return;
+      run_sbr(g, tb, gr, m, g_me, mu_me, v_me, tau_f, t_me, nullptr, sm);
+      if (!phase_end(bar, bk, clk, 0, clock_cta)) return;
     }
-    phase_cut(clk, 8);
-    run_grad(g, tb, ot, t_me, t_ot, nullptr, sm);           // the other's loss gradient at v_hat
-    if (!phase_end(bar, bk, clk, 1)) return;
+    phase_cut(clk, 8, clock_cta);
+    run_grad(g, tb, gr, ot, t_me, t_ot, nullptr, sm);           // the other's loss gradient at v_hat
+    if (!phase_end(bar, bk, clk, 1, clock_cta)) return;
     // other_+ = (1 - tau) other + tau other_mu(v_hat)
-    run_sbr(g, tb, ot, t_ot, mu_ot, v_ot, tau_f, v_ot_n, nullptr, sm);
-    if (!phase_end(bar, bk, clk, 2)) return;
-    run_grad(g, tb, m, v_ot_n, g_me_n, g64_me, sm);         // my loss gradient at other_+
-    if (!phase_end(bar, bk, clk, 3)) return;
+    run_sbr(g, tb, gr, ot, t_ot, mu_ot, v_ot, tau_f, v_ot_n, nullptr, sm);
+    if (!phase_end(bar, bk, clk, 2, clock_cta)) return;
+    run_grad(g, tb, gr, m, v_ot_n, g_me_n, g64_me, sm);         // my loss gradient at other_+
+    if (!phase_end(bar, bk, clk, 3, clock_cta)) return;
     // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part
-    run_sbr(g, tb, m, g_me_n, mu_tilde, v_me, tau_f, v_me_n, partA, sm);
-    if (!phase_end(bar, bk, clk, 4)) return;
+    run_sbr(g, tb, gr, m, g_me_n, mu_tilde, v_me, tau_f, v_me_n, partA, sm);
+    if (!phase_end(bar, bk, clk, 4, clock_cta)) return;
     {
       // the other's loss gradient at v_+, and the next v_hat when the same player steps
       const int n_items = T + (sp == 1 ? NB : 0);
-      for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+      for (int item = gr.rank; item < n_items; item += gr.size) {
         if (item < T) {
           term_item<float>(g, tb.grad, ot, item, v_me_n, g_ot_n, g64_ot, sm);
         } else {
@@ -395,7 +410,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
         }
       }
     }
-    if (!phase_end(bar, bk, clk, 5)) return;
+    if (!phase_end(bar, bk, clk, 5, clock_cta)) return;
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     if (tail) {
       // the other's EGV part and / or the next v_hat (items [0, NB)), the residual's
@@ -403,7 +418,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
       const int n_sbr = check || sp == 2 ? NB : 0;
       const int n_items = n_sbr + (gap_due ? 2 * NB : 0);
       const TpxTab tp = pick(tb, ot);
-      for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+      for (int item = gr.rank; item < n_items; item += gr.size) {
         if (item < n_sbr) {
           SbrItemArgs a;
           a.g = g_ot_n;
@@ -420,10 +435,10 @@ __global__ void __launch_bounds__(kItemThreads, 1)
           run_br_items(g, tb, item - n_sbr, NB, b, partBR0, partBR1, sm);
         }
       }
-      if (!phase_end(bar, bk, clk, 6)) return;
+      if (!phase_end(bar, bk, clk, 6, clock_cta)) return;
       // the EGV parts (partA, partB) and the residual's values (partBR0, partBR1) in one pass
       reduce_arrays(b.partials, NB, check ? 0 : 2, gap_due ? 4 : 2, red);
-      phase_cut(clk, 7);
+      phase_cut(clk, 7, clock_cta);
     }
 
     if (lead) {
@@ -510,6 +525,37 @@ __global__ void __launch_bounds__(kItemThreads, 1)
   }
 }
 
+// One job on the whole grid, its description in the kernel parameters.
+__global__ void __launch_bounds__(kItemThreads, 1)
+    engine_kernel_one(EngineJob job, unsigned int extra, unsigned long long limit_ns) {
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  engine_job(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x},
+             (unsigned long long)gridDim.x + extra, limit_ns, smem_all);
+}
+
+// Groups of `gsize` consecutive CTAs; group q runs jobs q, q + groups, ...  Each
+// job's game description and buffers are copied to shared memory first.
+__global__ void __launch_bounds__(kItemThreads, 1)
+    engine_kernel(const EngineJob* __restrict__ jobs, int n_jobs, int gsize, unsigned int extra,
+                  unsigned long long limit_ns) {
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  __shared__ __align__(16) EngineJob job_s;
+  const int n_groups = gridDim.x / gsize;
+  const Grp gr{(int)blockIdx.x % gsize, gsize};
+  const int q = blockIdx.x / gsize;
+  if (q >= n_groups) return;
+  for (int j = q; j < n_jobs; j += n_groups) {
+    __syncthreads();   // the previous job's readers of job_s are done
+    {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(jobs + j);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&job_s);
+      for (int i = threadIdx.x; i < (int)(sizeof(EngineJob) / 8); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    engine_job(job_s.g, job_s.b, job_s.ctl, gr, (unsigned long long)gsize + extra, limit_ns, smem_all);
+  }
+}
+
 }  // namespace
 
 size_t engine_smem_bytes(const DevGame& g) {
@@ -521,32 +567,52 @@ size_t engine_smem_bytes(const DevGame& g) {
   return tabs_bytes(g) + m;
 }
 
-cudaError_t engine_launch(const DevGame& g, const EngineBufs& b, EngineCtl* ctl, int grid,
-                          unsigned int expected, unsigned long long limit_ns, cudaStream_t st) {
-  const size_t smem = engine_smem_bytes(g);
-  DevGame gg = g;
-  EngineBufs bb = b;
-  unsigned long long exp64 = expected;
-  void* args[] = {&gg, &bb, &ctl, &exp64, &limit_ns};
+cudaError_t engine_launch_one(const EngineJob& job, int grid, size_t smem, unsigned int extra,
+                              unsigned long long limit_ns, cudaStream_t st) {
+  EngineJob j = job;
+  unsigned int ex = extra;
+  unsigned long long lim = limit_ns;
+  void* args[] = {&j, &ex, &lim};
+  return cudaLaunchCooperativeKernel((const void*)engine_kernel_one, dim3(grid), dim3(kItemThreads), args,
+                                     smem, st);
+}
+
+cudaError_t engine_launch(const EngineJob* jobs_dev, int n_jobs, int gsize, int grid, size_t smem,
+                          unsigned int extra, unsigned long long limit_ns, cudaStream_t st) {
+  int nj = n_jobs, gs = gsize;
+  unsigned int ex = extra;
+  unsigned long long lim = limit_ns;
+  void* args[] = {(void*)&jobs_dev, &nj, &gs, &ex, &lim};
   return cudaLaunchCooperativeKernel((const void*)engine_kernel, dim3(grid), dim3(kItemThreads), args,
                                      smem, st);
 }
 
-int engine_max_grid(const DevGame& g) {
-  static int limit = 0;
-  if (limit == 0) limit = opt_in_dynamic_smem((const void*)engine_kernel);
+int engine_max_grid(size_t smem, bool batch) {
+  static int limit_one = 0, limit_batch = 0;
+  if (limit_one == 0) limit_one = opt_in_dynamic_smem((const void*)engine_kernel_one);
+  if (limit_batch == 0) limit_batch = opt_in_dynamic_smem((const void*)engine_kernel);
+  const int limit = batch ? limit_batch : limit_one;
   if (limit < 0) return -1;
-  const size_t smem = engine_smem_bytes(g);
   if (smem > (size_t)limit) return 0;
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel, kItemThreads, smem) !=
-          cudaSuccess)
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
     return -1;
+  const cudaError_t e = batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel,
+                                                                              kItemThreads, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel_one,
+                                                                              kItemThreads, smem);
+  if (e != cudaSuccess) return -1;
   if (!coop) return 0;
   return sms * per_sm;
+}
+
+int engine_items(const DevGame& g) {
+  const int NB = g.ld / kSbrHands;
+  // widest phase: the last product with the next v_hat, or the EGV SBR with the
+  // residual's two best responses
+  return std::max(3 * NB, g.terms[0].n + NB);
 }
 
 }  // namespace egt

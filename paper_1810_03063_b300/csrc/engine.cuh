@@ -50,16 +50,34 @@ struct EngineBufs {
   int log_cap;
 };
 
+// One game of a launch: its device tables, buffers and control block.
+struct EngineJob {
+  DevGame g;
+  EngineBufs b;
+  EngineCtl* ctl;
+};
+static_assert(sizeof(EngineJob) % 8 == 0, "EngineJob is copied in 8-byte words");
+
+// Dynamic shared memory the driver needs for game g (tables + the largest item).
 size_t engine_smem_bytes(const DevGame& g);
 
-// Largest co-resident grid for the engine on the current device (0: cannot run,
-// -1: CUDA error).
-int engine_max_grid(const DevGame& g);
+// Items of the widest phase of game g (more CTAs per game than this idle).
+int engine_items(const DevGame& g);
 
-// Cooperative launch of `grid` CTAs; `expected` is the number of barrier
-// arrivals that completes a grid barrier (grid, or more in a timeout test) and
-// limit_ns the barrier's time limit.
-cudaError_t engine_launch(const DevGame& g, const EngineBufs& b, EngineCtl* ctl, int grid,
-                          unsigned int expected, unsigned long long limit_ns, cudaStream_t st);
+// Largest co-resident grid of the driver (batch: the multi-job kernel, else the
+// one-job kernel) with `smem` bytes of dynamic shared memory per CTA on the
+// current device (0: cannot run, -1: CUDA error).
+int engine_max_grid(size_t smem, bool batch);
+
+// Cooperative launch of one job on `grid` CTAs (its description passed by value).
+cudaError_t engine_launch_one(const EngineJob& job, int grid, size_t smem, unsigned int extra,
+                              unsigned long long limit_ns, cudaStream_t st);
+
+// Cooperative launch of `grid` CTAs (a multiple of gsize) over n_jobs jobs in
+// device memory: groups of gsize CTAs, group q runs jobs q, q + grid / gsize, ...
+// `extra` phantom arrivals per group barrier (a timeout test: every wait then
+// runs out after limit_ns instead of completing).
+cudaError_t engine_launch(const EngineJob* jobs_dev, int n_jobs, int gsize, int grid, size_t smem,
+                          unsigned int extra, unsigned long long limit_ns, cudaStream_t st);
 
 }  // namespace egt

@@ -71,6 +71,10 @@ class SolveReport(C.Structure):
                 ("tau", C.c_double), ("seconds", C.c_double)]
 
 
+class BatchMemberInfo(C.Structure):
+    _fields_ = [("active", C.c_int32), ("status", C.c_int32), ("rep", SolveReport)]
+
+
 class StepInfo(C.Structure):
     _fields_ = [("player", C.c_int32), ("accepted", C.c_int32), ("backoffs", C.c_int32),
                 ("products", C.c_int32), ("tau", C.c_double), ("egv", C.c_double),
@@ -100,6 +104,13 @@ _SIGS = {
     "egt_iterate": [_vp, C.POINTER(SolveOpts), _i32, C.POINTER(SolveReport), _vp],
     "egt_engine_trace": [_vp, _i32, _vp, _vp, _vp],
     "egt_profile": [_vp, _i32],
+    "egt_batch_create": [_i32, C.POINTER(_vp)],
+    "egt_batch_destroy": [_vp],
+    "egt_batch_add": [_vp, _vp, C.POINTER(SolveOpts), C.POINTER(_i32)],
+    "egt_batch_remove": [_vp, _i32],
+    "egt_batch_step": [_vp, _i32, _i32, C.POINTER(_i32), _vp],
+    "egt_batch_member": [_vp, _i32, C.POINTER(BatchMemberInfo)],
+    "egt_batch_launch_shape": [_vp, C.POINTER(_i32), C.POINTER(_i32)],
     "egt_profile_read": [_vp, _vp, _vp],
 }
 KERNEL_KINDS = ("grad_f32", "grad_f64", "sbr", "br_f64", "engine")
@@ -360,3 +371,63 @@ class Game:
                                tau=log[i].tau, mu=(log[i].mu[0], log[i].mu[1]), egv=log[i].egv,
                                gap_mbb=log[i].gap_mbb) for i in range(n)]
         return out
+
+
+class Batch:
+    """Many games advanced together by one device-resident launch per step (egt_batch_*)."""
+
+    def __init__(self, device=0):
+        self._h = _vp()
+        _check(lib.egt_batch_create(device, C.byref(self._h)))
+        self.device = device
+        self.members = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib.egt_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, game, variant=EGT_AS, eps_mbb=1.0, max_iters=1000, gap_every=1):
+        """Add an initialised game (Game.solver_init); returns its slot."""
+        o, _, _ = Game._opts(variant=variant, eps_mbb=eps_mbb, max_iters=max_iters, gap_every=gap_every)
+        slot = C.c_int32()
+        _check(lib.egt_batch_add(self._h, game._h, C.byref(o), C.byref(slot)))
+        self.members[slot.value] = game
+        return slot.value
+
+    def remove(self, slot):
+        _check(lib.egt_batch_remove(self._h, slot))
+        self.members.pop(slot, None)
+
+    def step(self, n_iters, group=0, stream=None):
+        """One launch; returns the number of members still active."""
+        n = C.c_int32()
+        _check(lib.egt_batch_step(self._h, n_iters, group, C.byref(n), _stream(stream)))
+        return n.value
+
+    def member(self, slot):
+        m = BatchMemberInfo()
+        _check(lib.egt_batch_member(self._h, slot, C.byref(m)))
+        r = m.rep
+        return dict(active=bool(m.active), status=STATUS[m.status], iters=r.iters, products=r.products,
+                    backoffs=r.backoffs, gap_checks=r.gap_checks, gap_mbb=r.gap_mbb,
+                    mu=(r.mu[0], r.mu[1]), tau=r.tau, seconds=r.seconds)
+
+    def launch_shape(self):
+        g, n = C.c_int32(), C.c_int32()
+        _check(lib.egt_batch_launch_shape(self._h, C.byref(g), C.byref(n)))
+        return g.value, n.value
+
+    def run(self, n_iters=200, group=0, stream=None):
+        """Step until no member is active; returns the number of steps taken."""
+        steps = 0
+        while True:
+            steps += 1
+            if self.step(n_iters, group, stream) == 0:
+                return steps

@@ -1,0 +1,161 @@
+"""Batched solving (egt_batch_*): many games in one device-resident launch.
+
+A member's decisions come from the same fixed-order sums as when it runs
+alone, whatever the group size and whatever else shares the launch, so each
+member must end bit for bit where egt_solve takes the same game alone: same
+iterates, mu, tau, residual and iteration count.  Each member stops at its own
+target or iteration budget with its own status.
+"""
+import pytest
+
+from paper_1810_03063_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def egtlib():
+    if not torch.cuda.is_available():
+        pytest.fail("no CUDA device")
+    from paper_1810_03063_b300 import egt
+    return egt
+
+
+def mixed_specs():
+    return [synth.tiny(), synth.kuhn(), synth.full_deck(seed=synth.BASE_SEED + 3),
+            synth.tiny(seed=synth.BASE_SEED + 11), synth.large()]
+
+
+def solo(egtlib, spec, variant, eps, max_iters, gap_every):
+    g = egtlib.Game(spec, device=0)
+    x = torch.empty((g.S[0], g.ld), device="cuda")
+    y = torch.empty((g.S[1], g.ld), device="cuda")
+    rep = g.solve(x, y, variant=variant, alpha=0.01, eps_mbb=eps, max_iters=max_iters,
+                  gap_every=gap_every)
+    torch.cuda.synchronize()
+    g.close()
+    return x, y, rep
+
+
+def member_state(egtlib, g):
+    x = torch.empty((g.S[0], g.ld), device="cuda")
+    y = torch.empty((g.S[1], g.ld), device="cuda")
+    mu = g.state_get(x, y)
+    torch.cuda.synchronize()
+    return x, y, mu
+
+
+@pytest.mark.parametrize("group", [0, 1, 3])
+def test_batch_members_equal_solo_solves_bitwise(egtlib, group):
+    specs = mixed_specs()
+    iters = [40, 40, 40, 25, 12]
+    b = egtlib.Batch(0)
+    games, slots = [], []
+    for sp, n in zip(specs, iters):
+        g = egtlib.Game(sp, device=0)
+        g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+        slots.append(b.add(g, variant=egtlib.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1))
+        games.append(g)
+    steps = b.run(n_iters=7, group=group)
+    assert steps == 6                      # ceil(40 / 7) launches
+    if group:
+        assert b.launch_shape()[0] == group
+    for sp, n, g, s in zip(specs, iters, games, slots):
+        xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, n, 1)
+        xb, yb, mu = member_state(egtlib, g)
+        m = b.member(s)
+        assert not m["active"] and m["status"] == "EGT_OK"
+        assert m["iters"] == rs["iters"] == n
+        assert torch.equal(xb, xs) and torch.equal(yb, ys), sp.name
+        assert mu == rs["mu"] and m["tau"] == rs["tau"]
+        assert m["gap_mbb"] == rs["gap_mbb"]
+        # (the solo count also holds the initial point's products)
+        assert m["backoffs"] == rs["backoffs"] and m["products"] == 3 * (n + m["backoffs"])
+    b.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_batch_plain_variants_equal_solo(egtlib, variant):
+    specs = [synth.tiny(), synth.full_deck()]
+    b = egtlib.Batch(0)
+    games = []
+    for sp in specs:
+        g = egtlib.Game(sp, device=0)
+        g.solver_init(variant=variant, alpha=0.01)
+        games.append((b.add(g, variant=variant, eps_mbb=0.0, max_iters=30, gap_every=4), g))
+    b.run(n_iters=11)
+    for sp, (s, g) in zip(specs, games):
+        xs, ys, rs = solo(egtlib, sp, variant, 0.0, 30, 4)
+        xb, yb, mu = member_state(egtlib, g)
+        assert torch.equal(xb, xs) and torch.equal(yb, ys)
+        assert mu == rs["mu"] and b.member(s)["gap_mbb"] == rs["gap_mbb"]
+    b.close()
+
+
+def test_batch_members_stop_at_their_own_targets(egtlib):
+    targets = [400.0, 150.0, 60.0]
+    specs = [synth.tiny(seed=synth.BASE_SEED + k) for k in range(3)]
+    b = egtlib.Batch(0)
+    games = []
+    for sp, eps in zip(specs, targets):
+        g = egtlib.Game(sp, device=0)
+        g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+        games.append((b.add(g, variant=egtlib.EGT_AS, eps_mbb=eps, max_iters=20000, gap_every=1), g))
+    b.run(n_iters=50)
+    for sp, eps, (s, g) in zip(specs, targets, games):
+        m = b.member(s)
+        xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, eps, 20000, 1)
+        assert m["status"] == rs["status"] == "EGT_OK"
+        assert m["gap_mbb"] <= eps and m["gap_mbb"] == rs["gap_mbb"]
+        assert m["iters"] == rs["iters"]
+        xb, yb, _ = member_state(egtlib, g)
+        assert torch.equal(xb, xs) and torch.equal(yb, ys)
+    b.close()
+
+
+def test_batch_budget_and_slots(egtlib):
+    b = egtlib.Batch(0)
+    g1 = egtlib.Game(synth.tiny(), device=0)
+    g1.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+    g2 = egtlib.Game(synth.kuhn(), device=0)
+    g2.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+    s1 = b.add(g1, eps_mbb=1e-9, max_iters=30)        # unreachable target
+    s2 = b.add(g2, eps_mbb=0.0, max_iters=10)
+    with pytest.raises(egtlib.EGTError):
+        b.add(g1, max_iters=5)                        # already a member
+    assert b.step(100) == 0
+    assert b.member(s1)["status"] == "EGT_ERR_NOT_CONVERGED" and b.member(s1)["iters"] == 30
+    assert b.member(s2)["status"] == "EGT_OK" and b.member(s2)["iters"] == 10
+    b.remove(s1)
+    with pytest.raises(egtlib.EGTError):
+        b.member(s1)
+    g3 = egtlib.Game(synth.tiny(seed=7), device=0)
+    g3.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+    assert b.add(g3, max_iters=5) == s1                # freed slot reused
+    assert b.step(100) == 0 and b.member(s1)["iters"] == 5
+    uninit = egtlib.Game(synth.tiny(), device=0)
+    with pytest.raises(egtlib.EGTError):
+        b.add(uninit, max_iters=5)
+    b.close()
+
+
+def test_batch_barrier_timeout_is_reported_per_member(egtlib, monkeypatch):
+    b = egtlib.Batch(0)
+    games = []
+    for k in range(2):
+        g = egtlib.Game(synth.tiny(seed=synth.BASE_SEED + k), device=0)
+        g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+        games.append((b.add(g, max_iters=10), g))
+    monkeypatch.setenv("EGT_TEST_BARRIER_EXTRA", "1")
+    monkeypatch.setenv("EGT_BARRIER_TIMEOUT_MS", "50")
+    assert b.step(5, group=2) == 0
+    for s, _ in games:
+        assert b.member(s)["status"] == "EGT_ERR_TIMEOUT"
+    monkeypatch.delenv("EGT_TEST_BARRIER_EXTRA")
+    # the context is still usable
+    g = egtlib.Game(synth.tiny(), device=0)
+    x = torch.empty((g.S[0], g.ld), device="cuda")
+    y = torch.empty((g.S[1], g.ld), device="cuda")
+    assert g.solve(x, y, variant=egtlib.EGT_AS, alpha=0.01, eps_mbb=0.0, max_iters=5)["iters"] == 5
+    b.close()
