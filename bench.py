@@ -36,6 +36,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "EGT iter/s"
+# dram__bytes_read.sum + dram__bytes_write.sum of one timed engine launch (100 iterations after an
+# L2 flush), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+# -k regex:engine_kernel_one -s 3 -c 1 python bench.py --steps 3 --warmup 3 --no-ttg --cpu-seconds 0
+# --batch-games 0`; to be re-taken (or set to None) whenever the engine kernel changes.
+ENGINE_TRAFFIC_BYTES = 1243136 + 285440
 UNIT = "iter/s"
 WORKLOAD = "full-deck river endgame: 52 cards, 1081 hands/player, bets {0.5,1}xpot + all-in, raise cap 3, stack 10, pot 1, EGT/as"
 
@@ -51,6 +56,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample (cpu_baseline)")
     ap.add_argument("--ttg-max-iters", type=int, default=20000)
     ap.add_argument("--no-ttg", action="store_true")
+    ap.add_argument("--batch-games", type=int, default=64,
+                    help="games of the batched measurement (the mixed 20/52-card endgames); 0 skips it")
+    ap.add_argument("--batch-iters", type=int, default=200, help="iterations per game in the batched measurement")
     ap.add_argument("--engine", default="device", choices=["device", "host"],
                     help="device: each step is one egt_iterate launch; host: egt_step + egt_state_gap per iteration")
     return ap.parse_args()
@@ -310,6 +318,62 @@ def run_ours(args, world, rank, local):
                 per_launch=per_launch, one_per_launch=one_per_launch)
 
 
+def run_batched(args, local):
+    """Many independent endgames (mixed 20 / 52-card decks, raise caps 2-4, 1-4 bet sizes) advanced
+    --batch-iters EGT/as iterations each: one egt_batch_step launch for all of them against one
+    egt_iterate launch per game (all CTAs on one game at a time), each timed with CUDA events
+    after an L2 flush."""
+    import torch
+
+    from paper_1810_03063_b300 import egt, synth
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    specs = synth.batch_mix(args.batch_games)
+    games = [egt.Game(sp, device=local) for sp in specs]
+    n = args.batch_iters
+
+    def timed(fn):
+        for g in games:
+            g.solver_init(variant=egt.EGT_AS, alpha=0.01)
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e-3, out
+
+    def one_per_launch():
+        for g in games:
+            g.iterate(n, variant=egt.EGT_AS, gap_every=1)
+
+    def batched():
+        bt = egt.Batch(local)
+        for g in games:
+            bt.add(g, variant=egt.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1)
+        steps = bt.run(n_iters=n)
+        shape = bt.launch_shape()
+        bt.close()
+        return steps, shape
+
+    timed(batched)                                    # warm-up (module load, opt-in)
+    seq_s, _ = timed(one_per_launch)
+    bat_s, (steps, shape) = timed(batched)
+    total = len(games) * n
+    state_bytes = sum(4 * g.ld * (2 * g.S[0] + 2 * g.S[1] + 4 * g.T) for g in games)
+    for g in games:
+        g.close()
+    return {"workload": f"{len(games)} mixed river endgames (20/52-card decks, raise caps 2-4, "
+                        f"1-4 bet sizes), {n} EGT/as iterations each with the FP64 gap every iteration",
+            "value": round(total / bat_s, 1), "unit": UNIT,
+            "one_game_per_launch": round(total / seq_s, 1), "speedup": round(seq_s / bat_s, 3),
+            "launches": steps, "grid": shape[1], "widest_group": shape[0],
+            "state_mb": round(state_bytes / 2 ** 20, 1), "seconds": round(bat_s, 4),
+            "l2": "flushed before each timed pass"}
+
+
 def oracle_iterations(seconds, max_iters=None, seed=None):
     """The FP64 oracle's EGT/as on the same game: (iterations done, seconds, threads)."""
     from oracle import egt as OE
@@ -386,6 +450,7 @@ def main():
             print(json.dumps(out))
         return
     r = run_ours(args, world, rank, local)
+    batched = run_batched(args, local) if args.batch_games > 0 else None
     if rank != 0:
         return
     # bounded oracle sample on the host cores (rank 0 at N=1 only)
@@ -413,13 +478,14 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": r["dom"], "achieved": round(r["achieved"], 2),
                      "peak": r["peak"], "unit": "GB/s", "frac": round(r["achieved"] / r["peak"], 5),
-                     "peak_source": r["peak_kind"], "traffic": None,
+                     "peak_source": r["peak_kind"], "traffic": ENGINE_TRAFFIC_BYTES,
                      "alg_bytes_per_launch": int(r["per_launch"][r["dom"]]),
                      "avg_launch_us": round(r["avg_ms"] * 1e3, 3)},
         "kernels": r["kernels"],
         "cpu_baseline": cpu,
         "e2e": r["e2e"],
         "time_to_gap": r["ttg"],
+        "batched": batched,
         "gpu_launches": r["gpu_launches"],
         "clocks": r["clocks"],
         "backoffs_in_timed_region": r["backoffs"],

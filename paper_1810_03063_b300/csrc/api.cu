@@ -871,6 +871,8 @@ struct egt_batch {
   EngineCtl* ctl_host = nullptr;
   EngineJob* jobs_dev = nullptr;
   EngineJob* jobs_host = nullptr;
+  EngineGroup* plan_dev = nullptr;
+  EngineGroup* plan_host = nullptr;
   int cap = 0;
   int last_group = 0, last_grid = 0;
 };
@@ -880,12 +882,16 @@ namespace {
 void batch_free_arrays(egt_batch* B) {
   cudaFree(B->ctl_dev);
   cudaFree(B->jobs_dev);
+  cudaFree(B->plan_dev);
   if (B->ctl_host) cudaFreeHost(B->ctl_host);
   if (B->jobs_host) cudaFreeHost(B->jobs_host);
+  if (B->plan_host) cudaFreeHost(B->plan_host);
   B->ctl_dev = nullptr;
   B->jobs_dev = nullptr;
+  B->plan_dev = nullptr;
   B->ctl_host = nullptr;
   B->jobs_host = nullptr;
+  B->plan_host = nullptr;
   B->cap = 0;
 }
 
@@ -897,8 +903,85 @@ egt_status batch_reserve(egt_batch* B, int n) {
   CUDA_TRY(cudaMalloc(&B->jobs_dev, (size_t)cap * sizeof(EngineJob)));
   CUDA_TRY(cudaHostAlloc(&B->ctl_host, (size_t)cap * sizeof(EngineCtl), cudaHostAllocDefault));
   CUDA_TRY(cudaHostAlloc(&B->jobs_host, (size_t)cap * sizeof(EngineJob), cudaHostAllocDefault));
+  CUDA_TRY(cudaMalloc(&B->plan_dev, (size_t)cap * sizeof(EngineGroup)));
+  CUDA_TRY(cudaHostAlloc(&B->plan_host, (size_t)cap * sizeof(EngineGroup), cudaHostAllocDefault));
   B->cap = cap;
   return EGT_OK;
+}
+
+// Relative cost of one iteration of a game (three product phases of T terminal
+// items of ld hands, about seven SBR / best-response passes over S x ld).
+double iteration_work(const egt_game* G) {
+  const double S = 0.5 * (G->comp.tpx[0].S + G->comp.tpx[1].S);
+  return (double)G->ld * (3.0 * (double)G->comp.term.size() + 7.0 * S);
+}
+
+// Split maxg co-resident CTAs over n jobs (work w, useful CTAs at most cap each).
+// group > 0: groups of that size, jobs dealt round-robin.  Else one group per job
+// with CTAs in proportion to its work when the jobs fit, or one-CTA groups each
+// running a least-loaded share of the jobs when they do not.  Fills plan (groups
+// with contiguous job ranges) and order (job position -> input index); returns
+// the number of groups and sets *grid.
+int plan_groups(const std::vector<double>& w, const std::vector<int>& cap, int maxg, int group,
+                std::vector<EngineGroup>& plan, std::vector<int>& order, int* grid) {
+  const int n = (int)w.size();
+  plan.clear();
+  order.clear();
+  if (group > 0 || n > maxg) {
+    const int gsize = group > 0 ? std::min(group, maxg) : 1;
+    const int ng = std::min(n, maxg / gsize);
+    std::vector<std::vector<int>> lists(ng);
+    if (group > 0) {
+      for (int j = 0; j < n; ++j) lists[j % ng].push_back(j);
+    } else {
+      std::vector<int> idx(n);
+      std::iota(idx.begin(), idx.end(), 0);
+      std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return w[a] > w[b]; });
+      std::vector<double> load(ng, 0.0);
+      for (int j : idx) {
+        const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lists[q].push_back(j);
+        load[q] += w[j];
+      }
+    }
+    for (int q = 0; q < ng; ++q) {
+      EngineGroup e{q * gsize, gsize, (int)order.size(), 0};
+      for (int j : lists[q]) order.push_back(j);
+      e.job1 = (int)order.size();
+      plan.push_back(e);
+    }
+    *grid = ng * gsize;
+    return ng;
+  }
+  double W = 0.0;
+  for (double x : w) W += x;
+  std::vector<int> c(n);
+  int used = 0;
+  for (int j = 0; j < n; ++j) {
+    c[j] = std::max(1, std::min(cap[j], (int)std::floor(maxg * w[j] / W)));
+    used += c[j];
+  }
+  while (used > maxg) {   // rounding up to one CTA each overshot: take from the largest
+    const int j = (int)(std::max_element(c.begin(), c.end()) - c.begin());
+    --c[j];
+    --used;
+  }
+  while (used < maxg) {   // leftovers to the job with the most work per CTA that can use one
+    int best = -1;
+    for (int j = 0; j < n; ++j)
+      if (c[j] < cap[j] && (best < 0 || w[j] / c[j] > w[best] / c[best])) best = j;
+    if (best < 0) break;
+    ++c[best];
+    ++used;
+  }
+  int first = 0;
+  for (int j = 0; j < n; ++j) {
+    plan.push_back(EngineGroup{first, c[j], j, j + 1});
+    order.push_back(j);
+    first += c[j];
+  }
+  *grid = first;
+  return n;
 }
 
 egt_status check_slot(const egt_batch* B, int32_t slot) {
@@ -1415,22 +1498,28 @@ egt_status egt_batch_step(egt_batch* B, int32_t n_iters, int32_t group, int32_t*
   if (n == 0) return EGT_OK;
   EGT_TRY(batch_reserve(B, n));
   size_t smem = 0;
-  int items = 1;
-  for (int k : act) {
-    smem = std::max(smem, engine_smem_bytes(B->members[k].G->dg));
-    items = std::max(items, engine_items(B->members[k].G->dg));
+  std::vector<double> w(n);
+  std::vector<int> cap(n);
+  for (int i = 0; i < n; ++i) {
+    const egt_game* G = B->members[act[i]].G;
+    smem = std::max(smem, engine_smem_bytes(G->dg));
+    w[i] = iteration_work(G);
+    cap[i] = engine_items(G->dg);
   }
   const int maxg = engine_max_grid(smem, true);
   if (maxg <= 0) return fail(EGT_ERR_CUDA, "the device-resident driver cannot run on this device");
-  // CTAs per game: what the device holds split over the members, at most the widest
-  // phase of the largest member
-  int gsize = group > 0 ? group : std::max(1, std::min(maxg / n, items));
-  gsize = std::min(gsize, maxg);
-  const int grid = gsize * std::min(n, maxg / gsize);
-  B->last_group = gsize;
+  std::vector<EngineGroup> plan;
+  std::vector<int> order;
+  int grid = 0;
+  const int n_groups = plan_groups(w, cap, maxg, group, plan, order, &grid);
+  int widest = 0;
+  for (const auto& e : plan) widest = std::max(widest, e.size);
+  B->last_group = widest;
   B->last_grid = grid;
+  std::vector<int> slot_of(n);
   for (int i = 0; i < n; ++i) {
-    egt_batch::Member& m = B->members[act[i]];
+    slot_of[i] = act[order[i]];
+    egt_batch::Member& m = B->members[slot_of[i]];
     const int left = m.max_iters - m.iters;
     engine_ctl_init(m.G, B->ctl_host[i], m.variant, m.eps_mbb, m.gap_every, std::min(n_iters, left));
     // the residual at the member's last iteration, as egt_solve does
@@ -1441,20 +1530,23 @@ egt_status egt_batch_step(egt_batch* B, int32_t n_iters, int32_t group, int32_t*
     j.b = engine_bufs(m.G, nullptr, 0);
     j.ctl = B->ctl_dev + i;
   }
+  std::copy(plan.begin(), plan.end(), B->plan_host);
   const unsigned extra = (unsigned)std::max(0, env_int("EGT_TEST_BARRIER_EXTRA", 0));
   const unsigned long long limit_ns =
       1000000ull * (unsigned long long)std::max(1, env_int("EGT_BARRIER_TIMEOUT_MS", 2000));
   const auto t0 = std::chrono::steady_clock::now();
   CUDA_TRY(cudaMemcpyAsync(B->ctl_dev, B->ctl_host, (size_t)n * sizeof(EngineCtl), cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaMemcpyAsync(B->jobs_dev, B->jobs_host, (size_t)n * sizeof(EngineJob), cudaMemcpyHostToDevice, st));
-  const cudaError_t le = engine_launch(B->jobs_dev, n, gsize, grid, smem, extra, limit_ns, st);
+  CUDA_TRY(cudaMemcpyAsync(B->plan_dev, B->plan_host, (size_t)n_groups * sizeof(EngineGroup),
+                           cudaMemcpyHostToDevice, st));
+  const cudaError_t le = engine_launch(B->jobs_dev, B->plan_dev, n_groups, grid, smem, extra, limit_ns, st);
   if (le != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("engine launch: ") + cudaGetErrorString(le));
   CUDA_TRY(cudaMemcpyAsync(B->ctl_host, B->ctl_dev, (size_t)n * sizeof(EngineCtl), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   int still = 0;
   for (int i = 0; i < n; ++i) {
-    egt_batch::Member& m = B->members[act[i]];
+    egt_batch::Member& m = B->members[slot_of[i]];
     const EngineCtl& c = B->ctl_host[i];
     engine_ctl_apply(m.G, c, nullptr);
     m.iters += c.done_iters;

@@ -533,18 +533,21 @@ __global__ void __launch_bounds__(kItemThreads, 1)
              (unsigned long long)gridDim.x + extra, limit_ns, smem_all);
 }
 
-// Groups of `gsize` consecutive CTAs; group q runs jobs q, q + groups, ...  Each
-// job's game description and buffers are copied to shared memory first.
+// CTA groups of a launch as the plan gives them (group q: CTAs [first, first +
+// size), jobs [job0, job1) in turn).  Each job's game description and buffers
+// are copied to shared memory first.
 __global__ void __launch_bounds__(kItemThreads, 1)
-    engine_kernel(const EngineJob* __restrict__ jobs, int n_jobs, int gsize, unsigned int extra,
-                  unsigned long long limit_ns) {
+    engine_kernel(const EngineJob* __restrict__ jobs, const EngineGroup* __restrict__ plan, int n_groups,
+                  unsigned int extra, unsigned long long limit_ns) {
   extern __shared__ __align__(16) unsigned char smem_all[];
   __shared__ __align__(16) EngineJob job_s;
-  const int n_groups = gridDim.x / gsize;
-  const Grp gr{(int)blockIdx.x % gsize, gsize};
-  const int q = blockIdx.x / gsize;
-  if (q >= n_groups) return;
-  for (int j = q; j < n_jobs; j += n_groups) {
+  int q = 0;
+  while (q < n_groups && !(plan[q].first <= (int)blockIdx.x && (int)blockIdx.x < plan[q].first + plan[q].size))
+    ++q;
+  if (q == n_groups) return;
+  const EngineGroup pg = plan[q];
+  const Grp gr{(int)blockIdx.x - pg.first, pg.size};
+  for (int j = pg.job0; j < pg.job1; ++j) {
     __syncthreads();   // the previous job's readers of job_s are done
     {
       const unsigned long long* src = reinterpret_cast<const unsigned long long*>(jobs + j);
@@ -552,7 +555,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
       for (int i = threadIdx.x; i < (int)(sizeof(EngineJob) / 8); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    engine_job(job_s.g, job_s.b, job_s.ctl, gr, (unsigned long long)gsize + extra, limit_ns, smem_all);
+    engine_job(job_s.g, job_s.b, job_s.ctl, gr, (unsigned long long)pg.size + extra, limit_ns, smem_all);
   }
 }
 
@@ -577,12 +580,12 @@ cudaError_t engine_launch_one(const EngineJob& job, int grid, size_t smem, unsig
                                      smem, st);
 }
 
-cudaError_t engine_launch(const EngineJob* jobs_dev, int n_jobs, int gsize, int grid, size_t smem,
-                          unsigned int extra, unsigned long long limit_ns, cudaStream_t st) {
-  int nj = n_jobs, gs = gsize;
+cudaError_t engine_launch(const EngineJob* jobs_dev, const EngineGroup* plan_dev, int n_groups, int grid,
+                          size_t smem, unsigned int extra, unsigned long long limit_ns, cudaStream_t st) {
+  int ng = n_groups;
   unsigned int ex = extra;
   unsigned long long lim = limit_ns;
-  void* args[] = {(void*)&jobs_dev, &nj, &gs, &ex, &lim};
+  void* args[] = {(void*)&jobs_dev, (void*)&plan_dev, &ng, &ex, &lim};
   return cudaLaunchCooperativeKernel((const void*)engine_kernel, dim3(grid), dim3(kItemThreads), args,
                                      smem, st);
 }

@@ -73,11 +73,17 @@ int engine_max_grid(size_t smem, bool batch);
 cudaError_t engine_launch_one(const EngineJob& job, int grid, size_t smem, unsigned int extra,
                               unsigned long long limit_ns, cudaStream_t st);
 
-// Cooperative launch of `grid` CTAs (a multiple of gsize) over n_jobs jobs in
-// device memory: groups of gsize CTAs, group q runs jobs q, q + grid / gsize, ...
+// A group of a multi-job launch: CTAs [first, first + size) run jobs [job0, job1)
+// one after the other.
+struct EngineGroup {
+  int first, size, job0, job1;
+};
+
+// Cooperative launch of `grid` CTAs over the jobs in device memory, split into
+// the n_groups groups of plan_dev (disjoint CTA ranges inside the grid).
 // `extra` phantom arrivals per group barrier (a timeout test: every wait then
 // runs out after limit_ns instead of completing).
-cudaError_t engine_launch(const EngineJob* jobs_dev, int n_jobs, int gsize, int grid, size_t smem,
-                          unsigned int extra, unsigned long long limit_ns, cudaStream_t st);
+cudaError_t engine_launch(const EngineJob* jobs_dev, const EngineGroup* plan_dev, int n_groups, int grid,
+                          size_t smem, unsigned int extra, unsigned long long limit_ns, cudaStream_t st);
 
 }  // namespace egt

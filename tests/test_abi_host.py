@@ -95,3 +95,15 @@ def test_disjoint_ranges_give_zero_chance_mass():
     with pytest.raises(egt.EGTError) as e:
         egt.Game(synth.GameSpec(**{**spec.__dict__, "ranges": r}), device=-1)
     assert "Z = 0" in str(e.value)
+
+
+def test_product_path_never_imports_the_oracle():
+    """The library package and bench's own arm reach the oracle nowhere (it is test
+    infrastructure; only tests, smoke() and bench's CPU legs may call it)."""
+    import pathlib
+    import re
+    pkg = pathlib.Path(__file__).resolve().parents[1] / "paper_1810_03063_b300"
+    pat = re.compile(r"^\s*(from\s+oracle\b|import\s+oracle\b)|[\"']oracle/", re.M)
+    for f in pkg.rglob("*"):
+        if f.suffix in (".py", ".cu", ".cuh", ".cpp", ".hpp", ".h"):
+            assert not pat.search(f.read_text()), f
