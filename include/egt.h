@@ -109,6 +109,8 @@ typedef struct {
   int32_t T, n_fold;
   double Z, normA, M[2], Omega[2];
   int64_t table_bytes;   /* bytes of compiled tables uploaded by egt_create_game */
+  int64_t device_bytes;  /* device memory the game holds (tables and solver state); also
+                            filled for host-only games, so a caller can size admission */
 } egt_dims;
 
 /* Compile the game (betting tree, treeplex tables, hand/card tables) and
@@ -332,6 +334,66 @@ EGT_API egt_status egt_batch_member(const egt_batch* batch, int32_t slot, egt_ba
 
 /* Launch shape of the last egt_batch_step: CTAs per member and grid (host, either may be NULL). */
 EGT_API egt_status egt_batch_launch_shape(const egt_batch* batch, int32_t* group, int32_t* grid);
+
+/* ---- serving: continuous batching of solve requests ------------------------
+ * A server owns a batch on one device.  Requests (a game description and
+ * solve options) wait in a FIFO queue; each egt_server_step admits queued
+ * requests in order while their device memory (egt_dims.device_bytes) fits the
+ * budget, runs one egt_batch_step over all running requests, and retires the
+ * ones that stopped: their iterates are copied to host memory and their device
+ * memory released.  Running requests keep x, y, mu on the device between
+ * steps.  A request's result is bit for bit what egt_solve gives it alone. */
+typedef struct egt_server egt_server;
+
+typedef struct {
+  int64_t mem_budget_bytes;   /* device memory for running requests; 0: 90 % of the free memory
+                                 at creation (also the cap) */
+  int32_t max_running;        /* 0: no cap besides memory */
+  int32_t iters_per_step;     /* iterations per launch (0: 200) */
+  int32_t group;              /* CTAs per request (0: automatic, see egt_batch_step) */
+} egt_server_opts;
+
+typedef struct {
+  int32_t queued, running;
+  int64_t completed, launches, used_bytes, budget_bytes;
+  double clock;               /* seconds since the server was created */
+} egt_server_stats;
+
+typedef struct {
+  int32_t state;              /* 0 queued, 1 running, 2 done */
+  int32_t status;             /* egt_status once done (OK, NOT_CONVERGED, or the failure) */
+  double t_submit, t_admit, t_done;   /* server clock (seconds); -1 if not yet */
+  egt_solve_report rep;       /* once done: iterations, products, back-offs, residual, mu, tau */
+  int32_t S[2], ld;           /* result layout: x [S[0]][ld], y [S[1]][ld] */
+} egt_server_request_info;
+
+/* opts (host) may be NULL (defaults). */
+EGT_API egt_status egt_server_create(int32_t device, const egt_server_opts* opts, egt_server** out);
+EGT_API egt_status egt_server_destroy(egt_server* server);
+
+/* Seconds since the server was created (its clock for arrival and completion times). */
+EGT_API double egt_server_clock(const egt_server* server);
+
+/* Queue a request: the description is copied (the caller's arrays may be freed
+ * after the call); opts: variant, alpha / mu0, eps_mbb, max_iters, gap_every
+ * (replay and log are not accepted).  arrival: its arrival time on the server
+ * clock (< 0: now), the origin of its latency.  *id (host): its handle.
+ * OOM if the game alone exceeds the memory budget. */
+EGT_API egt_status egt_server_submit(egt_server* server, const egt_game_desc* desc,
+                                     const egt_solve_opts* opts, double arrival, int64_t* id);
+
+/* Admit, run one launch over the running requests, retire the finished ones.
+ * stats (host) may be NULL. */
+EGT_API egt_status egt_server_step(egt_server* server, egt_server_stats* stats, void* stream);
+
+/* State of a request; once done, its iterates are copied to x, y (host arrays
+ * of S[0] x ld and S[1] x ld floats, either may be NULL) and, if release != 0,
+ * the request is forgotten. */
+EGT_API egt_status egt_server_result(egt_server* server, int64_t id, egt_server_request_info* info,
+                                     float* x, float* y, int32_t release);
+
+/* "queued", "running" or "done". */
+EGT_API const char* egt_server_state_name(int32_t state);
 
 /* ---- per-kernel device time accounting -------------------------------------- */
 

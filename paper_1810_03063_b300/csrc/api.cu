@@ -107,12 +107,23 @@ struct egt_game {
   long long prof_n[EGT_KERNEL_KINDS] = {0};
   long long launches[EGT_KERNEL_KINDS] = {0};   // always counted, reset by egt_profile
   size_t table_bytes = 0;
+  size_t device_bytes = 0;       // tables + solver state on the device (known before upload)
 };
 
 namespace {
 
 size_t vec_elems(const egt_game* G, int p) { return (size_t)G->comp.tpx[p].S * G->ld; }
 size_t contrib_elems(const egt_game* G) { return std::max<size_t>(G->comp.term.size(), 1) * G->ld; }
+
+// Device bytes alloc_state takes (the sizes of alloc_state below).
+size_t state_bytes(const egt_game* G) {
+  const size_t n0 = vec_elems(G, 0), n1 = vec_elems(G, 1), nc = contrib_elems(G);
+  const size_t t0 = std::max(n0, nc), t1 = std::max(n1, nc);
+  const size_t floats = 2 * n0 + 2 * n1 + 4 * nc + t0 + t1 + 10 * 64;
+  return floats * sizeof(float) + 3 * nc * sizeof(double) + 1024 * sizeof(double) + 16 * 4 + 16 * 8 + 4 +
+         sizeof(EngineCtl) + 4 * (size_t)(G->ld / kSbrHands) * sizeof(double);
+}
+
 
 egt_status check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
@@ -336,7 +347,6 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
     for (int j = 0; j < C.tpx[p].J; ++j) th[p].log_n[j] = (float)std::log((double)C.tpx[p].inf_n[j]);
   }
 
-  if (!to_device) return EGT_OK;
   size_t bytes = 1 << 16;
   bytes += ld * (sizeof(uchar2) + sizeof(ushort2) + sizeof(uchar4) + sizeof(uint4)) + card_hands.size() * 2 +
            card_len.size() * 4;
@@ -347,6 +357,8 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
     bytes += (tptr[p].size() + 2 * topp[p].size()) * sizeof(int) + tcoef[p].size() * (sizeof(float) + sizeof(double));
   }
   bytes += 64 * 256;   // alignment slack
+  G->device_bytes = bytes + state_bytes(G);
+  if (!to_device) return EGT_OK;
   std::vector<char> host(bytes, 0);
   CUDA_TRY(cudaMalloc(&G->arena, bytes));
   char* hp = host.data();
@@ -1083,6 +1095,7 @@ egt_status egt_dims_query(const egt_game* G, egt_dims* o) {
   o->Z = G->Z;
   o->normA = G->normA;
   o->table_bytes = (int64_t)G->table_bytes;
+  o->device_bytes = (int64_t)G->device_bytes;
   return EGT_OK;
 }
 

@@ -48,7 +48,7 @@ class Dims(C.Structure):
     _fields_ = [("H", C.c_int32), ("ld", C.c_int32), ("S", C.c_int32 * 2), ("J", C.c_int32 * 2),
                 ("L", C.c_int32 * 2), ("T", C.c_int32), ("n_fold", C.c_int32), ("Z", C.c_double),
                 ("normA", C.c_double), ("M", C.c_double * 2), ("Omega", C.c_double * 2),
-                ("table_bytes", C.c_int64)]
+                ("table_bytes", C.c_int64), ("device_bytes", C.c_int64)]
 
 
 class IterLog(C.Structure):
@@ -73,6 +73,23 @@ class SolveReport(C.Structure):
 
 class BatchMemberInfo(C.Structure):
     _fields_ = [("active", C.c_int32), ("status", C.c_int32), ("rep", SolveReport)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_int64), ("max_running", C.c_int32),
+                ("iters_per_step", C.c_int32), ("group", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int32), ("running", C.c_int32), ("completed", C.c_int64),
+                ("launches", C.c_int64), ("used_bytes", C.c_int64), ("budget_bytes", C.c_int64),
+                ("clock", C.c_double)]
+
+
+class ServerRequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("rep", SolveReport),
+                ("S", C.c_int32 * 2), ("ld", C.c_int32)]
 
 
 class StepInfo(C.Structure):
@@ -111,6 +128,11 @@ _SIGS = {
     "egt_batch_step": [_vp, _i32, _i32, C.POINTER(_i32), _vp],
     "egt_batch_member": [_vp, _i32, C.POINTER(BatchMemberInfo)],
     "egt_batch_launch_shape": [_vp, C.POINTER(_i32), C.POINTER(_i32)],
+    "egt_server_create": [_i32, C.POINTER(ServerOpts), C.POINTER(_vp)],
+    "egt_server_destroy": [_vp],
+    "egt_server_submit": [_vp, C.POINTER(GameDesc), C.POINTER(SolveOpts), _f64, C.POINTER(C.c_int64)],
+    "egt_server_step": [_vp, C.POINTER(ServerStats), _vp],
+    "egt_server_result": [_vp, C.c_int64, C.POINTER(ServerRequestInfo), _vp, _vp, _i32],
     "egt_profile_read": [_vp, _vp, _vp],
 }
 KERNEL_KINDS = ("grad_f32", "grad_f64", "sbr", "br_f64", "engine")
@@ -121,6 +143,10 @@ for _name, _args in _SIGS.items():
     _fn.restype = C.c_int
 lib.egt_last_error.argtypes = []
 lib.egt_last_error.restype = C.c_char_p
+lib.egt_server_clock.argtypes = [_vp]
+lib.egt_server_clock.restype = C.c_double
+lib.egt_server_state_name.argtypes = [_i32]
+lib.egt_server_state_name.restype = C.c_char_p
 
 
 def declared_symbols(header=HEADER):
@@ -162,31 +188,36 @@ def _f64p(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def _desc(spec):
+    """egt_game_desc of a synth.GameSpec, with the arrays it points into (keep them alive)."""
+    keep = dict(
+        cards=np.ascontiguousarray(spec.hands, dtype=np.int32),
+        strength=np.ascontiguousarray(spec.strength, dtype=np.int32),
+        r0=np.ascontiguousarray(spec.ranges[0], dtype=np.float64),
+        r1=np.ascontiguousarray(spec.ranges[1], dtype=np.float64),
+        bets=np.ascontiguousarray(spec.bet_fracs, dtype=np.float64),
+    )
+    d = GameDesc()
+    d.n_cards = spec.n_cards
+    d.hand_size = spec.hand_size
+    d.n_hands = spec.n_hands
+    d.hand_cards = _i32p(keep["cards"])
+    d.strength = _i32p(keep["strength"])
+    d.range[0] = _f64p(keep["r0"])
+    d.range[1] = _f64p(keep["r1"])
+    d.pot, d.stack, d.bb = spec.pot, spec.stack, spec.bb
+    d.n_bets = len(spec.bet_fracs)
+    d.bet_fracs = _f64p(keep["bets"])
+    d.allin = int(spec.allin)
+    d.raise_cap = spec.raise_cap
+    return d, keep
+
+
 class Game:
     """One compiled river endgame on a device (owns its device memory)."""
 
     def __init__(self, spec, device=0, stream=None):
-        self._keep = dict(
-            cards=np.ascontiguousarray(spec.hands, dtype=np.int32),
-            strength=np.ascontiguousarray(spec.strength, dtype=np.int32),
-            r0=np.ascontiguousarray(spec.ranges[0], dtype=np.float64),
-            r1=np.ascontiguousarray(spec.ranges[1], dtype=np.float64),
-            bets=np.ascontiguousarray(spec.bet_fracs, dtype=np.float64),
-        )
-        k = self._keep
-        d = GameDesc()
-        d.n_cards = spec.n_cards
-        d.hand_size = spec.hand_size
-        d.n_hands = spec.n_hands
-        d.hand_cards = _i32p(k["cards"])
-        d.strength = _i32p(k["strength"])
-        d.range[0] = _f64p(k["r0"])
-        d.range[1] = _f64p(k["r1"])
-        d.pot, d.stack, d.bb = spec.pot, spec.stack, spec.bb
-        d.n_bets = len(spec.bet_fracs)
-        d.bet_fracs = _f64p(k["bets"])
-        d.allin = int(spec.allin)
-        d.raise_cap = spec.raise_cap
+        d, self._keep = _desc(spec)
         self._h = _vp()
         _check(lib.egt_create_game(C.byref(d), device, _stream(stream), C.byref(self._h)))
         self.spec = spec
@@ -202,6 +233,7 @@ class Game:
         self.M = (dims.M[0], dims.M[1])
         self.Omega = (dims.Omega[0], dims.Omega[1])
         self.table_bytes = dims.table_bytes
+        self.device_bytes = dims.device_bytes
         order = np.empty(self.H, dtype=np.int32)
         _check(lib.egt_hand_order(self._h, order.ctypes.data))
         self.order = order
@@ -431,3 +463,62 @@ class Batch:
             steps += 1
             if self.step(n_iters, group, stream) == 0:
                 return steps
+
+
+class Server:
+    """Continuous batching of solve requests on one device (egt_server_*)."""
+
+    def __init__(self, device=0, mem_budget_bytes=0, max_running=0, iters_per_step=200, group=0):
+        o = ServerOpts(mem_budget_bytes, max_running, iters_per_step, group)
+        self._h = _vp()
+        _check(lib.egt_server_create(device, C.byref(o), C.byref(self._h)))
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib.egt_server_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def clock(self):
+        return lib.egt_server_clock(self._h)
+
+    def submit(self, spec, arrival=-1.0, variant=EGT_AS, alpha=0.01, eps_mbb=1.0, max_iters=20000,
+               gap_every=1):
+        d, keep = _desc(spec)
+        o, _, _ = Game._opts(variant=variant, alpha=alpha, eps_mbb=eps_mbb, max_iters=max_iters,
+                             gap_every=gap_every)
+        rid = C.c_int64()
+        _check(lib.egt_server_submit(self._h, C.byref(d), C.byref(o), float(arrival), C.byref(rid)))
+        return rid.value
+
+    def step(self, stream=None):
+        st = ServerStats()
+        _check(lib.egt_server_step(self._h, C.byref(st), _stream(stream)))
+        return dict(queued=st.queued, running=st.running, completed=st.completed, launches=st.launches,
+                    used_bytes=st.used_bytes, budget_bytes=st.budget_bytes, clock=st.clock)
+
+    def result(self, rid, release=True, iterates=True):
+        """State of a request; once done also its iterates (host numpy [S][ld]) and report."""
+        info = ServerRequestInfo()
+        _check(lib.egt_server_result(self._h, rid, C.byref(info), None, None, 0))
+        out = dict(state=lib.egt_server_state_name(info.state).decode(), status=STATUS[info.status],
+                   t_submit=info.t_submit, t_admit=info.t_admit, t_done=info.t_done)
+        if info.state == 2:
+            r = info.rep
+            out.update(iters=r.iters, products=r.products, backoffs=r.backoffs, gap_mbb=r.gap_mbb,
+                       mu=(r.mu[0], r.mu[1]), tau=r.tau, latency=info.t_done - info.t_submit)
+            x = y = None
+            if iterates:
+                x = np.empty((info.S[0], info.ld), np.float32)
+                y = np.empty((info.S[1], info.ld), np.float32)
+            _check(lib.egt_server_result(self._h, rid, C.byref(info),
+                                         x.ctypes.data if x is not None else None,
+                                         y.ctypes.data if y is not None else None, int(release)))
+            out.update(x=x, y=y)
+        return out
