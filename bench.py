@@ -59,6 +59,15 @@ def parse():
     ap.add_argument("--batch-games", type=int, default=64,
                     help="games of the batched measurement (the mixed 20/52-card endgames); 0 skips it")
     ap.add_argument("--batch-iters", type=int, default=200, help="iterations per game in the batched measurement")
+    ap.add_argument("--serve", action="store_true",
+                    help="instead of the iteration benchmark: Poisson request streams through egt_server_*")
+    ap.add_argument("--variants", action="store_true",
+                    help="instead of the iteration benchmark: gap against gradient products for theory EGT, "
+                         "practical EGT and EGT/as")
+    ap.add_argument("--variant-iters", type=int, default=20000)
+    ap.add_argument("--serve-rates", default="10,100,500", help="arrival rates (requests/s)")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests per rate")
+    ap.add_argument("--serve-iters", type=int, default=200, help="iterations per server launch")
     ap.add_argument("--engine", default="device", choices=["device", "host"],
                     help="device: each step is one egt_iterate launch; host: egt_step + egt_state_gap per iteration")
     return ap.parse_args()
@@ -374,6 +383,127 @@ def run_batched(args, local):
             "l2": "flushed before each timed pass"}
 
 
+def serve_requests(n, rate, seed):
+    """n requests: arrival times of a Poisson stream at `rate`, each a full-deck game (bets {0.5, 1},
+    cap 3) or a large one (bets {0.25, 0.5, 1, 2}, cap 4) with probability 1/2 and a fresh seed, gap
+    target log-uniform in [0.5, 5] mbb/hand."""
+    import numpy as np
+
+    from paper_1810_03063_b300 import synth
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    reqs = []
+    for i in range(n):
+        s = seed + 1000 + i
+        spec = synth.full_deck(seed=s) if rng.random() < 0.5 else synth.large(seed=s)
+        eps = float(np.exp(rng.uniform(np.log(0.5), np.log(5.0))))
+        reqs.append((float(arrivals[i]), spec, eps))
+    return reqs
+
+
+def run_serve(args, local):
+    """Served solves/s and latency percentiles: each request arrives at its Poisson time, waits in
+    the server's queue, runs in the continuous batch until its own gap target, and is answered
+    with its iterates on the host.  Beside it, the same requests solved one after the other with
+    egt_solve (one game per launch, all CTAs), the plain GPU EGT."""
+    import numpy as np
+    import torch
+
+    from paper_1810_03063_b300 import egt
+
+    torch.cuda.set_device(local)
+    out = []
+    for rate in [float(r) for r in args.serve_rates.split(",")]:
+        reqs = serve_requests(args.serve_requests, rate, synth_seed(rate))
+        srv = egt.Server(local, iters_per_step=args.serve_iters)
+        t0 = srv.clock()
+        ids, nxt = [], 0
+        while True:
+            now = srv.clock() - t0
+            while nxt < len(reqs) and reqs[nxt][0] <= now:
+                a, spec, eps = reqs[nxt]
+                ids.append(srv.submit(spec, arrival=t0 + a, eps_mbb=eps, max_iters=40000))
+                nxt += 1
+            st = srv.step()
+            if st["queued"] == 0 and st["running"] == 0:
+                if nxt == len(reqs):
+                    break
+                time.sleep(max(0.0, reqs[nxt][0] - (srv.clock() - t0)))
+        res = [srv.result(i, iterates=True) for i in ids]
+        srv.close()
+        lat = np.array([r["latency"] for r in res])
+        span = max(r["t_done"] for r in res) - (t0 + reqs[0][0])
+        ok = sum(r["status"] == "EGT_OK" for r in res)
+        out.append({"rate": rate, "requests": len(res), "reached": ok,
+                    "solves_per_s": round(len(res) / span, 3),
+                    "latency_p50_s": round(float(np.percentile(lat, 50)), 3),
+                    "latency_p99_s": round(float(np.percentile(lat, 99)), 3),
+                    "launches": st["launches"], "iters_mean": round(float(np.mean([r["iters"] for r in res])), 1)})
+    # the plain GPU EGT: the last rate's requests solved one at a time, back to back
+    t = time.perf_counter()
+    for a, spec, eps in reqs:
+        g = egt.Game(spec, device=local)
+        x = torch.empty((g.S[0], g.ld), device="cuda")
+        y = torch.empty((g.S[1], g.ld), device="cuda")
+        g.solve(x, y, variant=egt.EGT_AS, alpha=0.01, eps_mbb=eps, max_iters=40000, gap_every=1)
+        x.cpu(), y.cpu()
+        g.close()
+    seq = time.perf_counter() - t
+    return {"metric": "served solves/s", "unit": "solves/s", "higher_is_better": True,
+            "workload": "Poisson request streams; each request a full-deck (52 cards, bets {0.5,1}, cap 3) or "
+                        "large (bets {0.25,0.5,1,2}, cap 4) river endgame with probability 1/2, fresh seed, "
+                        "gap target log-uniform in [0.5, 5] mbb/hand, EGT/as",
+            "iters_per_launch": args.serve_iters, "rates": out,
+            "one_game_per_launch": {"requests": len(reqs), "solves_per_s": round(len(reqs) / seq, 3),
+                                    "seconds": round(seq, 2)},
+            "data": "synthetic"}
+
+
+def run_variants(args, local):
+    """Sec. 7's comparison of the EGT variants on synthetic endgames: the FP64 saddle-point gap
+    after every iteration against the gradient products spent (3 per Step; a back-off of Alg. 4
+    spends 3 more), until 1 mbb/hand or --variant-iters iterations."""
+    import torch
+
+    from paper_1810_03063_b300 import egt, synth
+
+    torch.cuda.set_device(local)
+    names = {egt.THEORY: "EGT, Alg. 1 (theory mu, tau_t = 2/(t+3))",
+             egt.PRACTICAL: "EGT (tuned mu, alpha 0.01, balancing)",
+             egt.EGT_AS: "EGT/as (Alg. 3 + 4, alpha 0.01)"}
+    games = {"tiny (20 cards)": synth.tiny(), "full deck (52 cards)": synth.full_deck()}
+    marks = [10 ** k for k in range(1, 7)]
+    out = []
+    for gname, spec in games.items():
+        g = egt.Game(spec, device=local)
+        for v, vname in names.items():
+            n = args.variant_iters
+            rep = g.solve(variant=v, alpha=0.01, eps_mbb=1.0, max_iters=n, gap_every=1, log_cap=n)
+            log = rep.get("log", [])
+            # gap after the iteration at which each mark was first reached (the log's gap_mbb is the
+            # residual before that iteration's update; the next entry holds it after)
+            gaps, prod, k = [], 0, 0
+            for i, e in enumerate(log):
+                prod += 3 * (1 + e["backoffs"])
+                after = log[i + 1]["gap_mbb"] if i + 1 < len(log) else rep["gap_mbb"]
+                while k < len(marks) and prod >= marks[k]:
+                    gaps.append({"products": marks[k], "gap_mbb": round(after, 4)})
+                    k += 1
+            out.append({"game": gname, "variant": vname, "status": rep["status"], "iters": rep["iters"],
+                        "products": rep["products"], "backoffs": rep["backoffs"],
+                        "final_gap_mbb": round(rep["gap_mbb"], 4), "seconds": round(rep["seconds"], 3),
+                        "gap_at_products": gaps})
+        g.close()
+    return {"study": "gap vs gradient products by EGT variant", "target_mbb": 1.0,
+            "max_iters": args.variant_iters, "data": "synthetic", "runs": out}
+
+
+def synth_seed(rate):
+    from paper_1810_03063_b300 import synth
+    return synth.BASE_SEED + 500 + int(rate)
+
+
 def oracle_iterations(seconds, max_iters=None, seed=None):
     """The FP64 oracle's EGT/as on the same game: (iterations done, seconds, threads)."""
     from oracle import egt as OE
@@ -447,6 +577,16 @@ def main():
     if args.impl == "reference":
         out = run_reference(args, world, rank)
         if out is not None:
+            print(json.dumps(out))
+        return
+    if args.variants:
+        out = run_variants(args, local)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    if args.serve:
+        out = run_serve(args, local)
+        if rank == 0:
             print(json.dumps(out))
         return
     r = run_ours(args, world, rank, local)

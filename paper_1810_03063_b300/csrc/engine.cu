@@ -77,8 +77,9 @@ __device__ bool grid_sync(const GridBar& b, unsigned long long& k, PhaseClock* c
   if (threadIdx.x == 0) {
     if (clock_cta) clk->arrive = global_ns();
     int ok = 1;
-    __threadfence();                       // release this CTA's writes of the phase
-    atomicAdd(b.arrive, 1ull);
+    // arrival with release semantics at GPU scope: the CTA barrier above ordered every
+    // thread's writes of the phase before it (cumulativity), no separate fence needed
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(b.arrive) : "memory");
     const unsigned long long target = k * b.expected;
     unsigned int polls = 0;
     unsigned long long t0 = 0;

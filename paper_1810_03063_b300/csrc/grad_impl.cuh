@@ -221,20 +221,102 @@ __device__ __forceinline__ unsigned long long fx_round(const Wide& w, int s, int
 }
 
 // FP32 value of a fixed-point sum, a x 2^-ex correctly rounded (all 87 bits of
-// the sum count, not only its integer part), with integer operations.
+// the sum count, not only its integer part), with integer operations.  The
+// fraction limb is first carried into [0, 2^40); when the integer limb alone
+// holds 24 or more bits it decides the significand (the fraction only breaks
+// ties), else the whole magnitude fits 64 bits.  Subnormal and overflowing
+// results take the general path.
 __device__ __forceinline__ float fx_to_f32(Fx a, int ex) {
-  const Wide w = fx_wide(a);
-  if (w.nb == 0) return 0.f;
-  const unsigned bits = (unsigned)fx_round(w, -40 - ex, 24, -126, 127);
-  return __uint_as_float(((unsigned)w.neg << 31) | bits);
+  const long long v0 = a.v0 + (a.v1 >> 40);
+  const unsigned long long f = (unsigned long long)a.v1 & ((1ull << 40) - 1ull);
+  const bool neg = v0 < 0;
+  const unsigned long long m0 = neg ? (unsigned long long)(-(v0 + (f ? 1 : 0))) : (unsigned long long)v0;
+  const unsigned long long m1 = neg ? (f ? (1ull << 40) - f : 0ull) : f;
+  if (m0 == 0 && m1 == 0) return 0.f;
+  unsigned long long q;
+  int e;
+  if (m0 >= (1ull << 24)) {
+    const int nb = 64 - __clzll(m0);
+    const int sh = nb - 24;
+    q = m0 >> sh;
+    const unsigned long long rem = m0 & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m1 != 0 || (q & 1ull)))) ++q;
+    e = nb - 1 - ex;
+  } else {
+    const unsigned long long u = (m0 << 40) | m1;
+    const int nb = 64 - __clzll(u);
+    if (nb <= 24) {
+      q = u << (24 - nb);
+    } else {
+      const int sh = nb - 24;
+      q = u >> sh;
+      const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+      if (rem > half || (rem == half && (q & 1ull))) ++q;
+    }
+    e = nb - 1 - 40 - ex;
+  }
+  if (q == (1ull << 24)) {
+    q >>= 1;
+    ++e;
+  }
+  if (e + 127 < 1 || e + 127 > 254) {
+    const Wide w = fx_wide(a);
+    return __uint_as_float(((unsigned)w.neg << 31) | (unsigned)fx_round(w, -40 - ex, 24, -126, 127));
+  }
+  return __uint_as_float(((unsigned)neg << 31) | ((unsigned)(e + 127) << 23) | (unsigned)(q & 0x7fffffull));
 }
 
-// FP64 value of a fixed-point sum, a x 2^-ex correctly rounded, with integer operations.
+// FP64 value of a fixed-point sum, a x 2^-ex correctly rounded, with integer
+// operations: as fx_to_f32, with the middle case (the integer limb holds 24 to
+// 52 bits) completed by the leading bits of the fraction limb.
 __device__ __forceinline__ double fx_to_f64(Fx a, int ex) {
-  const Wide w = fx_wide(a);
-  if (w.nb == 0) return 0.0;
-  const unsigned long long bits = fx_round(w, -40 - ex, 53, -1022, 1023);
-  return __longlong_as_double((long long)(((unsigned long long)w.neg << 63) | bits));
+  const long long v0 = a.v0 + (a.v1 >> 40);
+  const unsigned long long f = (unsigned long long)a.v1 & ((1ull << 40) - 1ull);
+  const bool neg = v0 < 0;
+  const unsigned long long m0 = neg ? (unsigned long long)(-(v0 + (f ? 1 : 0))) : (unsigned long long)v0;
+  const unsigned long long m1 = neg ? (f ? (1ull << 40) - f : 0ull) : f;
+  if (m0 == 0 && m1 == 0) return 0.0;
+  unsigned long long q;
+  int e;
+  if (m0 >= (1ull << 53)) {
+    const int nb = 64 - __clzll(m0);
+    const int sh = nb - 53;
+    q = m0 >> sh;
+    const unsigned long long rem = m0 & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m1 != 0 || (q & 1ull)))) ++q;
+    e = nb - 1 - ex;
+  } else if (m0 >= (1ull << 24)) {
+    const int nb = 64 - __clzll(m0);      // 25 .. 53
+    const int k = 53 - nb;                 // bits taken from the fraction limb, 0 .. 28
+    q = (m0 << k) | (m1 >> (40 - k));
+    const int rb = 39 - k;                 // rounding bit of m1
+    const unsigned long long round = (m1 >> rb) & 1ull, sticky = m1 & ((1ull << rb) - 1ull);
+    if (round && (sticky != 0 || (q & 1ull))) ++q;
+    e = nb - 1 - ex;
+  } else {
+    const unsigned long long u = (m0 << 40) | m1;
+    const int nb = 64 - __clzll(u);
+    if (nb <= 53) {
+      q = u << (53 - nb);
+    } else {
+      const int sh = nb - 53;
+      q = u >> sh;
+      const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+      if (rem > half || (rem == half && (q & 1ull))) ++q;
+    }
+    e = nb - 1 - 40 - ex;
+  }
+  if (q == (1ull << 53)) {
+    q >>= 1;
+    ++e;
+  }
+  if (e + 1023 < 1 || e + 1023 > 2046) {
+    const Wide w = fx_wide(a);
+    return __longlong_as_double(
+        (long long)(((unsigned long long)w.neg << 63) | fx_round(w, -40 - ex, 53, -1022, 1023)));
+  }
+  return __longlong_as_double((long long)(((unsigned long long)neg << 63) |
+                                          ((unsigned long long)(e + 1023) << 52) | (q & ((1ull << 52) - 1ull))));
 }
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
