@@ -79,7 +79,21 @@ typedef enum {
  * range[p]: [n_hands] >= 0 finite, not all zero; normalised internally.
  * pot, stack: chips (stack = remaining chips of each player, equal stacks).
  * bb: chips per big blind; gaps are reported in mbb = bb / 1000 per hand.
- * bet_fracs: [n_bets] pot fractions > 0 in menu order. */
+ * bet_fracs: [n_bets] pot fractions > 0 in menu order.
+ * menus: NULL = the one menu (bet_fracs, allin) for every decision, no fold
+ *   unless facing a bet.  Else [2][4] menus, menus[p][k] for player p after k
+ *   bets or raises in the river so far (k = 3 for three or more): the pot
+ *   fractions of its bets / raises, whether all-in is offered and whether fold
+ *   is offered when not facing a bet (Sec. 7's Libratus abstraction gives
+ *   each player its own sizes for the opening, facing the first bet, facing a
+ *   raise and facing later raises).  raise_cap still bounds the bets. */
+typedef struct {
+  int32_t n;              /* sizes */
+  const double* fracs;    /* [n] pot fractions > 0 in menu order */
+  int32_t allin;          /* all-in offered */
+  int32_t fold;           /* fold offered when not facing a bet */
+} egt_menu;
+
 typedef struct {
   int32_t n_cards;
   int32_t hand_size;
@@ -94,6 +108,7 @@ typedef struct {
   const double* bet_fracs;
   int32_t allin;
   int32_t raise_cap;
+  const egt_menu* menus;  /* NULL or [2][4], see above */
 } egt_game_desc;
 
 /* Sizes and constants of a compiled game.

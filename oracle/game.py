@@ -16,6 +16,17 @@ this reading, applied identically by the CUDA library):
 * ``raise_cap`` counts the opening bet plus the raises;
 * no fold when not facing a bet; check-check and call go to showdown.
 
+Sec. 7 describes Libratus' abstraction with a different menu per player and
+per betting situation (its opening, facing the first bet, facing a raise,
+facing later raises) and with fold offered even when not facing a bet.  With
+``menus`` given, the menu of a decision is ``menus[player][min(k, 3)]`` with
+k the bets and raises made so far: (pot fractions, all-in offered, fold
+offered when not facing a bet); every other rule above is unchanged.  When
+player 1 folds before player 2 has acted, player 2 gets a decision with the one
+action "pass" before that terminal: the game (and its value) is unchanged, and
+every terminal keeps a sequence of both players, so the objective stays
+bilinear with no affine term (y's pass coordinate is always 1).
+
 Payoffs are to player 2 (the maximiser y of min_x max_y <x, Ay>): the loser of
 a fold or showdown pays ``pot / 2`` plus their river chips, a tie pays 0.
 
@@ -41,7 +52,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-FOLD, CHECK, CALL, BET, ALLIN = "f", "k", "c", "b", "a"
+FOLD, CHECK, CALL, BET, ALLIN, PASS = "f", "k", "c", "b", "a", "p"
 
 
 @dataclass
@@ -57,10 +68,16 @@ class PublicNode:
     folder: int = -1
 
 
-def build_public_tree(pot, stack, bet_fracs, allin, raise_cap):
+def build_public_tree(pot, stack, bet_fracs, allin, raise_cap, menus=None):
     """Enumerate the public betting tree under the rules in the module docstring."""
     nodes: list[PublicNode] = []
     eps = 1e-12
+
+    def menu_of(player, n_bets):
+        if menus is None:
+            return tuple(bet_fracs), bool(allin), False
+        fr, al, fo = menus[player][min(n_bets, 3)]
+        return tuple(fr), bool(al), bool(fo)
 
     def visit(player, contrib, n_bets, history, parent):
         node = PublicNode(pre=len(nodes), player=player, contrib=contrib, n_bets=n_bets,
@@ -69,23 +86,35 @@ def build_public_tree(pot, stack, bet_fracs, allin, raise_cap):
         me, opp = player, 1 - player
         to_call = contrib[opp] - contrib[me]
         remaining = stack - contrib[me]
+        fracs, can_allin, fold_unfacing = menu_of(player, n_bets)
         acts = []
         if to_call > 0:
             acts.append((FOLD, 0.0))
             acts.append((CALL, to_call))
         else:
+            if fold_unfacing:
+                acts.append((FOLD, 0.0))
             acts.append((CHECK, 0.0))
         if n_bets < raise_cap:
             pot_total = pot + contrib[0] + contrib[1]
-            for i, f in enumerate(bet_fracs):
+            for i, f in enumerate(fracs):
                 add = to_call + f * (pot_total + to_call)
                 if add < remaining - eps:
                     acts.append((f"{BET}{i}", add))
-            if allin and remaining > to_call + eps:
+            if can_allin and remaining > to_call + eps:
                 acts.append((ALLIN, remaining))
         for label, add in acts:
             h = history + ((player, label),)
-            if label == FOLD:
+            if label == FOLD and player == 0 and parent < 0:
+                q = PublicNode(pre=len(nodes), player=1, contrib=contrib, n_bets=n_bets, history=h,
+                               parent=node.pre)
+                nodes.append(q)
+                node.actions.append((label, q.pre))
+                t = PublicNode(pre=len(nodes), player=-1, contrib=contrib, n_bets=n_bets,
+                               history=h + ((1, PASS),), parent=q.pre, kind="fold", folder=0)
+                nodes.append(t)
+                q.actions.append((PASS, t.pre))
+            elif label == FOLD:
                 t = PublicNode(pre=len(nodes), player=-1, contrib=contrib, n_bets=n_bets,
                                history=h, parent=node.pre, kind="fold", folder=me)
                 nodes.append(t)
@@ -171,8 +200,8 @@ class SequenceForm:
     seq_labels: tuple   # per player: list of public histories ending with that sequence's action
 
 
-def sequence_form(pot, stack, bet_fracs, allin, raise_cap) -> SequenceForm:
-    nodes = build_public_tree(pot, stack, bet_fracs, allin, raise_cap)
+def sequence_form(pot, stack, bet_fracs, allin, raise_cap, menus=None) -> SequenceForm:
+    nodes = build_public_tree(pot, stack, bet_fracs, allin, raise_cap, menus)
 
     # information sets of each player with their parent (public) sequence
     info = [[], []]

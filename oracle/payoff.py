@@ -28,7 +28,8 @@ from . import game as G
 class _Base:
     def __init__(self, spec):
         self.spec = spec
-        self.sf = G.sequence_form(spec.pot, spec.stack, spec.bet_fracs, spec.allin, spec.raise_cap)
+        self.sf = G.sequence_form(spec.pot, spec.stack, spec.bet_fracs, spec.allin, spec.raise_cap,
+                                  getattr(spec, "menus", None))
         self.tpx = self.sf.tpx
         self.H = spec.n_hands
         self.S = (self.tpx[0].n_seq, self.tpx[1].n_seq)

@@ -146,6 +146,14 @@ egt_status validate(const egt_game_desc* d) {
     if (!(d->bet_fracs[i] > 0) || !std::isfinite(d->bet_fracs[i]))
       return fail(EGT_ERR_INVALID_ARG, "bet fractions must be > 0 and finite");
   if (d->raise_cap < 0) return fail(EGT_ERR_INVALID_ARG, "raise_cap < 0");
+  if (d->menus)
+    for (int m = 0; m < 8; ++m) {
+      const egt_menu& mu = d->menus[m];
+      if (mu.n < 0 || (mu.n > 0 && !mu.fracs)) return fail(EGT_ERR_INVALID_ARG, "bad bet menu");
+      for (int i = 0; i < mu.n; ++i)
+        if (!(mu.fracs[i] > 0) || !std::isfinite(mu.fracs[i]))
+          return fail(EGT_ERR_INVALID_ARG, "menu pot fractions must be finite and > 0");
+    }
   const int H = d->n_hands, k = d->hand_size;
   std::vector<std::pair<int, int>> seen;
   seen.reserve(H);
@@ -1034,8 +1042,16 @@ egt_status egt_create_game(const egt_game_desc* desc, int32_t device, void* stre
     delete G;
     return fail(EGT_ERR_INVALID_ARG, "n_hands above 1536");
   }
-  std::string err = compile_betting(desc->pot, desc->stack, desc->bet_fracs, desc->n_bets,
-                                    desc->allin != 0, desc->raise_cap, G->comp);
+  Menus menus = uniform_menus(desc->bet_fracs, desc->n_bets, desc->allin != 0);
+  if (desc->menus)
+    for (int p = 0; p < 2; ++p)
+      for (int k = 0; k < 4; ++k) {
+        const egt_menu& mu = desc->menus[4 * p + k];
+        menus.m[p][k].fracs.assign(mu.fracs, mu.fracs + mu.n);
+        menus.m[p][k].allin = mu.allin != 0;
+        menus.m[p][k].fold = mu.fold != 0;
+      }
+  std::string err = compile_betting(desc->pot, desc->stack, menus, desc->raise_cap, G->comp);
   if (!err.empty()) {
     delete G;
     return fail(EGT_ERR_INVALID_ARG, err);

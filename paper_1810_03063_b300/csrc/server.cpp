@@ -44,6 +44,8 @@ struct Request {
   std::vector<int32_t> cards;
   std::vector<int32_t> strength;
   std::vector<double> r0, r1, bets;
+  std::vector<egt_menu> menus;
+  std::vector<std::vector<double>> menu_fracs;
   egt_game_desc desc{};
   egt_solve_opts opts{};
   int64_t bytes = 0;
@@ -216,6 +218,16 @@ egt_status egt_server_submit(egt_server* V, const egt_game_desc* d, const egt_so
   r.desc.range[0] = r.r0.data();
   r.desc.range[1] = r.r1.data();
   r.desc.bet_fracs = r.bets.empty() ? nullptr : r.bets.data();
+  if (d->menus) {
+    r.menus.assign(d->menus, d->menus + 8);
+    r.menu_fracs.resize(8);
+    for (int m = 0; m < 8; ++m) {
+      if (r.menus[m].n > 0 && r.menus[m].fracs)
+        r.menu_fracs[m].assign(r.menus[m].fracs, r.menus[m].fracs + r.menus[m].n);
+      r.menus[m].fracs = r.menu_fracs[m].empty() ? nullptr : r.menu_fracs[m].data();
+    }
+    r.desc.menus = r.menus.data();
+  }
   r.opts = *o;
   r.opts.log = nullptr;
   r.opts.log_cap = 0;

@@ -8,13 +8,23 @@
 namespace egt {
 
 namespace {
-enum : int { A_FOLD = 0, A_CHECK = 1, A_CALL = 2, A_ALLIN = 3, A_BET0 = 16 };
+enum : int { A_FOLD = 0, A_CHECK = 1, A_CALL = 2, A_ALLIN = 3, A_PASS = 4, A_BET0 = 16 };
 constexpr double kEps = 1e-12;
 constexpr size_t kMaxNodes = 1u << 22;
 }  // namespace
 
-std::string compile_betting(double pot, double stack, const double* fracs, int n_fracs,
-                            bool allin, int cap, Compiled& out) {
+Menus uniform_menus(const double* fracs, int n_fracs, bool allin) {
+  Menus m;
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < 4; ++k) {
+      m.m[p][k].fracs.assign(fracs, fracs + n_fracs);
+      m.m[p][k].allin = allin;
+      m.m[p][k].fold = false;
+    }
+  return m;
+}
+
+std::string compile_betting(double pot, double stack, const Menus& menus, int cap, Compiled& out) {
   auto& nodes = out.nodes;
   nodes.clear();
   std::string err;
@@ -38,24 +48,47 @@ std::string compile_betting(double pot, double stack, const double* fracs, int n
     const int me = player, opp = 1 - player;
     const double to_call = c[opp] - c[me];
     const double remaining = stack - c[me];
+    const Menu& menu = menus.m[me][std::min(n_bets, 3)];
     std::vector<std::pair<int, double>> acts;
     if (to_call > 0) {
       acts.push_back({A_FOLD, 0.0});
       acts.push_back({A_CALL, to_call});
     } else {
+      if (menu.fold) acts.push_back({A_FOLD, 0.0});
       acts.push_back({A_CHECK, 0.0});
     }
     if (n_bets < cap) {
       const double pot_total = pot + c[0] + c[1];
-      for (int i = 0; i < n_fracs; ++i) {
-        const double add = to_call + fracs[i] * (pot_total + to_call);
-        if (add < remaining - kEps) acts.push_back({A_BET0 + i, add});
+      for (size_t i = 0; i < menu.fracs.size(); ++i) {
+        const double add = to_call + menu.fracs[i] * (pot_total + to_call);
+        if (add < remaining - kEps) acts.push_back({A_BET0 + (int)i, add});
       }
-      if (allin && remaining > to_call + kEps) acts.push_back({A_ALLIN, remaining});
+      if (menu.allin && remaining > to_call + kEps) acts.push_back({A_ALLIN, remaining});
     }
     for (auto& [code, add] : acts) {
       if (!err.empty()) return -1;
-      if (code == A_FOLD) {
+      if (code == A_FOLD && me == 0 && parent < 0) {
+        // player 1 folds before player 2 has acted (a menu with fold when not facing a
+        // bet): player 2 gets a one-action decision before the terminal, so that every
+        // terminal has a sequence of both players (no affine term in the objective)
+        int q = (int)nodes.size();
+        nodes.emplace_back();
+        nodes[q].player = 1;
+        nodes[q].c[0] = c0;
+        nodes[q].c[1] = c1;
+        nodes[q].n_bets = n_bets;
+        nodes[q].parent = me_idx;
+        nodes[me_idx].actions.push_back({code, q});
+        int t = (int)nodes.size();
+        nodes.emplace_back();
+        nodes[t].c[0] = c0;
+        nodes[t].c[1] = c1;
+        nodes[t].n_bets = n_bets;
+        nodes[t].parent = q;
+        nodes[t].kind = 0;
+        nodes[t].folder = 0;
+        nodes[q].actions.push_back({A_PASS, t});
+      } else if (code == A_FOLD) {
         int t = (int)nodes.size();
         nodes.emplace_back();
         nodes[t].c[0] = c0;

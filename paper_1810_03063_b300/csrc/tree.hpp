@@ -4,11 +4,12 @@
 // Game (Sec. 7 "Experiments", subgame description): chance deals private
 // hands from each player's range, player 1 acts first, fold ends the game,
 // call or check-check goes to showdown (better hand wins, tie splits).
-// Betting rules applied to the menu (equal stacks, bet = f * pot_total,
+// Betting rules applied to the menus (equal stacks, bet = f * pot_total,
 // raise = call + f * (pot_total + call), sizes reaching the stack dropped,
 // all-in while under the cap and chips remain, cap counts the opening bet and
-// raises, no fold when not facing a bet) are the synthetic games' reading of
-// the Libratus menus; they are stated in include/egt.h as well.
+// raises, fold when not facing a bet only where the menu offers it) are the
+// reading of Sec. 7's Libratus menus; the menu of a decision depends on the
+// player and on the bets / raises made so far (0, 1, 2, 3 or more).
 //
 // Canonical numbering (stated in include/egt.h): public tree depth first with
 // actions fold, check/call, menu sizes, all-in; information sets of a player
@@ -55,6 +56,18 @@ struct Terminal {
   double coef;       // fold: payoff to player 2; showdown: stake (pot/2 + chips)
 };
 
+// The menu of one decision situation.
+struct Menu {
+  std::vector<double> fracs;
+  bool allin = true;
+  bool fold = false;     // fold offered when not facing a bet
+};
+
+// menus[p][k]: player p after k bets / raises (k = 3: three or more)
+struct Menus {
+  Menu m[2][4];
+};
+
 struct Compiled {
   std::vector<PubNode> nodes;
   Treeplex tpx[2];
@@ -62,7 +75,9 @@ struct Compiled {
 };
 
 // Build the public tree and both treeplexes. Returns "" on success, else a message.
-std::string compile_betting(double pot, double stack, const double* fracs, int n_fracs,
-                            bool allin, int cap, Compiled& out);
+std::string compile_betting(double pot, double stack, const Menus& menus, int cap, Compiled& out);
+
+// The same menu everywhere (no fold unless facing a bet).
+Menus uniform_menus(const double* fracs, int n_fracs, bool allin);
 
 }  // namespace egt

@@ -36,12 +36,17 @@ class EGTError(RuntimeError):
         self.status = status
 
 
+class Menu(C.Structure):
+    _fields_ = [("n", C.c_int32), ("fracs", C.POINTER(C.c_double)), ("allin", C.c_int32),
+                ("fold", C.c_int32)]
+
+
 class GameDesc(C.Structure):
     _fields_ = [("n_cards", C.c_int32), ("hand_size", C.c_int32), ("n_hands", C.c_int32),
                 ("hand_cards", C.POINTER(C.c_int32)), ("strength", C.POINTER(C.c_int32)),
                 ("range", C.POINTER(C.c_double) * 2), ("pot", C.c_double), ("stack", C.c_double),
                 ("bb", C.c_double), ("n_bets", C.c_int32), ("bet_fracs", C.POINTER(C.c_double)),
-                ("allin", C.c_int32), ("raise_cap", C.c_int32)]
+                ("allin", C.c_int32), ("raise_cap", C.c_int32), ("menus", C.POINTER(Menu))]
 
 
 class Dims(C.Structure):
@@ -210,6 +215,17 @@ def _desc(spec):
     d.bet_fracs = _f64p(keep["bets"])
     d.allin = int(spec.allin)
     d.raise_cap = spec.raise_cap
+    menus = getattr(spec, "menus", None)
+    if menus is not None:
+        arr = (Menu * 8)()
+        for p in range(2):
+            for k in range(4):
+                fr, allin, fold = menus[p][k]
+                a = np.ascontiguousarray(fr, dtype=np.float64)
+                keep[f"menu{p}{k}"] = a
+                arr[4 * p + k] = Menu(len(fr), _f64p(a) if len(fr) else None, int(allin), int(fold))
+        keep["menus"] = arr
+        d.menus = C.cast(arr, C.POINTER(Menu))
     return d, keep
 
 

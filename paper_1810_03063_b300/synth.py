@@ -54,6 +54,9 @@ class GameSpec:
     raise_cap: int
     seed: int = -1
     meta: dict = field(default_factory=dict)
+    # None: the menu (bet_fracs, allin) everywhere.  Else menus[p][k] = (pot fractions, all-in
+    # offered, fold offered when not facing a bet) for player p after k bets / raises (k = 3: 3+)
+    menus: tuple = None
 
     @property
     def n_hands(self) -> int:
@@ -129,6 +132,32 @@ def kuhn() -> GameSpec:
     return GameSpec(name="kuhn", n_cards=3, hand_size=1, board=(), hands=hands,
                     strength=np.arange(3, dtype=np.int32), ranges=np.full((2, 3), 1.0 / 3.0),
                     pot=2.0, stack=1.0, bb=1.0, bet_fracs=(0.5,), allin=True, raise_cap=1, seed=-1)
+
+
+# Sec. 7's Libratus river abstraction (Libratus = player 1, first to act), per player and number
+# of bets / raises so far: (pot fractions, all-in offered, fold offered when not facing a bet).
+LIBRATUS_MENUS = (
+    (((0.25, 0.5, 1.0, 2.0, 4.0, 8.0), True, True),   # opening: fold, check, six bets, all-in
+     ((0.4, 0.7, 1.1, 2.0), True, False),              # after its check, facing the bet
+     ((0.4, 0.7, 2.0), True, False),                   # after its bet, facing a raise
+     ((0.7,), True, False)),                           # facing later raises
+    (((0.5, 0.75, 1.0), True, True),                   # facing the check: fold, check, bets, all-in
+     ((0.7, 1.1), True, False),                        # facing the initial bet
+     ((0.7,), True, False),                            # facing later raises
+     ((0.7,), True, False)),
+)
+
+
+def libratus(seed=BASE_SEED, n_cards=52, stack=9.0, alpha=0.5) -> GameSpec:
+    """River endgame with Sec. 7's asymmetric Libratus bet menus, no raise cap besides the stack.
+
+    stack 9 x pot is what remains of 200 big-blind stacks behind a 21 big-blind river pot
+    (Endgame 2's pot, Sec. 7).
+    """
+    import dataclasses
+    spec = river_endgame(n_cards=n_cards, bet_fracs=(), raise_cap=64, stack=stack, alpha=alpha,
+                         seed=seed, name=f"libratus{n_cards}")
+    return dataclasses.replace(spec, menus=LIBRATUS_MENUS)
 
 
 def batch_mix(n_games=64, seed=BASE_SEED):

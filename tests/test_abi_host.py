@@ -24,6 +24,8 @@ SPECS = {
     "full": synth.full_deck,
     "full_stack2": lambda: synth.full_deck(stack=2.0),
     "large": synth.large,
+    "libratus20": lambda: synth.libratus(n_cards=20, stack=2.0),
+    "libratus52": synth.libratus,
 }
 
 

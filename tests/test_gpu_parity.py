@@ -43,7 +43,8 @@ GAMES = {}
 def get(name, egtlib):
     if name not in GAMES:
         spec = {"kuhn": synth.kuhn, "tiny": synth.tiny, "full": synth.full_deck,
-                "large": synth.large, "tiny7": lambda: synth.tiny(seed=7)}[name]()
+                "large": synth.large, "tiny7": lambda: synth.tiny(seed=7),
+                "libratus": lambda: synth.libratus(n_cards=20, stack=2.0)}[name]()
         og = payoff.make_game(spec)
         GAMES[name] = (spec, og, OE.Problem(og), egtlib.Game(spec, device=0))
     return GAMES[name]
@@ -93,7 +94,7 @@ def rand_vec(rng, S, H, kind):
     return rng.random((S, H)) ** 8        # many tiny entries next to large ones
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "tiny7", "full"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "tiny7", "full", "libratus"])
 @pytest.mark.parametrize("kind", ["uniform01", "signed", "skewed", "spread"])
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_grad_f32_matches_oracle(egtlib, name, kind, seed):
@@ -115,7 +116,7 @@ def test_grad_f32_matches_oracle(egtlib, name, kind, seed):
         assert torch.all(tout[:, g.H:] == 0)
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "full"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus"])
 def test_grad_f64_matches_oracle(egtlib, name):
     spec, og, P, g = get(name, egtlib)
     rng = np.random.default_rng(5)
@@ -171,7 +172,7 @@ def sbr_conditioning(P, player, gvec, mu):
     return kappa, mag
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "full"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus"])
 @pytest.mark.parametrize("mu_scale", [1.0, 1e-2, 1e-4])
 def test_smoothed_br_matches_oracle(egtlib, name, mu_scale):
     spec, og, P, g = get(name, egtlib)
@@ -196,7 +197,7 @@ def test_smoothed_br_matches_oracle(egtlib, name, mu_scale):
         assert torch.all(q[:, g.H:] == 0)
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "full"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus"])
 def test_best_response_f64_matches_oracle(egtlib, name):
     spec, og, P, g = get(name, egtlib)
     rng = np.random.default_rng(23)
@@ -209,7 +210,7 @@ def test_best_response_f64_matches_oracle(egtlib, name):
         assert abs(got - ref) <= 64 * EPS64 * np.abs(gv).sum()
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "full"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus"])
 def test_gap_matches_oracle(egtlib, name):
     spec, og, P, g = get(name, egtlib)
     rng = np.random.default_rng(29)
@@ -224,7 +225,7 @@ def rel_linf(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("name", ["tiny", "full"])
+@pytest.mark.parametrize("name", ["tiny", "full", "libratus"])
 @pytest.mark.parametrize("variant", ["theory", "egt"])
 def test_trajectory_plain_egt_100_iterations(egtlib, name, variant):
     spec, og, P, g = get(name, egtlib)
@@ -250,22 +251,29 @@ def replay_on_gpu(g, og, mu0, schedule):
     return host(g, x), host(g, y), rep
 
 
-@pytest.mark.parametrize("name", ["tiny", "full"])
+@pytest.mark.parametrize("name", ["tiny", "full", "libratus"])
 def test_trajectory_egt_as_tau_replay_30(egtlib, name):
-    """EGT/as in tau-replay mode while its smoothing is still well conditioned."""
+    """EGT/as in tau-replay mode while its smoothing is still well conditioned: within
+    1e-5, or 3x the FP32 noise floor of the FP64 oracle where that floor (the largest
+    drift of four FP32-perturbed oracle runs) already reaches a few 1e-6 after 30
+    iterations, as it does on the Libratus-menu game (up to 1.0e-5)."""
     spec, og, P, g = get(name, egtlib)
     mu0 = (0.01 * P.theory_mu(),) * 2
     r = OE.solve(P, variant="egt_as", eps_mbb=0.0, max_iters=30, mu0=mu0, gap_every=1000)
+    runs = [fp32_noise_floor(P, mu0, r.schedule, seed) for seed in range(4)]
+    fx = max(rel_linf(f.x, r.x) for f in runs)
+    fy = max(rel_linf(f.y, r.y) for f in runs)
     xg, yg, rep = replay_on_gpu(g, og, mu0, r.schedule)
-    assert rel_linf(xg, r.x) <= 1e-5 and rel_linf(yg, r.y) <= 1e-5
+    assert rel_linf(xg, r.x) <= max(1e-5, 3 * fx), (rel_linf(xg, r.x), fx)
+    assert rel_linf(yg, r.y) <= max(1e-5, 3 * fy), (rel_linf(yg, r.y), fy)
     assert abs(rep["gap_mbb"] - r.gap_mbb) <= 1e-3 * r.gap_mbb
 
 
-def fp32_noise_floor(P, mu0, schedule):
+def fp32_noise_floor(P, mu0, schedule, seed=0):
     """The oracle's own trajectory when every product is perturbed by FP32-sized noise
     (relative 2^-24, iterates rounded to FP32): how far any FP32 run may drift."""
     orig = P.loss_grad
-    rng = np.random.default_rng(0)
+    rng = np.random.default_rng(seed)
 
     def noisy(player, other):
         gv = orig(player, other.astype(np.float32).astype(np.float64))
@@ -279,7 +287,7 @@ def fp32_noise_floor(P, mu0, schedule):
         P.loss_grad = orig
 
 
-@pytest.mark.parametrize("name", ["tiny", "full"])
+@pytest.mark.parametrize("name", ["tiny", "full", "libratus"])
 def test_trajectory_egt_as_tau_replay_100(egtlib, name):
     """After 100 EGT/as iterations mu is small and the smoothed best responses are ill
     conditioned (max |g_hat| / (mu beta) reaches 1e3-1e4): an FP32-sized perturbation
@@ -300,7 +308,7 @@ def test_trajectory_egt_as_tau_replay_100(egtlib, name):
     assert abs(rep["gap_mbb"] - P.to_mbb(P.eps_sad(xg, yg))) <= 1e-6 * rep["gap_mbb"]
 
 
-@pytest.mark.parametrize("name", ["tiny", "full"])
+@pytest.mark.parametrize("name", ["tiny", "full", "libratus"])
 def test_egt_as_free_running_decisions(egtlib, name):
     """Free-running EGT/as: the tau / player decisions follow the oracle's (EGV signs agree)."""
     spec, og, P, g = get(name, egtlib)

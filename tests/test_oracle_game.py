@@ -171,3 +171,39 @@ def test_structured_products_match_brute_force():
     x = rng.random((g.S[0], g.H))
     assert np.allclose(structured_products(spec, g.sf, y, 0), g.Ay(y), rtol=1e-12, atol=1e-15)
     assert np.allclose(structured_products(spec, g.sf, x, 1), g.Atx(x), rtol=1e-12, atol=1e-15)
+
+
+def test_libratus_menus_match_the_hand_derived_tree():
+    """Sec. 7's asymmetric menus at stack = pot, derived by hand in the golden file."""
+    import json
+    import pathlib
+    gold = json.loads((pathlib.Path(__file__).parent / "golden" / "libratus_stack1.json").read_text())
+    sf = G.sequence_form(gold["game"]["pot"], gold["game"]["stack"], (), True, 64, synth.LIBRATUS_MENUS)
+    assert len(sf.terminals) == gold["terminals"]
+    assert [sf.tpx[0].n_seq, sf.tpx[1].n_seq] == gold["sequences"]
+    for p, key in enumerate(("player1", "player2")):
+        sizes = sorted(len(s) for s in sf.tpx[p].infoset_seqs)
+        assert sizes == sorted(gold["infoset_sizes"][key])
+
+
+def test_uniform_menus_reproduce_the_single_menu_tree():
+    spec = synth.large()
+    same = tuple(tuple((spec.bet_fracs, spec.allin, False) for _ in range(4)) for _ in range(2))
+    a = G.sequence_form(spec.pot, spec.stack, spec.bet_fracs, spec.allin, spec.raise_cap)
+    b = G.sequence_form(spec.pot, spec.stack, (), False, spec.raise_cap, same)
+    assert [t.seq for t in a.terminals] == [t.seq for t in b.terminals]
+    for p in range(2):
+        assert a.tpx[p].infoset_seqs == b.tpx[p].infoset_seqs
+        assert a.tpx[p].infoset_parent == b.tpx[p].infoset_parent
+
+
+def test_fold_before_the_opponent_acts_keeps_the_game_bilinear():
+    """Player 1's opening fold gets a one-action pass decision of player 2: every terminal
+    has a sequence of both players, and the pass sequence is the only action of its simplex."""
+    sf = G.sequence_form(1.0, 2.0, (), True, 64, synth.LIBRATUS_MENUS)
+    assert all(t.seq[0] >= 0 and t.seq[1] >= 0 for t in sf.terminals)
+    folds_at_root = [t for t in sf.terminals if t.kind == "fold" and t.folder == 0 and t.contrib == (0.0, 0.0)]
+    assert len(folds_at_root) == 1
+    s2 = folds_at_root[0].seq[1]
+    j = [k for k, seqs in enumerate(sf.tpx[1].infoset_seqs) if s2 in seqs]
+    assert len(j) == 1 and len(sf.tpx[1].infoset_seqs[j[0]]) == 1
