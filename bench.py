@@ -472,7 +472,8 @@ def run_variants(args, local):
     names = {egt.THEORY: "EGT, Alg. 1 (theory mu, tau_t = 2/(t+3))",
              egt.PRACTICAL: "EGT (tuned mu, alpha 0.01, balancing)",
              egt.EGT_AS: "EGT/as (Alg. 3 + 4, alpha 0.01)"}
-    games = {"tiny (20 cards)": synth.tiny(), "full deck (52 cards)": synth.full_deck()}
+    games = {"tiny (20 cards)": synth.tiny(), "full deck (52 cards)": synth.full_deck(),
+             "Libratus menus (52 cards, stack 9 pots)": synth.libratus()}
     marks = [10 ** k for k in range(1, 7)]
     out = []
     for gname, spec in games.items():
