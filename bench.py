@@ -613,7 +613,8 @@ def main():
                    "engine": args.engine, "iterations_per_step": r["ips"],
                    "reinit_every": args.reinit_every,
                    "one_iteration_per_launch": {"value": r["one_per_launch"], "unit": UNIT},
-                   "precision": "products and smoothed BR in f32 (compensated sums); gap, EGV sums, mu in f64",
+                   "precision": "exact fixed-point product sums rounded to f32; smoothed BR in f32; gap, EGV sums, "
+                                "mu / tau in f64",
                    "l2": "flushed (256 MB write) before every timed step (one launch of iterations_per_step "
                          "iterations; the ~2 MB state stays L2-resident inside the launch, as in a solve)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -162,11 +162,13 @@ EGT_API egt_status egt_terminal_query(const egt_game* game, int32_t* seq1, int32
  * player 0: out[S0][ld] = A in, in = y [S1][ld];
  * player 1: out[S1][ld] = A^T in, in = x [S0][ld].  Device pointers, in != out.
  * Computed per terminal with card-removal inclusion-exclusion (folds) and
- * strength-sorted prefix sums with per-card corrections (showdowns), FP32
- * with compensated (float-float) sums. */
+ * strength-sorted prefix sums with per-card corrections (showdowns).  The sums
+ * are exact (w = r x in formed exactly, two-limb fixed point 2^-87 below the
+ * terminal's largest |w|); the output is the correctly rounded FP32 value of
+ * r_me / Z x the sum of the sequence's terminal contributions. */
 EGT_API egt_status egt_grad(egt_game* game, int32_t player, const float* in, float* out, void* stream);
 
-/* Same product in FP64 throughout (used by the stopping gap). */
+/* Same product with FP64 input and output (the stopping gap's precision). */
 EGT_API egt_status egt_grad_f64(egt_game* game, int32_t player, const double* in, double* out,
                         void* stream);
 
