@@ -197,16 +197,16 @@ __device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, Grp g
     term_item<float>(g, tb.grad, player, item, in, c32, c64, sm);
 }
 
-// The residual's two FP64 best responses as items [first, first + 2 NB) of a phase
-// (br item i < NB: player 0, else player 1), partials to partBR0 / partBR1.
-__device__ __forceinline__ void run_br_items(const DevGame& g, const Tabs& tb, int item, int NB,
-                                             const EngineBufs& b, double* partBR0, double* partBR1,
-                                             unsigned char* sm) {
-  if (item < NB)
+// Item `item` of player p's FP64 best response of the residual (player 0: min over x of
+// <x, A y>, player 1: max over y of <y, A^T x>), its partial to partBR0 / partBR1.
+__device__ __forceinline__ void run_br_item(const DevGame& g, const Tabs& tb, int p, int item,
+                                            const EngineBufs& b, double* partBR0, double* partBR1,
+                                            unsigned char* sm) {
+  if (p == 0)
     br64_item(g, tb.tpx[0], item, b.g64[0], true, g.rz64[0], 1.0, partBR0 + item,
               reinterpret_cast<double*>(sm));
   else
-    br64_item(g, tb.tpx[1], item - NB, b.g64[1], true, g.rz64[1], -1.0, partBR1 + item - NB,
+    br64_item(g, tb.tpx[1], item, b.g64[1], true, g.rz64[1], -1.0, partBR1 + item,
               reinterpret_cast<double*>(sm));
 }
 
@@ -282,7 +282,6 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
   const bool clock_cta = gr.rank == 0;
   const bool writer = clock_cta && lead;
   const int NB = g.ld / kSbrHands;
-  const int T = g.terms[0].n;
   double* partA = b.partials;
   double* partB = b.partials + NB;
   double* partBR0 = b.partials + 2 * NB;
@@ -387,11 +386,34 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
     if (!phase_end(bar, bk, clk, 2, clock_cta)) return;
     run_grad(g, tb, gr, m, v_ot_n, g_me_n, g64_me, sm);         // my loss gradient at other_+
     if (!phase_end(bar, bk, clk, 3, clock_cta)) return;
-    // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part
-    run_sbr(g, tb, gr, m, g_me_n, mu_tilde, v_me, tau_f, v_me_n, partA, sm);
+    // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part.
+    // When the residual is due, my FP64 best response (on the FP64 product of the last
+    // phase) runs beside it as items [NB, 2 NB).
+    {
+      const int n_items = gap_due ? 2 * NB : NB;
+      const TpxTab tp = pick(tb, m);
+      for (int item = gr.rank; item < n_items; item += gr.size) {
+        if (item < NB) {
+          SbrItemArgs a;
+          a.g = g_me_n;
+          a.contrib = true;
+          a.grz = m ? g.rz[1] : g.rz[0];
+          a.sign = m == 0 ? 1.f : -1.f;
+          a.mu = mu_tilde;
+          a.old = v_me;
+          a.tau = tau_f;
+          a.out = v_me_n;
+          a.value_partial = partA + item;
+          sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
+        } else {
+          run_br_item(g, tb, m, item - NB, b, partBR0, partBR1, sm);
+        }
+      }
+    }
     if (!phase_end(bar, bk, clk, 4, clock_cta)) return;
     {
       // the other's loss gradient at v_+, and the next v_hat when the same player steps
+      const int T = ot ? g.terms[1].n : g.terms[0].n;
       const int n_items = T + (sp == 1 ? NB : 0);
       for (int item = gr.rank; item < n_items; item += gr.size) {
         if (item < T) {
@@ -414,10 +436,10 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
     if (!phase_end(bar, bk, clk, 5, clock_cta)) return;
     double red[4] = {0.0, 0.0, 0.0, 0.0};
     if (tail) {
-      // the other's EGV part and / or the next v_hat (items [0, NB)), the residual's
-      // best responses when due (the following 2 NB items)
+      // the other's EGV part and / or the next v_hat (items [0, NB)), the other's FP64
+      // best response when the residual is due (the following NB items)
       const int n_sbr = check || sp == 2 ? NB : 0;
-      const int n_items = n_sbr + (gap_due ? 2 * NB : 0);
+      const int n_items = n_sbr + (gap_due ? NB : 0);
       const TpxTab tp = pick(tb, ot);
       for (int item = gr.rank; item < n_items; item += gr.size) {
         if (item < n_sbr) {
@@ -433,7 +455,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
           a.value_partial = check ? partB + item : nullptr;
           sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
         } else {
-          run_br_items(g, tb, item - n_sbr, NB, b, partBR0, partBR1, sm);
+          run_br_item(g, tb, ot, item - n_sbr, b, partBR0, partBR1, sm);
         }
       }
       if (!phase_end(bar, bk, clk, 6, clock_cta)) return;
@@ -614,9 +636,9 @@ int engine_max_grid(size_t smem, bool batch) {
 
 int engine_items(const DevGame& g) {
   const int NB = g.ld / kSbrHands;
-  // widest phase: the last product with the next v_hat, or the EGV SBR with the
-  // residual's two best responses
-  return std::max(3 * NB, g.terms[0].n + NB);
+  // widest phase: the last product with the next v_hat, or an SBR phase with one of
+  // the residual's best responses
+  return std::max(2 * NB, std::max(g.terms[0].n, g.terms[1].n) + NB);
 }
 
 }  // namespace egt

@@ -12,11 +12,14 @@
 // Top-down: q_i = q_{p_j} q_bar_i.
 //
 // Sec. 6: the per-hand treeplexes form a Cartesian product at the root, so
-// hands are independent.  One item = 32 hands (one per lane, sequence rows
-// load as 128-byte lines); the whole [S][32] tile of g (and of the previous
-// iterate that the output is mixed with) is fetched into shared memory in one
-// coalesced pass before the recursion, which then runs on shared memory: the
-// warps split the simplexes of a level, levels are separated by __syncthreads.
+// hands are independent.  One item = 16 hands; a warp holds each hand twice
+// (lane = hand + 16 x sub-lane) and the two sub-lanes take a simplex's branches
+// alternately, halving the dependent chain of every simplex; the minimum and
+// the sums over branches combine the sub-lanes with one shuffle.  The whole
+// [S][16] tile of g (and of the previous iterate the output is mixed with) is
+// fetched into shared memory before the recursion (two 64-byte row pieces per
+// warp load), which then runs on shared memory: the warps split the simplexes
+// of a level, levels are separated by __syncthreads.
 #pragma once
 #include <math.h>
 
@@ -116,31 +119,39 @@ __device__ __forceinline__ double reduce_partials(const double* p, int n, int la
   return v;
 }
 
-// One item (32 hands starting at blk * 32) of player `player`'s smoothed best response.
+// Lane layout of an item: hand hl = lane % 16, branch sub-lane bl = lane / 16.
+constexpr int kSubLanes = 32 / kSbrHands;
+static_assert(kSbrHands * kSubLanes == 32, "an item's hands times sub-lanes fill a warp");
+
+// One item (kSbrHands hands starting at blk * kSbrHands) of player `player`'s smoothed
+// best response.
 __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, const SbrItemArgs& a,
                                 float* sm) {
+  constexpr int kH = kSbrHands;
   const int S = tp.S, J = tp.J, ld = g.ld;
   constexpr int kWarps = kItemThreads / 32;
-  float* G = sm;                                   // [S][32] sign*g -> g_hat -> q_bar -> q
-  float* O = G + (size_t)S * kSbrHands;            // [S][32] previous iterate
-  float* V = O + (size_t)S * kSbrHands;            // [J][32] simplex values
-  float* tj = V + (size_t)J * kSbrHands;           // [J] t_j = mu beta_j
+  float* G = sm;                                   // [S][kH] sign*g -> g_hat -> q_bar -> q
+  float* O = G + (size_t)S * kH;                   // [S][kH] previous iterate
+  float* V = O + (size_t)S * kH;                   // [J][kH] simplex values
+  float* tj = V + (size_t)J * kH;                  // [J] t_j = mu beta_j
   float* itj = tj + J;                             // [J] 1 / t_j
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int h0 = blk * kSbrHands, h = h0 + lane;
+  const int hl = lane % kH, bl = lane / kH;
+  const int h0 = blk * kH, h = h0 + hl;
   const bool live = h < g.H;
 
-  // the [S][32] tile of sign * g (and of the previous iterate): each warp takes rows
-  // warp, warp + 16, ...; the loads of kU rows are issued before any is used
+  // the [S][kH] tile of sign * g (and of the previous iterate): each warp takes rows
+  // 2 warp + bl, 2 warp + bl + 32, ...; the loads of kU rows are issued before any is used
   {
     constexpr int kU = 4;
+    constexpr int kRowStep = kWarps * kSubLanes;
     const float rz = (a.g != nullptr && a.contrib && live) ? a.grz[h] : 0.f;
-    for (int s0 = warp; s0 < S; s0 += kWarps * kU) {
+    for (int s0 = kSubLanes * warp + bl; s0 < S; s0 += kRowStep * kU) {
       float c0[kU], c1[kU], o[kU];
       int e0[kU], e1[kU];
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
-        const int s = s0 + u * kWarps;
+        const int s = s0 + u * kRowStep;
         c0[u] = c1[u] = o[u] = 0.f;
         e0[u] = e1[u] = 0;
         if (s < S) {
@@ -159,7 +170,7 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
       }
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
-        const int s = s0 + u * kWarps;
+        const int s = s0 + u * kRowStep;
         if (s < S) {
           float v = c0[u];
           if (a.contrib) {
@@ -170,8 +181,8 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
             for (int e = e0[u] + 2; e < e1[u]; ++e) acc += __ldcg(a.g + (size_t)e * ld + h);
             v = rz * acc;
           }
-          G[s * kSbrHands + lane] = a.sign * v;
-          if (a.old != nullptr) O[s * kSbrHands + lane] = o[u];
+          G[s * kH + hl] = a.sign * v;
+          if (a.old != nullptr) O[s * kH + hl] = o[u];
         }
       }
     }
@@ -187,37 +198,40 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
     for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
       const int s0 = tp.inf_first[j], n = tp.inf_n[j];
       float m = INFINITY;
-      for (int i = 0; i < n; ++i) {
+      for (int i = bl; i < n; i += kSubLanes) {
         const int s = s0 + i;
-        float gh = G[s * kSbrHands + lane];
-        for (int c = tp.child_ptr[s]; c < tp.child_ptr[s + 1]; ++c)
-          gh += V[tp.child_idx[c] * kSbrHands + lane];
-        G[s * kSbrHands + lane] = gh;
+        float gh = G[s * kH + hl];
+        for (int c = tp.child_ptr[s]; c < tp.child_ptr[s + 1]; ++c) gh += V[tp.child_idx[c] * kH + hl];
+        G[s * kH + hl] = gh;
         m = fminf(m, gh);
       }
+      m = fminf(m, __shfl_xor_sync(0xffffffffu, m, kH));
       // e_i = exp(-(g_hat_i - m)/t) keeps tiny q_bar accurate; X = sum_i (e_i - 1) via expm1
       // keeps the value accurate: t log q_bar_i* + t log n = -t log1p(X / n)
       const float it = itj[j];
       float sum = 0.f, X = 0.f;
-      for (int i = 0; i < n; ++i) {
-        float* u = G + (s0 + i) * kSbrHands + lane;
+      for (int i = bl; i < n; i += kSubLanes) {
+        float* u = G + (s0 + i) * kH + hl;
         const float d = -(*u - m) * it;
         const float e = expf(d);
         X += expm1f(d);
         *u = e;
         sum += e;
       }
+      // both sub-lanes get partial(0) + partial(1) (addition commutes: the same bits)
+      sum += __shfl_xor_sync(0xffffffffu, sum, kH);
+      X += __shfl_xor_sync(0xffffffffu, X, kH);
       const float inv = 1.f / sum;
-      for (int i = 0; i < n; ++i) G[(s0 + i) * kSbrHands + lane] *= inv;
-      V[j * kSbrHands + lane] = m - tj[j] * log1pf(X / (float)n);
+      for (int i = bl; i < n; i += kSubLanes) G[(s0 + i) * kH + hl] *= inv;
+      if (bl == 0) V[j * kH + hl] = m - tj[j] * log1pf(X / (float)n);
     }
     __syncthreads();
   }
 
   if (a.value_partial != nullptr && warp == 0) {
     double v = 0.0;
-    if (live)
-      for (int j = tp.level_ptr[0]; j < tp.level_ptr[1]; ++j) v += (double)V[j * kSbrHands + lane];
+    if (live && bl == 0)
+      for (int j = tp.level_ptr[0]; j < tp.level_ptr[1]; ++j) v += (double)V[j * kH + hl];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
     if (lane == 0) *a.value_partial = v;
@@ -228,14 +242,14 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
     for (int l = 0; l < tp.L; ++l) {
       for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
         const int p = tp.inf_parent[j];
-        const float qp = p < 0 ? 1.f : G[p * kSbrHands + lane];
+        const float qp = p < 0 ? 1.f : G[p * kH + hl];
         const int s0 = tp.inf_first[j], n = tp.inf_n[j];
-        for (int i = 0; i < n; ++i) {
+        for (int i = bl; i < n; i += kSubLanes) {
           const int s = s0 + i;
-          const float q = qp * G[s * kSbrHands + lane];
-          G[s * kSbrHands + lane] = q;
+          const float q = qp * G[s * kH + hl];
+          G[s * kH + hl] = q;
           float o = q;
-          if (a.old != nullptr) o = omt * O[s * kSbrHands + lane] + tau * q;
+          if (a.old != nullptr) o = omt * O[s * kH + hl] + tau * q;
           a.out[(size_t)s * ld + h] = live ? o : 0.f;
         }
       }
@@ -247,27 +261,31 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
 
 // One item of the FP64 best-response value: sign * min over the treeplex of
 // <q, sign * g> summed over the item's live hands, written to *value_partial.
-// gv as in SbrItemArgs: dense [S][ld] or (contrib) terminal contributions.
+// gv as in SbrItemArgs: dense [S][ld] or (contrib) terminal contributions.  Same
+// lane layout as sbr_item.
 __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, const double* gv,
                                  bool contrib, const double* grz, double sign,
                                  double* value_partial, double* sm) {
+  constexpr int kH = kSbrHands;
   const int S = tp.S, ld = g.ld;
   constexpr int kWarps = kItemThreads / 32;
-  double* G = sm;                                  // [S][32]
-  double* V = G + (size_t)S * kSbrHands;           // [J][32]
+  double* G = sm;                                  // [S][kH]
+  double* V = G + (size_t)S * kH;                  // [J][kH]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int h0 = blk * kSbrHands, h = h0 + lane;
+  const int hl = lane % kH, bl = lane / kH;
+  const int h0 = blk * kH, h = h0 + hl;
   const bool live = h < g.H;
   {
     constexpr int kU = 4;
+    constexpr int kRowStep = kWarps * kSubLanes;
     const bool neg = sign < 0;
     const double rz = (contrib && live) ? grz[h] : 0.0;
-    for (int s0 = warp; s0 < S; s0 += kWarps * kU) {
+    for (int s0 = kSubLanes * warp + bl; s0 < S; s0 += kRowStep * kU) {
       double c0[kU], c1[kU];
       int e0[kU], e1[kU];
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
-        const int s = s0 + u * kWarps;
+        const int s = s0 + u * kRowStep;
         c0[u] = c1[u] = 0.0;
         e0[u] = e1[u] = 0;
         if (s < S && live) {
@@ -283,7 +301,7 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
       }
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
-        const int s = s0 + u * kWarps;
+        const int s = s0 + u * kRowStep;
         if (s < S) {
           double v = c0[u];
           if (contrib) {
@@ -295,7 +313,7 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
           } else if (neg) {
             v = -v;
           }
-          G[s * kSbrHands + lane] = v;
+          G[s * kH + hl] = v;
         }
       }
     }
@@ -305,21 +323,21 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
     for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
       const int s0 = tp.inf_first[j], n = tp.inf_n[j];
       double m = INFINITY;
-      for (int i = 0; i < n; ++i) {
+      for (int i = bl; i < n; i += kSubLanes) {
         const int s = s0 + i;
-        double gh = G[s * kSbrHands + lane];
-        for (int c = tp.child_ptr[s]; c < tp.child_ptr[s + 1]; ++c)
-          gh += V[tp.child_idx[c] * kSbrHands + lane];
+        double gh = G[s * kH + hl];
+        for (int c = tp.child_ptr[s]; c < tp.child_ptr[s + 1]; ++c) gh += V[tp.child_idx[c] * kH + hl];
         m = fmin(m, gh);
       }
-      V[j * kSbrHands + lane] = m;
+      m = fmin(m, __shfl_xor_sync(0xffffffffu, m, kH));
+      if (bl == 0) V[j * kH + hl] = m;
     }
     __syncthreads();
   }
   if (warp == 0) {
     double v = 0.0;
-    if (live)
-      for (int j = tp.level_ptr[0]; j < tp.level_ptr[1]; ++j) v += V[j * kSbrHands + lane];
+    if (live && bl == 0)
+      for (int j = tp.level_ptr[0]; j < tp.level_ptr[1]; ++j) v += V[j * kH + hl];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
     if (lane == 0) *value_partial = sign * v;
