@@ -1528,10 +1528,13 @@ egt_status egt_batch_step(egt_batch* B, int32_t n_iters, int32_t group, int32_t*
   EGT_TRY(batch_reserve(B, n));
   size_t smem = 0;
   std::vector<double> w(n);
-  std::vector<int> cap(n);
+  std::vector<int> cap(n), pair(n);
+  const int limit = engine_smem_limit(true);
   for (int i = 0; i < n; ++i) {
     const egt_game* G = B->members[act[i]].G;
-    smem = std::max(smem, engine_smem_bytes(G->dg));
+    // two SBR / best-response items per CTA at a time where shared memory allows
+    pair[i] = limit > 0 && engine_smem_bytes(G->dg, true) <= (size_t)limit;
+    smem = std::max(smem, engine_smem_bytes(G->dg, pair[i] != 0));
     w[i] = iteration_work(G);
     cap[i] = engine_items(G->dg);
   }
@@ -1558,6 +1561,7 @@ egt_status egt_batch_step(egt_batch* B, int32_t n_iters, int32_t group, int32_t*
     j.g = m.G->dg;
     j.b = engine_bufs(m.G, nullptr, 0);
     j.ctl = B->ctl_dev + i;
+    j.pair = pair[order[i]];
   }
   std::copy(plan.begin(), plan.end(), B->plan_host);
   const unsigned extra = (unsigned)std::max(0, env_int("EGT_TEST_BARRIER_EXTRA", 0));

@@ -168,12 +168,39 @@ __device__ __forceinline__ TpxTab pick(const Tabs& tb, int p) {
 
 // One SBR phase: all 32-hand items of `player`, spread over the CTAs; gv holds the
 // player's terminal contributions (or is NULL).
-__device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, Grp gr, int player, const float* gv,
-                                        double mu, const float* old, float tau, float* out,
+// Shared memory of one SBR / best-response item of either player (a warp half's share
+// when items run in pairs).
+__device__ __forceinline__ size_t pair_half_bytes(const DevGame& g) {
+  size_t m = 0;
+  for (int p = 0; p < 2; ++p) m = max(m, max(sbr_item_smem(g, p), br_item_smem(g, p)));
+  return gradimpl::align16(m);
+}
+
+// The items of an SBR / best-response phase this CTA takes: one at a time on the whole
+// CTA, or (pairs) two at a time, one per warp half with its own named barrier, when the
+// job allows it and the group has at least two items per CTA.  Calls f(item, wg, smem).
+template <typename F>
+__device__ __forceinline__ void for_items(const DevGame& g, Grp gr, int n_items, bool pair_ok, unsigned char* sm,
+                                          F f) {
+  const bool pair = pair_ok && 2 * gr.size <= n_items;
+  if (!pair) {
+    for (int item = gr.rank; item < n_items; item += gr.size) f(item, WarpGroup{0, kItemThreads / 32, 0}, sm);
+    return;
+  }
+  constexpr int kHalf = kItemThreads / 64;
+  const int half = (int)(threadIdx.x >> 5) >= kHalf ? 1 : 0;
+  const WarpGroup wg{half * kHalf, kHalf, 1 + half};
+  unsigned char* hs = sm + half * pair_half_bytes(g);
+  for (int base = 2 * gr.rank; base < n_items; base += 2 * gr.size)
+    if (base + half < n_items) f(base + half, wg, hs);
+}
+
+__device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, Grp gr, bool pair_ok, int player,
+                                        const float* gv, double mu, const float* old, float tau, float* out,
                                         double* partials, unsigned char* sm) {
   const int NB = g.ld / kSbrHands;
   const TpxTab tp = pick(tb, player);
-  for (int item = gr.rank; item < NB; item += gr.size) {
+  for_items(g, gr, NB, pair_ok, sm, [&](int item, const WarpGroup& wg, unsigned char* ism) {
     SbrItemArgs a;
     a.g = gv;
     a.contrib = true;
@@ -184,8 +211,8 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, Grp gr
     a.tau = tau;
     a.out = out;
     a.value_partial = partials ? partials + item : nullptr;
-    sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
-  }
+    sbr_item(g, tp, item, a, reinterpret_cast<float*>(ism), wg);
+  });
 }
 
 // One product phase: every terminal of `player`'s grouping; c64 (FP64 contributions
@@ -201,13 +228,13 @@ __device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, Grp g
 // <x, A y>, player 1: max over y of <y, A^T x>), its partial to partBR0 / partBR1.
 __device__ __forceinline__ void run_br_item(const DevGame& g, const Tabs& tb, int p, int item,
                                             const EngineBufs& b, double* partBR0, double* partBR1,
-                                            unsigned char* sm) {
+                                            unsigned char* sm, const WarpGroup& wg) {
   if (p == 0)
     br64_item(g, tb.tpx[0], item, b.g64[0], true, g.rz64[0], 1.0, partBR0 + item,
-              reinterpret_cast<double*>(sm));
+              reinterpret_cast<double*>(sm), wg);
   else
     br64_item(g, tb.tpx[1], item, b.g64[1], true, g.rz64[1], -1.0, partBR1 + item,
-              reinterpret_cast<double*>(sm));
+              reinterpret_cast<double*>(sm), wg);
 }
 
 // Fixed-order sums of the per-item partial arrays [first, last) (each of n
@@ -256,8 +283,8 @@ struct Sched {
 // One job (game) run by the group `gr`: its tables staged in smem_all, then up to
 // ctl->n_iters iterations.  Returns when the job stops or fails (status recorded).
 __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b, EngineCtl* ctl, Grp gr,
-                                        unsigned long long expected, unsigned long long limit_ns,
-                                        unsigned char* smem_all) {
+                                           bool pair_ok, unsigned long long expected,
+                                           unsigned long long limit_ns, unsigned char* smem_all) {
   Tabs tb;
   tb.grad = stage_grad_tab(g, smem_all);
   tb.tpx[0] = stage_tpx_tab(g, 0, smem_all + grad_tab_bytes(g));
@@ -375,14 +402,14 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
 
     // v_hat = (1 - tau) v + tau v_mu(other)
     if (!have_hat) {
-      run_sbr(g, tb, gr, m, g_me, mu_me, v_me, tau_f, t_me, nullptr, sm);
+      run_sbr(g, tb, gr, pair_ok, m, g_me, mu_me, v_me, tau_f, t_me, nullptr, sm);
       if (!phase_end(bar, bk, clk, 0, clock_cta)) return;
     }
     phase_cut(clk, 8, clock_cta);
     run_grad(g, tb, gr, ot, t_me, t_ot, nullptr, sm);           // the other's loss gradient at v_hat
     if (!phase_end(bar, bk, clk, 1, clock_cta)) return;
     // other_+ = (1 - tau) other + tau other_mu(v_hat)
-    run_sbr(g, tb, gr, ot, t_ot, mu_ot, v_ot, tau_f, v_ot_n, nullptr, sm);
+    run_sbr(g, tb, gr, pair_ok, ot, t_ot, mu_ot, v_ot, tau_f, v_ot_n, nullptr, sm);
     if (!phase_end(bar, bk, clk, 2, clock_cta)) return;
     run_grad(g, tb, gr, m, v_ot_n, g_me_n, g64_me, sm);         // my loss gradient at other_+
     if (!phase_end(bar, bk, clk, 3, clock_cta)) return;
@@ -392,7 +419,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
     {
       const int n_items = gap_due ? 2 * NB : NB;
       const TpxTab tp = pick(tb, m);
-      for (int item = gr.rank; item < n_items; item += gr.size) {
+      for_items(g, gr, n_items, pair_ok, sm, [&](int item, const WarpGroup& wg, unsigned char* ism) {
         if (item < NB) {
           SbrItemArgs a;
           a.g = g_me_n;
@@ -404,11 +431,11 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
           a.tau = tau_f;
           a.out = v_me_n;
           a.value_partial = partA + item;
-          sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
+          sbr_item(g, tp, item, a, reinterpret_cast<float*>(ism), wg);
         } else {
-          run_br_item(g, tb, m, item - NB, b, partBR0, partBR1, sm);
+          run_br_item(g, tb, m, item - NB, b, partBR0, partBR1, ism, wg);
         }
-      }
+      });
     }
     if (!phase_end(bar, bk, clk, 4, clock_cta)) return;
     {
@@ -441,7 +468,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
       const int n_sbr = check || sp == 2 ? NB : 0;
       const int n_items = n_sbr + (gap_due ? NB : 0);
       const TpxTab tp = pick(tb, ot);
-      for (int item = gr.rank; item < n_items; item += gr.size) {
+      for_items(g, gr, n_items, pair_ok, sm, [&](int item, const WarpGroup& wg, unsigned char* ism) {
         if (item < n_sbr) {
           SbrItemArgs a;
           a.g = g_ot_n;
@@ -453,11 +480,11 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
           a.tau = sp == 2 ? tau2_f : 0.f;
           a.out = sp == 2 ? t_ot : nullptr;
           a.value_partial = check ? partB + item : nullptr;
-          sbr_item(g, tp, item, a, reinterpret_cast<float*>(sm));
+          sbr_item(g, tp, item, a, reinterpret_cast<float*>(ism), wg);
         } else {
-          run_br_item(g, tb, ot, item - n_sbr, b, partBR0, partBR1, sm);
+          run_br_item(g, tb, ot, item - n_sbr, b, partBR0, partBR1, ism, wg);
         }
-      }
+      });
       if (!phase_end(bar, bk, clk, 6, clock_cta)) return;
       // the EGV parts (partA, partB) and the residual's values (partBR0, partBR1) in one pass
       reduce_arrays(b.partials, NB, check ? 0 : 2, gap_due ? 4 : 2, red);
@@ -552,7 +579,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
 __global__ void __launch_bounds__(kItemThreads, 1)
     engine_kernel_one(EngineJob job, unsigned int extra, unsigned long long limit_ns) {
   extern __shared__ __align__(16) unsigned char smem_all[];
-  engine_job(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x},
+  engine_job(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x}, job.pair != 0,
              (unsigned long long)gridDim.x + extra, limit_ns, smem_all);
 }
 
@@ -578,19 +605,21 @@ __global__ void __launch_bounds__(kItemThreads, 1)
       for (int i = threadIdx.x; i < (int)(sizeof(EngineJob) / 8); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    engine_job(job_s.g, job_s.b, job_s.ctl, gr, (unsigned long long)pg.size + extra, limit_ns, smem_all);
+    engine_job(job_s.g, job_s.b, job_s.ctl, gr, job_s.pair != 0, (unsigned long long)pg.size + extra, limit_ns,
+               smem_all);
   }
 }
 
 }  // namespace
 
-size_t engine_smem_bytes(const DevGame& g) {
-  size_t m = grad_item_smem(g);
+size_t engine_smem_bytes(const DevGame& g, bool pair) {
+  size_t m = 0;
   for (int p = 0; p < 2; ++p) {
     m = std::max(m, sbr_item_smem(g, p));
     m = std::max(m, br_item_smem(g, p));
   }
-  return tabs_bytes(g) + m;
+  m = pair ? 2 * gradimpl::align16(m) : m;
+  return tabs_bytes(g) + std::max(m, grad_item_smem(g));
 }
 
 cudaError_t engine_launch_one(const EngineJob& job, int grid, size_t smem, unsigned int extra,
@@ -613,11 +642,15 @@ cudaError_t engine_launch(const EngineJob* jobs_dev, const EngineGroup* plan_dev
                                      smem, st);
 }
 
-int engine_max_grid(size_t smem, bool batch) {
+int engine_smem_limit(bool batch) {
   static int limit_one = 0, limit_batch = 0;
   if (limit_one == 0) limit_one = opt_in_dynamic_smem((const void*)engine_kernel_one);
   if (limit_batch == 0) limit_batch = opt_in_dynamic_smem((const void*)engine_kernel);
-  const int limit = batch ? limit_batch : limit_one;
+  return batch ? limit_batch : limit_one;
+}
+
+int engine_max_grid(size_t smem, bool batch) {
+  const int limit = engine_smem_limit(batch);
   if (limit < 0) return -1;
   if (smem > (size_t)limit) return 0;
   int dev = 0, sms = 0, per_sm = 0, coop = 0;

@@ -55,14 +55,21 @@ struct EngineJob {
   DevGame g;
   EngineBufs b;
   EngineCtl* ctl;
+  int pair;       // SBR / best-response items may run two at a time on the CTA's warp halves
+  int pad;
 };
 static_assert(sizeof(EngineJob) % 8 == 0, "EngineJob is copied in 8-byte words");
 
-// Dynamic shared memory the driver needs for game g (tables + the largest item).
-size_t engine_smem_bytes(const DevGame& g);
+// Dynamic shared memory the driver needs for game g (tables + the largest item, or two
+// SBR / best-response items side by side when pair is set).
+size_t engine_smem_bytes(const DevGame& g, bool pair = false);
 
 // Items of the widest phase of game g (more CTAs per game than this idle).
 int engine_items(const DevGame& g);
+
+// Largest dynamic shared memory per CTA of the driver's kernels on the current device
+// (-1: CUDA error).
+int engine_smem_limit(bool batch);
 
 // Largest co-resident grid of the driver (batch: the multi-job kernel, else the
 // one-job kernel) with `smem` bytes of dynamic shared memory per CTA on the

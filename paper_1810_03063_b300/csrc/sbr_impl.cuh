@@ -41,12 +41,12 @@ struct SbrItemArgs {
 };
 
 // (the shared memory below excludes the staged tables)
-inline size_t sbr_item_smem(const DevGame& g, int player) {
+__host__ __device__ inline size_t sbr_item_smem(const DevGame& g, int player) {
   const DevTpx& tp = g.tpx[player];
   return ((size_t)2 * tp.S * kSbrHands + (size_t)tp.J * kSbrHands + 2 * (size_t)tp.J) * sizeof(float);
 }
 
-inline size_t br_item_smem(const DevGame& g, int player) {
+__host__ __device__ inline size_t br_item_smem(const DevGame& g, int player) {
   const DevTpx& tp = g.tpx[player];
   return ((size_t)tp.S * kSbrHands + (size_t)tp.J * kSbrHands) * sizeof(double);
 }
@@ -123,28 +123,40 @@ __device__ __forceinline__ double reduce_partials(const double* p, int n, int la
 constexpr int kSubLanes = 32 / kSbrHands;
 static_assert(kSbrHands * kSubLanes == 32, "an item's hands times sub-lanes fill a warp");
 
+// The warps that run an item: all of the CTA (bar = 0: __syncthreads), or half of it
+// with its own named barrier (bar = 1 or 2) so that two items run side by side.
+struct WarpGroup {
+  int first_warp, n_warps, bar;
+};
+constexpr WarpGroup kWholeCta = {0, kItemThreads / 32, 0};
+
+__device__ __forceinline__ void group_sync(const WarpGroup& wg) {
+  if (wg.bar == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(wg.bar), "r"(wg.n_warps * 32) : "memory");
+}
+
 // One item (kSbrHands hands starting at blk * kSbrHands) of player `player`'s smoothed
 // best response.
 __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, const SbrItemArgs& a,
-                                float* sm) {
+                                float* sm, WarpGroup wg = kWholeCta) {
   constexpr int kH = kSbrHands;
   const int S = tp.S, J = tp.J, ld = g.ld;
-  constexpr int kWarps = kItemThreads / 32;
+  const int kWarps = wg.n_warps;
   float* G = sm;                                   // [S][kH] sign*g -> g_hat -> q_bar -> q
   float* O = G + (size_t)S * kH;                   // [S][kH] previous iterate
   float* V = O + (size_t)S * kH;                   // [J][kH] simplex values
   float* tj = V + (size_t)J * kH;                  // [J] t_j = mu beta_j
   float* itj = tj + J;                             // [J] 1 / t_j
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x - wg.first_warp * 32, lane = threadIdx.x & 31, warp = tid >> 5;
   const int hl = lane % kH, bl = lane / kH;
   const int h0 = blk * kH, h = h0 + hl;
   const bool live = h < g.H;
 
   // the [S][kH] tile of sign * g (and of the previous iterate): each warp takes rows
-  // 2 warp + bl, 2 warp + bl + 32, ...; the loads of kU rows are issued before any is used
+  // 2 warp + bl, 2 warp + bl + 2 warps, ...; the loads of kU rows are issued before any is used
   {
     constexpr int kU = 4;
-    constexpr int kRowStep = kWarps * kSubLanes;
+    const int kRowStep = kWarps * kSubLanes;
     const float rz = (a.g != nullptr && a.contrib && live) ? a.grz[h] : 0.f;
     for (int s0 = kSubLanes * warp + bl; s0 < S; s0 += kRowStep * kU) {
       float c0[kU], c1[kU], o[kU];
@@ -187,12 +199,12 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
       }
     }
   }
-  for (int j = tid; j < J; j += kItemThreads) {
+  for (int j = tid; j < J; j += kWarps * 32) {
     const float t = (float)(a.mu * tp.beta[j]);
     tj[j] = t;
     itj[j] = 1.f / t;
   }
-  __syncthreads();
+  group_sync(wg);
 
   for (int l = tp.L - 1; l >= 0; --l) {
     for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
@@ -225,7 +237,7 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
       for (int i = bl; i < n; i += kSubLanes) G[(s0 + i) * kH + hl] *= inv;
       if (bl == 0) V[j * kH + hl] = m - tj[j] * log1pf(X / (float)n);
     }
-    __syncthreads();
+    group_sync(wg);
   }
 
   if (a.value_partial != nullptr && warp == 0) {
@@ -253,10 +265,10 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
           a.out[(size_t)s * ld + h] = live ? o : 0.f;
         }
       }
-      __syncthreads();
+      group_sync(wg);
     }
   }
-  __syncthreads();   // shared memory is reused by the caller's next item
+  group_sync(wg);   // shared memory is reused by the caller's next item
 }
 
 // One item of the FP64 best-response value: sign * min over the treeplex of
@@ -265,19 +277,19 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
 // lane layout as sbr_item.
 __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, const double* gv,
                                  bool contrib, const double* grz, double sign,
-                                 double* value_partial, double* sm) {
+                                 double* value_partial, double* sm, WarpGroup wg = kWholeCta) {
   constexpr int kH = kSbrHands;
   const int S = tp.S, ld = g.ld;
-  constexpr int kWarps = kItemThreads / 32;
+  const int kWarps = wg.n_warps;
   double* G = sm;                                  // [S][kH]
   double* V = G + (size_t)S * kH;                  // [J][kH]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x - wg.first_warp * 32, lane = threadIdx.x & 31, warp = tid >> 5;
   const int hl = lane % kH, bl = lane / kH;
   const int h0 = blk * kH, h = h0 + hl;
   const bool live = h < g.H;
   {
     constexpr int kU = 4;
-    constexpr int kRowStep = kWarps * kSubLanes;
+    const int kRowStep = kWarps * kSubLanes;
     const bool neg = sign < 0;
     const double rz = (contrib && live) ? grz[h] : 0.0;
     for (int s0 = kSubLanes * warp + bl; s0 < S; s0 += kRowStep * kU) {
@@ -318,7 +330,7 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
       }
     }
   }
-  __syncthreads();
+  group_sync(wg);
   for (int l = tp.L - 1; l >= 0; --l) {
     for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
       const int s0 = tp.inf_first[j], n = tp.inf_n[j];
@@ -332,7 +344,7 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
       m = fmin(m, __shfl_xor_sync(0xffffffffu, m, kH));
       if (bl == 0) V[j * kH + hl] = m;
     }
-    __syncthreads();
+    group_sync(wg);
   }
   if (warp == 0) {
     double v = 0.0;
@@ -342,7 +354,7 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
     for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
     if (lane == 0) *value_partial = sign * v;
   }
-  __syncthreads();
+  group_sync(wg);
 }
 
 }  // namespace egt
