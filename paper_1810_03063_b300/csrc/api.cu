@@ -1532,9 +1532,11 @@ egt_status egt_batch_step(egt_batch* B, int32_t n_iters, int32_t group, int32_t*
   const int limit = engine_smem_limit(true);
   for (int i = 0; i < n; ++i) {
     const egt_game* G = B->members[act[i]].G;
-    // two SBR / best-response items per CTA at a time where shared memory allows
-    pair[i] = limit > 0 && engine_smem_bytes(G->dg, true) <= (size_t)limit;
-    smem = std::max(smem, engine_smem_bytes(G->dg, pair[i] != 0));
+    // two items per CTA at a time where shared memory allows
+    pair[i] = 0;
+    for (int bit : {kPairTerms, kPairSbr})
+      if (limit > 0 && engine_smem_bytes(G->dg, pair[i] | bit) <= (size_t)limit) pair[i] |= bit;
+    smem = std::max(smem, engine_smem_bytes(G->dg, pair[i]));
     w[i] = iteration_work(G);
     cap[i] = engine_items(G->dg);
   }

@@ -216,12 +216,23 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, Grp gr
 }
 
 // One product phase: every terminal of `player`'s grouping; c64 (FP64 contributions
-// for the residual) may be NULL.
-__device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, Grp gr, int player, const float* in,
-                                         float* c32, double* c64, unsigned char* sm) {
+// for the residual) may be NULL.  With pairs (the job allows them and the group has at
+// least two terminals per CTA) each warp half takes its own terminals.
+__device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, Grp gr, bool pair_ok, int player,
+                                         const float* in, float* c32, double* c64, unsigned char* sm) {
   const int T = player ? g.terms[1].n : g.terms[0].n;
-  for (int item = gr.rank; item < T; item += gr.size)
-    term_item<float>(g, tb.grad, player, item, in, c32, c64, sm);
+  if (!(pair_ok && 2 * gr.size <= T)) {
+    for (int item = gr.rank; item < T; item += gr.size)
+      term_item<float>(g, tb.grad, player, item, in, c32, c64, sm);
+    return;
+  }
+  constexpr int kHalf = kItemThreads / 64;
+  const int half = (int)(threadIdx.x >> 5) >= kHalf ? 1 : 0;
+  unsigned char* hs = sm + half * gradimpl::align16(grad_item_smem(g));
+  for (int base = 2 * gr.rank; base < T; base += 2 * gr.size)
+    if (base + half < T)
+      term_item<float, kItemThreads / 2>(g, tb.grad, player, base + half, in, c32, c64, hs, half * kHalf,
+                                         1 + half);
 }
 
 // Item `item` of player p's FP64 best response of the residual (player 0: min over x of
@@ -283,8 +294,9 @@ struct Sched {
 // One job (game) run by the group `gr`: its tables staged in smem_all, then up to
 // ctl->n_iters iterations.  Returns when the job stops or fails (status recorded).
 __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b, EngineCtl* ctl, Grp gr,
-                                           bool pair_ok, unsigned long long expected,
+                                           int pair_bits, unsigned long long expected,
                                            unsigned long long limit_ns, unsigned char* smem_all) {
+  const bool pair_ok = (pair_bits & kPairSbr) != 0, pair_terms = (pair_bits & kPairTerms) != 0;
   Tabs tb;
   tb.grad = stage_grad_tab(g, smem_all);
   tb.tpx[0] = stage_tpx_tab(g, 0, smem_all + grad_tab_bytes(g));
@@ -406,12 +418,12 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
       if (!phase_end(bar, bk, clk, 0, clock_cta)) return;
     }
     phase_cut(clk, 8, clock_cta);
-    run_grad(g, tb, gr, ot, t_me, t_ot, nullptr, sm);           // the other's loss gradient at v_hat
+    run_grad(g, tb, gr, pair_terms, ot, t_me, t_ot, nullptr, sm);   // the other's loss gradient at v_hat
     if (!phase_end(bar, bk, clk, 1, clock_cta)) return;
     // other_+ = (1 - tau) other + tau other_mu(v_hat)
     run_sbr(g, tb, gr, pair_ok, ot, t_ot, mu_ot, v_ot, tau_f, v_ot_n, nullptr, sm);
     if (!phase_end(bar, bk, clk, 2, clock_cta)) return;
-    run_grad(g, tb, gr, m, v_ot_n, g_me_n, g64_me, sm);         // my loss gradient at other_+
+    run_grad(g, tb, gr, pair_terms, m, v_ot_n, g_me_n, g64_me, sm);   // my loss gradient at other_+
     if (!phase_end(bar, bk, clk, 3, clock_cta)) return;
     // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part.
     // When the residual is due, my FP64 best response (on the FP64 product of the last
@@ -438,10 +450,12 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
       });
     }
     if (!phase_end(bar, bk, clk, 4, clock_cta)) return;
-    {
-      // the other's loss gradient at v_+, and the next v_hat when the same player steps
+    if (sp != 1) {
+      run_grad(g, tb, gr, pair_terms, ot, v_me_n, g_ot_n, g64_ot, sm);   // the other's at v_+
+    } else {
+      // the other's loss gradient at v_+, and the next v_hat (the same player steps again)
       const int T = ot ? g.terms[1].n : g.terms[0].n;
-      const int n_items = T + (sp == 1 ? NB : 0);
+      const int n_items = T + NB;
       for (int item = gr.rank; item < n_items; item += gr.size) {
         if (item < T) {
           term_item<float>(g, tb.grad, ot, item, v_me_n, g_ot_n, g64_ot, sm);
@@ -579,7 +593,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
 __global__ void __launch_bounds__(kItemThreads, 1)
     engine_kernel_one(EngineJob job, unsigned int extra, unsigned long long limit_ns) {
   extern __shared__ __align__(16) unsigned char smem_all[];
-  engine_job(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x}, job.pair != 0,
+  engine_job(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x}, job.pair,
              (unsigned long long)gridDim.x + extra, limit_ns, smem_all);
 }
 
@@ -605,21 +619,23 @@ __global__ void __launch_bounds__(kItemThreads, 1)
       for (int i = threadIdx.x; i < (int)(sizeof(EngineJob) / 8); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    engine_job(job_s.g, job_s.b, job_s.ctl, gr, job_s.pair != 0, (unsigned long long)pg.size + extra, limit_ns,
+    engine_job(job_s.g, job_s.b, job_s.ctl, gr, job_s.pair, (unsigned long long)pg.size + extra, limit_ns,
                smem_all);
   }
 }
 
 }  // namespace
 
-size_t engine_smem_bytes(const DevGame& g, bool pair) {
+size_t engine_smem_bytes(const DevGame& g, int pair_bits) {
   size_t m = 0;
   for (int p = 0; p < 2; ++p) {
     m = std::max(m, sbr_item_smem(g, p));
     m = std::max(m, br_item_smem(g, p));
   }
-  m = pair ? 2 * gradimpl::align16(m) : m;
-  return tabs_bytes(g) + std::max(m, grad_item_smem(g));
+  size_t need = std::max(m, grad_item_smem(g));
+  if (pair_bits & kPairSbr) need = std::max(need, 2 * gradimpl::align16(m));
+  if (pair_bits & kPairTerms) need = std::max(need, 2 * gradimpl::align16(grad_item_smem(g)));
+  return tabs_bytes(g) + need;
 }
 
 cudaError_t engine_launch_one(const EngineJob& job, int grid, size_t smem, unsigned int extra,

@@ -55,14 +55,18 @@ struct EngineJob {
   DevGame g;
   EngineBufs b;
   EngineCtl* ctl;
-  int pair;       // SBR / best-response items may run two at a time on the CTA's warp halves
+  int pair;       // kPair* bits: items that may run two at a time on the CTA's warp halves
   int pad;
 };
 static_assert(sizeof(EngineJob) % 8 == 0, "EngineJob is copied in 8-byte words");
 
+// Items a batch job may pair on the CTA's two warp halves.
+constexpr int kPairSbr = 1;     // smoothed / FP64 best-response items
+constexpr int kPairTerms = 2;   // product (terminal) items
+
 // Dynamic shared memory the driver needs for game g (tables + the largest item, or two
-// SBR / best-response items side by side when pair is set).
-size_t engine_smem_bytes(const DevGame& g, bool pair = false);
+// items side by side for the kPair* bits set).
+size_t engine_smem_bytes(const DevGame& g, int pair_bits = 0);
 
 // Items of the widest phase of game g (more CTAs per game than this idle).
 int engine_items(const DevGame& g);

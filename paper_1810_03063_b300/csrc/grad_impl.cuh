@@ -321,9 +321,17 @@ __device__ __forceinline__ double fx_to_f64(Fx a, int ex) {
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-constexpr int kMaxHandsPerThread = 3;   // ld <= 1536 with 512 threads
+constexpr int kMaxLd = 1536;
 
 }  // namespace gradimpl
+
+// CTA barrier of an item run by kThreads threads: the whole CTA, or a warp half with
+// its own named barrier `bar` (two items side by side).
+template <int kThreads>
+__device__ __forceinline__ void item_sync(int bar) {
+  if (kThreads == kItemThreads) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(kThreads) : "memory");
+}
 
 // Shared memory of one terminal item: F (w in fixed point), P, PC, warp maxima,
 // warp totals (without the staged tables).
@@ -381,16 +389,20 @@ __device__ inline GradTab stage_grad_tab(const DevGame& g, unsigned char* dst) {
 // Contribution of terminal e (index in player `player`'s grouping, DevTerms) to that
 // player's product: c32[e][h] and / or c64[e][h] (either may be NULL) = coef_b x the
 // card-removal / strength sum of w = r_opp (.) in[sigma_opp(b)], without the r_me / Z
-// factor.  One CTA of kItemThreads threads.  `in` is read through L2 (it may have
-// been written earlier in the same launch by other CTAs).
-template <typename TIn>
+// factor.  Run by kThreads threads: the whole CTA, or the warp half starting at warp
+// first_warp with named barrier `bar`; the result does not depend on which (the sums
+// are exact).  `in` is read through L2 (it may have been written earlier in the same
+// launch by other CTAs).
+template <typename TIn, int kThreads = kItemThreads>
 __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player, int e,
                                  const TIn* __restrict__ in, float* __restrict__ c32,
-                                 double* __restrict__ c64, unsigned char* smem) {
+                                 double* __restrict__ c64, unsigned char* smem, int first_warp = 0,
+                                 int bar = 0) {
   using namespace gradimpl;
+  constexpr int kMaxHandsPerThread = (kMaxLd + kThreads - 1) / kThreads;
+  constexpr int kWarps = kThreads / 32;
   const int ld = g.ld, H = g.H, opp = 1 - player;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kWarps = kItemThreads / 32;
+  const int tid = threadIdx.x - first_warp * 32, lane = threadIdx.x & 31, warp = tid >> 5;
   const int lstride = g.lmax + 1;
 
   Fx* F = reinterpret_cast<Fx*>(smem);
@@ -413,19 +425,19 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
   TIn y[kMaxHandsPerThread];
 #pragma unroll
   for (int k = 0; k < kMaxHandsPerThread; ++k) {
-    const int h = tid + k * kItemThreads;
+    const int h = tid + k * kThreads;
     y[k] = h < H ? __ldcg(col + h) : TIn(0);
   }
   int mlg = INT_MIN;
 #pragma unroll
   for (int k = 0; k < kMaxHandsPerThread; ++k) {
-    const int h = tid + k * kItemThreads;
+    const int h = tid + k * kThreads;
     if (h < ld) mlg = max(mlg, wprod(r_opp[h], y[k]).lg);
   }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) mlg = max(mlg, __shfl_xor_sync(0xffffffffu, mlg, d));
   if (lane == 0) wmax[warp] = mlg;
-  __syncthreads();
+  item_sync<kThreads>(bar);
   int M = INT_MIN;
 #pragma unroll
   for (int q = 0; q < kWarps; ++q) M = max(M, wmax[q]);
@@ -433,13 +445,13 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
   // pass 2: exact fixed point
 #pragma unroll
   for (int k = 0; k < kMaxHandsPerThread; ++k) {
-    const int h = tid + k * kItemThreads;
+    const int h = tid + k * kThreads;
     if (h < ld) F[h] = to_fx(wprod(r_opp[h], y[k]), ex);
   }
-  __syncthreads();
+  item_sync<kThreads>(bar);
 
   // exclusive prefix over ascending strength: P[i] = sum_{k < i} w[k], P[ld] = total
-  const int K = (ld + kItemThreads - 1) / kItemThreads;   // raking chunk
+  const int K = (ld + kThreads - 1) / kThreads;   // raking chunk
   const int k0 = min(tid * K, ld), k1 = min(k0 + K, ld);
   Fx loc = fx_zero();
   for (int i = k0; i < k1; ++i) loc = fx_add(loc, F[i]);
@@ -447,7 +459,7 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
   if (lane == 31) wtot[warp] = inc;
   Fx run = fx_shfl_up(inc, 1);
   if (lane == 0) run = fx_zero();
-  __syncthreads();
+  item_sync<kThreads>(bar);
   for (int q = 0; q < warp; ++q) run = fx_add(run, wtot[q]);
   for (int i = k0; i < k1; ++i) {
     P[i] = run;
@@ -468,12 +480,12 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
     if (lane < len) pc[lane + 1] = a0;
     if (lane + 32 < len) pc[lane + 33] = a1;
   }
-  __syncthreads();
+  item_sync<kThreads>(bar);
 
   const Fx W = P[ld];
 #pragma unroll
   for (int k = 0; k < kMaxHandsPerThread; ++k) {
-    const int h = tid + k * kItemThreads;
+    const int h = tid + k * kThreads;
     if (h >= ld) break;
     const uint4 hi = tb.hinfo[h];
     const Fx C0 = PC[hi.z & 0xffffu];
@@ -492,7 +504,7 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
     if (c32 != nullptr) c32[(size_t)e * ld + h] = live ? coef32 * fx_to_f32(val, ex) : 0.f;
     if (c64 != nullptr) c64[(size_t)e * ld + h] = live ? coef64 * fx_to_f64(val, ex) : 0.0;
   }
-  __syncthreads();   // shared memory is reused by the caller's next item
+  item_sync<kThreads>(bar);   // shared memory is reused by the caller's next item
 }
 
 // Product row s of a player at hand h from the terminal contributions: the
