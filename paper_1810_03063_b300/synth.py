@@ -67,8 +67,9 @@ def river_endgame(*, n_cards=52, bet_fracs=(0.5, 1.0), raise_cap=3, stack=10.0,
                   pot=1.0, alpha=0.5, tie_prob=0.25, seed=BASE_SEED, allin=True,
                   bb=None, name="river") -> GameSpec:
     """Draw one seeded river endgame with a 5-card board and 2-card hands."""
-    if n_cards < 9 or n_cards > 52 or n_cards % 4:
-        raise ValueError("n_cards must be a multiple of 4 in [12, 52]")
+    # up to 60 cards (1485 hands, ld 1504): decks above 52 only exercise the library's size limit
+    if n_cards < 9 or n_cards > 60 or n_cards % 4:
+        raise ValueError("n_cards must be a multiple of 4 in [12, 60]")
     rng = np.random.Generator(np.random.PCG64(seed))
     deck_perm = rng.permutation(n_cards)
     board = tuple(sorted(int(c) for c in deck_perm[:5]))
@@ -119,6 +120,13 @@ def large(seed=BASE_SEED) -> GameSpec:
     """52 cards, 1081 hands, bets {0.25, 0.5, 1, 2} x pot + all-in, cap 4, stack 10."""
     return river_endgame(n_cards=52, bet_fracs=(0.25, 0.5, 1.0, 2.0), raise_cap=4, stack=10.0,
                          alpha=0.5, seed=seed, name="large52")
+
+
+def max_size(seed=BASE_SEED) -> GameSpec:
+    """60-card deck: 1485 hands per player (ld 1504, near the library's 1536 limit), bet {1} +
+    all-in, cap 2, stack 2; a size-limit case, not a poker deck."""
+    return river_endgame(n_cards=60, bet_fracs=(1.0,), raise_cap=2, stack=2.0, alpha=1.0,
+                         seed=seed, name="max60")
 
 
 def kuhn() -> GameSpec:

@@ -109,3 +109,29 @@ def test_product_path_never_imports_the_oracle():
     for f in pkg.rglob("*"):
         if f.suffix in (".py", ".cu", ".cuh", ".cpp", ".hpp", ".h"):
             assert not pat.search(f.read_text()), f
+
+
+def test_size_limits():
+    """1485 hands (ld 1504) compile and match the oracle's counts; a deck giving more than
+    1536 hands is refused with its own message."""
+    g = egt.Game(synth.max_size(), device=-1)
+    assert g.H == 1485 and g.ld == 1504
+    spec = synth.max_size()
+    over = np.array([(a, b) for a in range(64) for b in range(a + 1, 64)][:1600], dtype=np.int32)
+    big = synth.GameSpec(**{**spec.__dict__, "n_cards": 64, "hands": over,
+                            "strength": np.arange(len(over), dtype=np.int32),
+                            "ranges": np.full((2, len(over)), 1.0 / len(over))})
+    with pytest.raises(egt.EGTError) as e:
+        egt.Game(big, device=-1)
+    assert "1536" in str(e.value)
+
+
+def test_zero_range_hands_and_tiny_decks_compile():
+    """Hands a player never holds (range 0) and a 12-card deck (21 hands, ld 32) are valid."""
+    spec = synth.river_endgame(n_cards=12, bet_fracs=(1.0,), raise_cap=2, stack=2.0, alpha=1.0)
+    r = spec.ranges.copy()
+    r[0, ::3] = 0.0
+    r[0] /= r[0].sum()
+    g = egt.Game(synth.GameSpec(**{**spec.__dict__, "ranges": r}), device=-1)
+    og = payoff.make_game(synth.GameSpec(**{**spec.__dict__, "ranges": r}))
+    assert g.H == 21 and g.ld == 32 and g.S == og.S and np.isclose(g.Z, og.Z)

@@ -40,11 +40,22 @@ def egtlib():
 GAMES = {}
 
 
+def zero_range_game():
+    """12-card deck (21 hands, one 32-hand tile with 11 padding columns) where player 1
+    never holds every third hand."""
+    spec = synth.river_endgame(n_cards=12, bet_fracs=(1.0,), raise_cap=2, stack=2.0, alpha=1.0)
+    r = spec.ranges.copy()
+    r[0, ::3] = 0.0
+    r[0] /= r[0].sum()
+    return synth.GameSpec(**{**spec.__dict__, "ranges": r, "name": "zero_range12"})
+
+
 def get(name, egtlib):
     if name not in GAMES:
         spec = {"kuhn": synth.kuhn, "tiny": synth.tiny, "full": synth.full_deck,
                 "large": synth.large, "tiny7": lambda: synth.tiny(seed=7),
-                "libratus": lambda: synth.libratus(n_cards=20, stack=2.0)}[name]()
+                "libratus": lambda: synth.libratus(n_cards=20, stack=2.0),
+                "max": synth.max_size, "zero_range": zero_range_game}[name]()
         og = payoff.make_game(spec)
         GAMES[name] = (spec, og, OE.Problem(og), egtlib.Game(spec, device=0))
     return GAMES[name]
@@ -94,7 +105,7 @@ def rand_vec(rng, S, H, kind):
     return rng.random((S, H)) ** 8        # many tiny entries next to large ones
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "tiny7", "full", "libratus"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "tiny7", "full", "libratus", "max", "zero_range"])
 @pytest.mark.parametrize("kind", ["uniform01", "signed", "skewed", "spread"])
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_grad_f32_matches_oracle(egtlib, name, kind, seed):
@@ -116,7 +127,7 @@ def test_grad_f32_matches_oracle(egtlib, name, kind, seed):
         assert torch.all(tout[:, g.H:] == 0)
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus", "max", "zero_range"])
 def test_grad_f64_matches_oracle(egtlib, name):
     spec, og, P, g = get(name, egtlib)
     rng = np.random.default_rng(5)
@@ -172,7 +183,7 @@ def sbr_conditioning(P, player, gvec, mu):
     return kappa, mag
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus", "max", "zero_range"])
 @pytest.mark.parametrize("mu_scale", [1.0, 1e-2, 1e-4])
 def test_smoothed_br_matches_oracle(egtlib, name, mu_scale):
     spec, og, P, g = get(name, egtlib)
@@ -197,7 +208,7 @@ def test_smoothed_br_matches_oracle(egtlib, name, mu_scale):
         assert torch.all(q[:, g.H:] == 0)
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus", "max", "zero_range"])
 def test_best_response_f64_matches_oracle(egtlib, name):
     spec, og, P, g = get(name, egtlib)
     rng = np.random.default_rng(23)
@@ -210,7 +221,7 @@ def test_best_response_f64_matches_oracle(egtlib, name):
         assert abs(got - ref) <= 64 * EPS64 * np.abs(gv).sum()
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus", "max", "zero_range"])
 def test_gap_matches_oracle(egtlib, name):
     spec, og, P, g = get(name, egtlib)
     rng = np.random.default_rng(29)
@@ -225,7 +236,7 @@ def rel_linf(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("name", ["tiny", "full", "libratus"])
+@pytest.mark.parametrize("name", ["tiny", "full", "libratus", "max", "zero_range"])
 @pytest.mark.parametrize("variant", ["theory", "egt"])
 def test_trajectory_plain_egt_100_iterations(egtlib, name, variant):
     spec, og, P, g = get(name, egtlib)
