@@ -46,7 +46,7 @@ def run(egtlib, g, engine, variant, iters, eps=0.0, gap_every=1, log_cap=0):
     return x, y, rep
 
 
-@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus"])
+@pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus", "large"])
 @pytest.mark.parametrize("variant", [0, 1, 2])
 def test_device_engine_equals_host_loop_bitwise(egtlib, name, variant):
     g = game(egtlib, name)

@@ -127,6 +127,22 @@ def test_grad_f32_matches_oracle(egtlib, name, kind, seed):
         assert torch.all(tout[:, g.H:] == 0)
 
 
+def test_grad_large_game_full_size(egtlib):
+    """The large game (508 sequences, 677 terminals per player) at full size: both FP32
+    products of random iterates, every output against the oracle's Kronecker-factored
+    brute force."""
+    spec, og, P, g = get("large", egtlib)
+    rng = np.random.default_rng(11)
+    for player in (0, 1):
+        vin = rng.random((og.S[1 - player], og.H)).astype(np.float32).astype(np.float64)
+        ref = og.Ay(vin) if player == 0 else og.Atx(vin)
+        bound = 8 * EPS32 * abs_product(og, vin, player) + fixed_point_floor(og, vin, player) + 1e-300
+        tout = torch.full((og.S[player], g.ld), float("nan"), device="cuda")
+        g.grad(player, dev(g, vin), tout)
+        err = np.abs(host(g, tout) - ref)
+        assert (err <= bound).all(), (player, float((err / bound).max()))
+
+
 @pytest.mark.parametrize("name", ["kuhn", "tiny", "full", "libratus", "max", "zero_range"])
 def test_grad_f64_matches_oracle(egtlib, name):
     spec, og, P, g = get(name, egtlib)
