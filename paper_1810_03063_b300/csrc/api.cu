@@ -608,7 +608,7 @@ egt_status gap_internal(egt_game* G, const float* x, const float* y, double* gap
   CUDA_TRY(cudaStreamSynchronize(st));
   const double eps = G->pinned[9] - G->pinned[8];
   if (!std::isfinite(eps)) return fail(EGT_ERR_NUMERIC, "non-finite saddle-point residual");
-  *gap_mbb = eps / G->bb * 1000.0;
+  *gap_mbb = eps * (1000.0 / G->bb);   // mbb per hand (the engine uses the same scale)
   return EGT_OK;
 }
 
@@ -780,7 +780,7 @@ void engine_ctl_init(const egt_game* G, EngineCtl& c, int variant, double eps_mb
   c.gap_every = std::max(1, gap_every);
   c.max_t = G->t + n;
   c.eps_mbb = eps_mbb;
-  c.bb = G->bb;
+  c.mbb_scale = 1000.0 / G->bb;
   c.mu[0] = G->mu[0];
   c.mu[1] = G->mu[1];
   c.tau = G->tau;

@@ -332,7 +332,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
   // solver state: meaningful in thread 0 only (identical in every CTA)
   int t = 0, cur = 0, done = 0, backoffs_total = 0, products = 0, gap_checks = 0, reached = 0;
   int status = 0, last_player = -1, last_backoffs = 0, it = 0, me = 0, backoffs = 0, spec = 0;
-  double mu0 = 0, mu1 = 0, tau_as = 0, gap = 0, tau = 0, eps_mbb = 0, bb = 1;
+  double mu0 = 0, mu1 = 0, tau_as = 0, gap = 0, tau = 0, eps_mbb = 0, mbb_scale = 1;
   double last_tau = 0.0 / 0.0, last_egv = 0.0 / 0.0, egv = 0.0 / 0.0;
   bool pre = false;        // v_hat of this iteration already computed (ahead, by the previous one)
   bool new_iter = true;    // the next attempt starts an iteration (else it retries with tau / 2)
@@ -344,7 +344,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
     tau_as = ctl->tau;
     gap = ctl->gap_mbb;
     eps_mbb = ctl->eps_mbb;
-    bb = ctl->bb;
+    mbb_scale = ctl->mbb_scale;
   }
 
   for (;;) {
@@ -549,7 +549,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
         if (gap_due) {
           // eps_sad of the new iterates from the FP64 products of the Step:
           // max_y <y, A^T x> - min_x <x, A y>
-          gap = (red[3] - red[2]) / bb * 1000.0;
+          gap = (red[3] - red[2]) * mbb_scale;
           gap_checks += 1;
           if (!isfinite(gap)) status = EGT_ERR_NUMERIC;
           else reached = eps_mbb > 0 && gap <= eps_mbb ? 1 : 0;

@@ -20,7 +20,7 @@ constexpr int kEnginePhases = 9;
 struct EngineCtl {
   // configuration
   int variant, n_iters, gap_every, max_t;
-  double eps_mbb, bb;
+  double eps_mbb, mbb_scale;   // gap target; 1000 / bb (mbb per unit of payoff)
   // solver state (persists between launches)
   double mu[2];
   double tau;

@@ -117,6 +117,6 @@ extern "C" egt_status egt_gap_noalloc(const egt_game* game, const float* x, cons
   if (e != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("readback: ") + cudaGetErrorString(e));
   const double eps = host_vals[1] - host_vals[0];
   if (!std::isfinite(eps)) return fail(EGT_ERR_NUMERIC, "non-finite saddle-point residual");
-  *gap_mbb = eps / v.bb * 1000.0;
+  *gap_mbb = eps * (1000.0 / v.bb);
   return EGT_OK;
 }
