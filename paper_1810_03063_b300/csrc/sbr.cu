@@ -1,5 +1,5 @@
 // Standalone smoothed-best-response and FP64 best-response kernels: one CTA per
-// 32 hands running the shared bodies of sbr_impl.cuh (Sec. 5 recursion).  The
+// 16 hands running the shared bodies of sbr_impl.cuh (Sec. 5 recursion).  The
 // value summed over hands and root simplexes is reduced in FP64: per-CTA
 // partials, the last CTA to finish adds them in a fixed order (deterministic).
 #include "egt_internal.cuh"

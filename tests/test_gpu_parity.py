@@ -2,9 +2,10 @@
 
 Tolerances are derived from the arithmetic (eps32 = 2^-24, eps64 = 2^-53):
 
-* FP32 product: compensated sums make each terminal's contribution exact to a
-  few roundings of its own magnitude, so |err_i| <= 8 eps32 (|A| |y|)_i.
-* FP64 product: plain double sums over <= 2048 terms, |err_i| <= 64 eps64 (|A| |y|)_i.
+* FP32 product: each terminal's sum is exact in fixed point (down to 2^-87 of
+  its largest term, `fixed_point_floor`) and rounded once, then scaled and the
+  sequence's one or two terminals added: |err_i| <= 8 eps32 (|A| |y|)_i + floor.
+* FP64 product: the same exact sums rounded to FP64: |err_i| <= 64 eps64 (|A| |y|)_i + floor.
 * FP32 SBR: an exponent argument (g_hat - m)/t carries a relative error of a
   few eps32, i.e. an absolute error of about eps32 * kappa with kappa =
   max |g_hat| / t; q_i is a product of L such factors, so
