@@ -270,12 +270,15 @@ __device__ __forceinline__ void reduce_arrays(const double* p, int n, int first,
 // carried tau).
 __device__ __forceinline__ void choose(int variant, int t, double mu0, double mu1, double tau_as, int& me,
                                        double& tau) {
-  if (variant == EGT_THEORY) {
+  if (variant == EGT_AS) {   // (no division on the EGT/as path: FP64 is a narrow pipe here)
+    me = mu0 > mu1 ? 0 : 1;
+    tau = tau_as;
+  } else if (variant == EGT_THEORY) {
     me = t % 2 == 0 ? 0 : 1;
     tau = 2.0 / (t + 3);
   } else {
     me = mu0 > mu1 ? 0 : 1;
-    tau = variant == EGT_PRACTICAL ? 2.0 / (t + 3) : tau_as;
+    tau = 2.0 / (t + 3);
   }
 }
 
@@ -333,7 +336,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
   int t = 0, cur = 0, done = 0, backoffs_total = 0, products = 0, gap_checks = 0, reached = 0;
   int status = 0, last_player = -1, last_backoffs = 0, it = 0, me = 0, backoffs = 0, spec = 0;
   double mu0 = 0, mu1 = 0, tau_as = 0, gap = 0, tau = 0, eps_mbb = 0, mbb_scale = 1;
-  double last_tau = 0.0 / 0.0, last_egv = 0.0 / 0.0, egv = 0.0 / 0.0;
+  double last_tau = 0.0 / 0.0, last_egv = 0.0 / 0.0, egv = 0.0 / 0.0, mu_next = 0;
   bool pre = false;        // v_hat of this iteration already computed (ahead, by the previous one)
   bool new_iter = true;    // the next attempt starts an iteration (else it retries with tau / 2)
   if (lead) {
@@ -364,7 +367,8 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
         // response as the other's EGV part (same gradient, same mu).
         int me2;
         double tau2;
-        choose(variant, t + 1, xs ? (1 - tau) * mu0 : mu0, xs ? mu1 : (1 - tau) * mu1, tau, me2, tau2);
+        mu_next = (1 - tau) * (xs ? mu0 : mu1);   // mu of the stepping player if accepted
+        choose(variant, t + 1, xs ? mu_next : mu0, xs ? mu1 : mu_next, tau, me2, tau2);
         spec = me2 == me ? 1 : (check || gap_due ? 2 : 0);
         sc.cur = cur;
         sc.me = me;
@@ -375,7 +379,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
         sc.tau2 = (float)tau2;
         sc.mu_me = xs ? mu0 : mu1;
         sc.mu_ot = xs ? mu1 : mu0;
-        sc.mu_tilde = (1 - tau) * (xs ? mu0 : mu1);
+        sc.mu_tilde = mu_next;
       }
       sc.stop = stop;
     }
@@ -523,8 +527,8 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
       }
       if (accept) {
         // accept (Alg. 2 last lines): mu_me^+ = (1 - tau) mu_me, swap the iterate buffers
-        if (xs) mu0 *= (1.0 - tau);
-        else mu1 *= (1.0 - tau);
+        if (xs) mu0 = mu_next;   // (1 - tau) mu_x, computed with the attempt
+        else mu1 = mu_next;
         if (variant == EGT_AS) tau_as = tau;
         if (writer && b.log != nullptr && it < b.log_cap) {
           egt_iter_log& L = b.log[it];
