@@ -43,7 +43,8 @@ def drain(srv, limit=10000):
 def test_requests_in_the_mix_equal_solo_solves(egtlib):
     srv = egtlib.Server(0, iters_per_step=37)
     first = [(synth.tiny(), 150.0), (synth.kuhn(), 5.0), (synth.full_deck(seed=synth.BASE_SEED + 5), 40.0)]
-    later = [(synth.tiny(seed=synth.BASE_SEED + 9), 80.0), (synth.tiny(seed=synth.BASE_SEED + 2), 300.0)]
+    later = [(synth.tiny(seed=synth.BASE_SEED + 9), 80.0), (synth.tiny(seed=synth.BASE_SEED + 2), 300.0),
+             (synth.libratus(n_cards=20, stack=2.0), 100.0)]   # menus copied at submission
     ids = [(srv.submit(sp, eps_mbb=eps, max_iters=5000), sp, eps) for sp, eps in first]
     srv.step()
     srv.step()                                   # the first ones run while the others arrive
