@@ -40,7 +40,7 @@ METRIC = "EGT iter/s"
 # L2 flush), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 # -k regex:engine_kernel_one -s 3 -c 1 python bench.py --steps 3 --warmup 3 --no-ttg --cpu-seconds 0
 # --batch-games 0`; to be re-taken (or set to None) whenever the engine kernel changes.
-ENGINE_TRAFFIC_BYTES = None   # the engine changed since the last capture
+ENGINE_TRAFFIC_BYTES = 1873920   # dram read 1 513 728 + write 360 192 B, one ncu pass over one timed launch
 UNIT = "iter/s"
 WORKLOAD = "full-deck river endgame: 52 cards, 1081 hands/player, bets {0.5,1}xpot + all-in, raise cap 3, stack 10, pot 1, EGT/as"
 
@@ -65,6 +65,9 @@ def parse():
                     help="instead of the iteration benchmark: gap against gradient products for theory EGT, "
                          "practical EGT and EGT/as")
     ap.add_argument("--variant-iters", type=int, default=20000)
+    ap.add_argument("--phases", action="store_true",
+                    help="instead of the iteration benchmark: device time per engine phase (egt_engine_trace) "
+                         "over 300 EGT/as iterations of the full-deck, large and Libratus-menu games")
     ap.add_argument("--serve-rates", default="10,100,500", help="arrival rates (requests/s)")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests per rate")
     ap.add_argument("--serve-iters", type=int, default=200, help="iterations per server launch")
@@ -500,6 +503,29 @@ def run_variants(args, local):
             "max_iters": args.variant_iters, "data": "synthetic", "runs": out}
 
 
+def run_phases(args, local):
+    """Per-phase device time of the EGT/as driver, read from the engine's own %globaltimer trace
+    (CTA 0): each phase's average and the part before CTA 0 reached the group barrier."""
+    import torch
+
+    from paper_1810_03063_b300 import egt, synth
+
+    torch.cuda.set_device(local)
+    out = []
+    for name, spec in [("full deck", synth.full_deck()), ("large", synth.large()),
+                       ("Libratus menus", synth.libratus())]:
+        g = egt.Game(spec, device=local)
+        rep = g.solve(variant=egt.EGT_AS, alpha=0.01, eps_mbb=0.0, max_iters=300, gap_every=1)
+        tr = g.engine_trace()
+        tot = sum(v["us"] for v in tr.values())
+        out.append({"game": name, "S": list(g.S), "T": g.T, "iters": rep["iters"],
+                    "us_per_iter": round(tot / rep["iters"], 2),
+                    "phases": {k: {"n": v["n"], "avg_us": round(v["avg_us"], 2),
+                                   "work_us": round(v["avg_work_us"], 2)} for k, v in tr.items()}})
+        g.close()
+    return {"study": "engine phase times (CTA 0, 300 EGT/as iterations)", "data": "synthetic", "games": out}
+
+
 def synth_seed(rate):
     from paper_1810_03063_b300 import synth
     return synth.BASE_SEED + 500 + int(rate)
@@ -582,6 +608,11 @@ def main():
         return
     if args.variants:
         out = run_variants(args, local)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    if args.phases:
+        out = run_phases(args, local)
         if rank == 0:
             print(json.dumps(out))
         return
