@@ -59,6 +59,15 @@ __device__ __forceinline__ Fx fx_scan(Fx v, int lane) {
   }
   return v;
 }
+// inclusive scan within each 16-lane half of the warp (sl = lane & 15)
+__device__ __forceinline__ Fx fx_scan16(Fx v, int sl) {
+#pragma unroll
+  for (int d = 1; d < 16; d <<= 1) {
+    const Fx o = {__shfl_up_sync(0xffffffffu, v.v0, d, 16), __shfl_up_sync(0xffffffffu, v.v1, d, 16)};
+    if (sl >= d) v = fx_add(v, o);
+  }
+  return v;
+}
 
 // 2^e as float / double for the exponent ranges used here (split in two factors)
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
@@ -460,25 +469,37 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
   Fx run = fx_shfl_up(inc, 1);
   if (lane == 0) run = fx_zero();
   item_sync<kThreads>(bar);
-  for (int q = 0; q < warp; ++q) run = fx_add(run, wtot[q]);
+#pragma unroll
+  for (int q = 0; q < kWarps; ++q)   // (unrolled: the loads issue together)
+    if (q < warp) run = fx_add(run, wtot[q]);
   for (int i = k0; i < k1; ++i) {
     P[i] = run;
     run = fx_add(run, F[i]);
   }
   if (k0 < ld && k1 == ld) P[ld] = run;
 
-  // per-card exclusive prefixes, one warp per card slot
-  for (int c = warp; c < g.n_slots; c += kWarps) {
-    const int len = tb.card_len[c];
-    const uint16_t* lst = tb.card_hands + (size_t)c * g.lmax;
-    const Fx v0 = lane < len ? F[lst[lane]] : fx_zero();
-    const Fx v1 = lane + 32 < len ? F[lst[lane + 32]] : fx_zero();
-    const Fx a0 = fx_scan(v0, lane);
-    const Fx a1 = fx_add(fx_scan(v1, lane), fx_shfl(a0, 31));
-    Fx* pc = PC + (size_t)c * lstride;
-    if (lane == 0) pc[0] = fx_zero();
-    if (lane < len) pc[lane + 1] = a0;
-    if (lane + 32 < len) pc[lane + 33] = a1;
+  // per-card exclusive prefixes: a card slot per 16-lane half warp, four consecutive
+  // list entries (at most 64) per lane, summed serially, then one half-warp scan
+  {
+    const int sub = lane >> 4, sl = lane & 15, i0 = 4 * sl;
+    for (int c0 = 2 * warp; c0 < g.n_slots; c0 += 2 * kWarps) {   // (warp-uniform trip count)
+      const int c = c0 + sub;
+      const bool ok = c < g.n_slots;
+      const int len = ok ? tb.card_len[c] : 0;
+      const uint16_t* lst = tb.card_hands + (size_t)(ok ? c : 0) * g.lmax;
+      Fx a[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[j] = i0 + j < len ? F[lst[i0 + j]] : fx_zero();
+#pragma unroll
+      for (int j = 1; j < 4; ++j) a[j] = fx_add(a[j - 1], a[j]);
+      const Fx inc = fx_scan16(a[3], sl);
+      const Fx before = fx_sub(inc, a[3]);
+      Fx* pc = PC + (size_t)(ok ? c : 0) * lstride;
+      if (ok && sl == 0) pc[0] = fx_zero();
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (ok && i0 + j < len) pc[i0 + j + 1] = fx_add(before, a[j]);
+    }
   }
   item_sync<kThreads>(bar);
 
