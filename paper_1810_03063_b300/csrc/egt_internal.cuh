@@ -8,7 +8,7 @@
 namespace egt {
 
 constexpr int kSbrHands = 16;       // hands per SBR / best-response item (two lanes each)
-constexpr int kMaxListLen = 64;     // max hands holding one card (two per lane in a warp scan)
+constexpr int kMaxListLen = 64;     // max hands holding one card (four per lane in a half-warp scan)
 
 // One player's per-hand treeplex on the device (Sec. 4 notation).
 struct DevTpx {

@@ -28,6 +28,7 @@
 // one does not change the FP32 one.
 #pragma once
 #include <climits>
+#include <cstring>
 
 #include "egt_internal.cuh"
 
@@ -37,14 +38,68 @@ constexpr int kItemThreads = 512;     // threads of a CTA of the engine and of t
 
 namespace gradimpl {
 
+// Bit-level helpers that also compile for the host: the exact-arithmetic functions
+// below (w = r y, fixed point, rounding back to FP32 / FP64) are checked on the CPU
+// against rational arithmetic.
+__host__ __device__ __forceinline__ int clz64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned long long umul64hi(unsigned long long a, unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+__host__ __device__ __forceinline__ unsigned long long f64_bits(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  std::memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ double bits_f64(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  std::memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned f32_bits(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  unsigned b;
+  std::memcpy(&b, &x, 4);
+  return b;
+#endif
+}
+__host__ __device__ __forceinline__ float bits_f32(unsigned b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float x;
+  std::memcpy(&x, &b, 4);
+  return x;
+#endif
+}
+
 // fixed point: v0 = integer part, v1 = the next 40 fraction bits (both carry the sign)
 struct Fx {
   long long v0, v1;
 };
 
-__device__ __forceinline__ Fx fx_zero() { return {0, 0}; }
-__device__ __forceinline__ Fx fx_add(Fx a, Fx b) { return {a.v0 + b.v0, a.v1 + b.v1}; }
-__device__ __forceinline__ Fx fx_sub(Fx a, Fx b) { return {a.v0 - b.v0, a.v1 - b.v1}; }
+__host__ __device__ __forceinline__ Fx fx_zero() { return {0, 0}; }
+__host__ __device__ __forceinline__ Fx fx_add(Fx a, Fx b) { return {a.v0 + b.v0, a.v1 + b.v1}; }
+__host__ __device__ __forceinline__ Fx fx_sub(Fx a, Fx b) { return {a.v0 - b.v0, a.v1 - b.v1}; }
 __device__ __forceinline__ Fx fx_shfl_up(Fx a, int d) {
   return {__shfl_up_sync(0xffffffffu, a.v0, d), __shfl_up_sync(0xffffffffu, a.v1, d)};
 }
@@ -76,7 +131,7 @@ __device__ __forceinline__ double pow2d(int e) {
 }
 
 // floor(P / 2^k) of the 128-bit P = hi:lo, low 64 bits
-__device__ __forceinline__ unsigned long long shr128(unsigned long long hi, unsigned long long lo, int k) {
+__host__ __device__ __forceinline__ unsigned long long shr128(unsigned long long hi, unsigned long long lo, int k) {
   if (k <= 0) return lo;
   if (k >= 128) return 0;
   if (k >= 64) return hi >> (k - 64);
@@ -91,9 +146,9 @@ struct WBits {
 };
 
 // w = r * y exactly: 53-bit x 24-bit mantissa product
-__device__ __forceinline__ WBits wprod(double r, float y) {
-  const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
-  const unsigned yb = __float_as_uint(y);
+__host__ __device__ __forceinline__ WBits wprod(double r, float y) {
+  const unsigned long long rb = f64_bits(r);
+  const unsigned yb = f32_bits(y);
   int er = (int)((rb >> 52) & 0x7ffull), ey = (int)((yb >> 23) & 0xffu);
   unsigned long long mr = rb & ((1ull << 52) - 1), my = yb & 0x7fffffu;
   WBits w;
@@ -109,17 +164,17 @@ __device__ __forceinline__ WBits wprod(double r, float y) {
   if (ey == 0) ey = 1;
   else my |= 1ull << 23;
   w.lo = mr * my;
-  w.hi = __umul64hi(mr, my);
+  w.hi = umul64hi(mr, my);
   w.E = (er - 1075) + (ey - 150);
-  const int nb = w.hi ? 128 - __clzll(w.hi) : 64 - __clzll(w.lo);
+  const int nb = w.hi ? 128 - clz64(w.hi) : 64 - clz64(w.lo);
   w.lg = w.E + nb - 1;
   return w;
 }
 
 // w = r * y for an FP64 y: rounded once in FP64, then exact from there
-__device__ __forceinline__ WBits wprod(double r, double y) {
+__host__ __device__ __forceinline__ WBits wprod(double r, double y) {
   const double w = r * y;
-  const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+  const unsigned long long b = f64_bits(w);
   int e = (int)((b >> 52) & 0x7ffull);
   unsigned long long m = b & ((1ull << 52) - 1);
   WBits x;
@@ -135,12 +190,12 @@ __device__ __forceinline__ WBits wprod(double r, double y) {
   x.hi = 0;
   x.lo = m;
   x.E = e - 1075;
-  x.lg = x.E + (64 - __clzll(m)) - 1;
+  x.lg = x.E + (64 - clz64(m)) - 1;
   return x;
 }
 
 // |w| 2^ex as integer part + 40 truncated fraction bits, signed
-__device__ __forceinline__ Fx to_fx(const WBits& w, int ex) {
+__host__ __device__ __forceinline__ Fx to_fx(const WBits& w, int ex) {
   if (w.lg == INT_MIN) return fx_zero();
   const int s = w.E + ex;
   unsigned long long a, b;
@@ -158,7 +213,7 @@ __device__ __forceinline__ Fx to_fx(const WBits& w, int ex) {
 }
 
 // scale so that |w| 2^ex < 2^48 for the largest |w| (sums of 2048 terms < 2^59)
-__device__ __forceinline__ int scale_of(int maxlg) { return maxlg == INT_MIN ? 0 : 47 - maxlg; }
+__host__ __device__ __forceinline__ int scale_of(int maxlg) { return maxlg == INT_MIN ? 0 : 47 - maxlg; }
 
 // |N| of a fixed-point sum, N = v0 2^40 + v1 as a signed 128-bit integer
 // (uh:ul), its sign and bit length (0 when N = 0).
@@ -167,7 +222,7 @@ struct Wide {
   int nb, neg;
 };
 
-__device__ __forceinline__ Wide fx_wide(Fx a) {
+__host__ __device__ __forceinline__ Wide fx_wide(Fx a) {
   unsigned long long lo = (unsigned long long)a.v0 << 40;
   long long hi = a.v0 >> 24;
   const unsigned long long lo2 = lo + (unsigned long long)a.v1;
@@ -181,13 +236,13 @@ __device__ __forceinline__ Wide fx_wide(Fx a) {
     w.ul = ~w.ul + 1ull;
     w.uh = ~w.uh + (w.ul == 0 ? 1ull : 0ull);
   }
-  w.nb = w.uh ? 128 - __clzll(w.uh) : (w.ul ? 64 - __clzll(w.ul) : 0);
+  w.nb = w.uh ? 128 - clz64(w.uh) : (w.ul ? 64 - clz64(w.ul) : 0);
   return w;
 }
 
 // The leading P bits of |N| (nb >= 1, 1 <= P <= 53) rounded to nearest even:
 // the mantissa in [2^(P-1), 2^P]; a carry to 2^P is left to the caller.
-__device__ __forceinline__ unsigned long long round_top(const Wide& w, int P) {
+__host__ __device__ __forceinline__ unsigned long long round_top(const Wide& w, int P) {
   if (w.nb <= P) return w.ul << (P - w.nb);
   const int sh = w.nb - P;
   const unsigned long long mant = shr128(w.uh, w.ul, sh);
@@ -205,7 +260,7 @@ __device__ __forceinline__ unsigned long long round_top(const Wide& w, int P) {
 // significands, minimum normal exponent emin and bias `bias`: the magnitude's
 // bit pattern (exponent field << (P - 1) | fraction), or the all-ones exponent
 // field (infinity) on overflow.
-__device__ __forceinline__ unsigned long long fx_round(const Wide& w, int s, int P, int emin, int emax) {
+__host__ __device__ __forceinline__ unsigned long long fx_round(const Wide& w, int s, int P, int emin, int emax) {
   const int e0 = w.nb - 1 + s;                                // exponent of the leading bit
   if (e0 > emax) return (unsigned long long)(emax - emin + 2) << (P - 1);
   if (e0 >= emin) {
@@ -229,103 +284,52 @@ __device__ __forceinline__ unsigned long long fx_round(const Wide& w, int s, int
   return round_top(w, q);   // a carry to 2^q lands on the smallest normal, as it should
 }
 
-// FP32 value of a fixed-point sum, a x 2^-ex correctly rounded (all 87 bits of
-// the sum count, not only its integer part), with integer operations.  The
-// fraction limb is first carried into [0, 2^40); when the integer limb alone
-// holds 24 or more bits it decides the significand (the fraction only breaks
-// ties), else the whole magnitude fits 64 bits.  Subnormal and overflowing
-// results take the general path.
-__device__ __forceinline__ float fx_to_f32(Fx a, int ex) {
+// FP32 and FP64 values of a fixed-point sum, a x 2^-ex, both correctly rounded
+// (every bit of the sum counts), with integer operations and one normalisation:
+// the magnitude, a 104-bit integer hi:lo, is shifted so that its leading bit is
+// bit 63 of T, and each significand is rounded to nearest even from the top of T,
+// the bits below it (in T, and past T: `rest`) acting as the sticky bit.  Only
+// subnormal and overflowing results branch off, to the general path.
+__host__ __device__ __forceinline__ void fx_to_f32_f64(Fx a, int ex, float& r32, double& r64) {
   const long long v0 = a.v0 + (a.v1 >> 40);
   const unsigned long long f = (unsigned long long)a.v1 & ((1ull << 40) - 1ull);
   const bool neg = v0 < 0;
   const unsigned long long m0 = neg ? (unsigned long long)(-(v0 + (f ? 1 : 0))) : (unsigned long long)v0;
   const unsigned long long m1 = neg ? (f ? (1ull << 40) - f : 0ull) : f;
-  if (m0 == 0 && m1 == 0) return 0.f;
-  unsigned long long q;
-  int e;
-  if (m0 >= (1ull << 24)) {
-    const int nb = 64 - __clzll(m0);
-    const int sh = nb - 24;
-    q = m0 >> sh;
-    const unsigned long long rem = m0 & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (m1 != 0 || (q & 1ull)))) ++q;
-    e = nb - 1 - ex;
-  } else {
-    const unsigned long long u = (m0 << 40) | m1;
-    const int nb = 64 - __clzll(u);
-    if (nb <= 24) {
-      q = u << (24 - nb);
-    } else {
-      const int sh = nb - 24;
-      q = u >> sh;
-      const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-      if (rem > half || (rem == half && (q & 1ull))) ++q;
-    }
-    e = nb - 1 - 40 - ex;
+  const unsigned long long hi = m0 >> 24, lo = (m0 << 40) | m1;   // |sum| = hi 2^64 + lo
+  if ((hi | lo) == 0) {
+    r32 = 0.f;
+    r64 = 0.0;
+    return;
   }
-  if (q == (1ull << 24)) {
+  // hi < 2^40, so lz is in [24, 127] and every shift below is in [1, 63]
+  const int lz = hi ? clz64(hi) : 64 + clz64(lo);
+  const unsigned long long T = lz < 64 ? (hi << lz) | (lo >> (64 - lz)) : lo << (lz - 64);
+  const bool rest = lz < 64 && (lo << lz) != 0;
+  const int e = 127 - lz - 40 - ex;                               // exponent of the leading bit
+  unsigned long long q = T >> 11;
+  q += ((T >> 10) & 1ull) & (unsigned long long)(((T & 0x3ffull) != 0) | rest | (q & 1ull));
+  int e64 = e;
+  if (q >> 53) {
     q >>= 1;
-    ++e;
+    ++e64;
   }
-  if (e + 127 < 1 || e + 127 > 254) {
+  unsigned long long p = T >> 40;
+  p += ((T >> 39) & 1ull) & (unsigned long long)(((T & ((1ull << 39) - 1ull)) != 0) | rest | (p & 1ull));
+  int e32 = e;
+  if (p >> 24) {
+    p >>= 1;
+    ++e32;
+  }
+  if (e64 + 1023 < 1 || e64 + 1023 > 2046 || e32 + 127 < 1 || e32 + 127 > 254) {
     const Wide w = fx_wide(a);
-    return __uint_as_float(((unsigned)w.neg << 31) | (unsigned)fx_round(w, -40 - ex, 24, -126, 127));
+    r64 = bits_f64(((unsigned long long)w.neg << 63) | fx_round(w, -40 - ex, 53, -1022, 1023));
+    r32 = bits_f32(((unsigned)w.neg << 31) | (unsigned)fx_round(w, -40 - ex, 24, -126, 127));
+    return;
   }
-  return __uint_as_float(((unsigned)neg << 31) | ((unsigned)(e + 127) << 23) | (unsigned)(q & 0x7fffffull));
-}
-
-// FP64 value of a fixed-point sum, a x 2^-ex correctly rounded, with integer
-// operations: as fx_to_f32, with the middle case (the integer limb holds 24 to
-// 52 bits) completed by the leading bits of the fraction limb.
-__device__ __forceinline__ double fx_to_f64(Fx a, int ex) {
-  const long long v0 = a.v0 + (a.v1 >> 40);
-  const unsigned long long f = (unsigned long long)a.v1 & ((1ull << 40) - 1ull);
-  const bool neg = v0 < 0;
-  const unsigned long long m0 = neg ? (unsigned long long)(-(v0 + (f ? 1 : 0))) : (unsigned long long)v0;
-  const unsigned long long m1 = neg ? (f ? (1ull << 40) - f : 0ull) : f;
-  if (m0 == 0 && m1 == 0) return 0.0;
-  unsigned long long q;
-  int e;
-  if (m0 >= (1ull << 53)) {
-    const int nb = 64 - __clzll(m0);
-    const int sh = nb - 53;
-    q = m0 >> sh;
-    const unsigned long long rem = m0 & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (m1 != 0 || (q & 1ull)))) ++q;
-    e = nb - 1 - ex;
-  } else if (m0 >= (1ull << 24)) {
-    const int nb = 64 - __clzll(m0);      // 25 .. 53
-    const int k = 53 - nb;                 // bits taken from the fraction limb, 0 .. 28
-    q = (m0 << k) | (m1 >> (40 - k));
-    const int rb = 39 - k;                 // rounding bit of m1
-    const unsigned long long round = (m1 >> rb) & 1ull, sticky = m1 & ((1ull << rb) - 1ull);
-    if (round && (sticky != 0 || (q & 1ull))) ++q;
-    e = nb - 1 - ex;
-  } else {
-    const unsigned long long u = (m0 << 40) | m1;
-    const int nb = 64 - __clzll(u);
-    if (nb <= 53) {
-      q = u << (53 - nb);
-    } else {
-      const int sh = nb - 53;
-      q = u >> sh;
-      const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-      if (rem > half || (rem == half && (q & 1ull))) ++q;
-    }
-    e = nb - 1 - 40 - ex;
-  }
-  if (q == (1ull << 53)) {
-    q >>= 1;
-    ++e;
-  }
-  if (e + 1023 < 1 || e + 1023 > 2046) {
-    const Wide w = fx_wide(a);
-    return __longlong_as_double(
-        (long long)(((unsigned long long)w.neg << 63) | fx_round(w, -40 - ex, 53, -1022, 1023)));
-  }
-  return __longlong_as_double((long long)(((unsigned long long)neg << 63) |
-                                          ((unsigned long long)(e + 1023) << 52) | (q & ((1ull << 52) - 1ull))));
+  r64 = bits_f64(((unsigned long long)neg << 63) | ((unsigned long long)(e64 + 1023) << 52) |
+                 (q & ((1ull << 52) - 1ull)));
+  r32 = bits_f32(((unsigned)neg << 31) | ((unsigned)(e32 + 127) << 23) | (unsigned)(p & 0x7fffffull));
 }
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -522,8 +526,11 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
       val = fx_sub(gt, lt);
     }
     const bool live = h < H;
-    if (c32 != nullptr) c32[(size_t)e * ld + h] = live ? coef32 * fx_to_f32(val, ex) : 0.f;
-    if (c64 != nullptr) c64[(size_t)e * ld + h] = live ? coef64 * fx_to_f64(val, ex) : 0.0;
+    float v32;
+    double v64;
+    fx_to_f32_f64(val, ex, v32, v64);
+    if (c32 != nullptr) c32[(size_t)e * ld + h] = live ? coef32 * v32 : 0.f;
+    if (c64 != nullptr) c64[(size_t)e * ld + h] = live ? coef64 * v64 : 0.0;
   }
   item_sync<kThreads>(bar);   // shared memory is reused by the caller's next item
 }
