@@ -203,10 +203,20 @@ __host__ __device__ __forceinline__ Fx to_fx(const WBits& w, int ex) {
     a = w.lo << s;          // |w| 2^ex < 2^48 keeps this in range
     b = 0;
   } else {
-    const int k = -s;       // fraction bits of P 2^s
-    a = shr128(w.hi, w.lo, k);
-    b = k >= 40 ? (shr128(w.hi, w.lo, k - 40) & ((1ull << 40) - 1))
-                : ((w.lo & ((1ull << k) - 1)) << (40 - k));
+    // Q = P 2^(s + 40) truncated, holding a (integer part) and b (40 fraction bits),
+    // from one right shift of P 2^39 (P < 2^77) by u = -s - 1: no branch on the
+    // magnitude while u < 64 (hands within 35 binades of the column's largest |w|)
+    const unsigned long long Lhi = (w.hi << 39) | (w.lo >> 25), Llo = w.lo << 39;
+    const int u = -s - 1;
+    unsigned long long qhi = 0, qlo = 0;
+    if (u < 64) {
+      qlo = u ? (Llo >> u) | (Lhi << (64 - u)) : Llo;
+      qhi = Lhi >> u;
+    } else if (u < 128) {
+      qlo = Lhi >> (u - 64);
+    }
+    a = (qhi << 24) | (qlo >> 40);
+    b = qlo & ((1ull << 40) - 1);
   }
   const long long sa = (long long)a, sb = (long long)b;
   return w.neg ? Fx{-sa, -sb} : Fx{sa, sb};
