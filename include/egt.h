@@ -331,9 +331,9 @@ EGT_API egt_status egt_batch_add(egt_batch* batch, egt_game* game, const egt_sol
 EGT_API egt_status egt_batch_remove(egt_batch* batch, int32_t slot);
 
 /* One launch advancing every active member by up to n_iters iterations.
- * group: CTAs per member (0: the co-resident CTAs split evenly over the active
- * members, at most the widest phase of the largest one).  *n_active (host, may
- * be NULL): members still active afterwards.  A member stops being active when
+ * group: CTAs per member, members dealt round-robin over the groups (0: the
+ * batch's launch shape, egt_launch_shape below).  *n_active (host, may be
+ * NULL): members still active afterwards.  A member stops being active when
  * it reaches its target (status OK), runs out of iterations (OK, or
  * NOT_CONVERGED if it had a target) or fails (its status). */
 EGT_API egt_status egt_batch_step(egt_batch* batch, int32_t n_iters, int32_t group, int32_t* n_active,
@@ -351,6 +351,52 @@ EGT_API egt_status egt_batch_member(const egt_batch* batch, int32_t slot, egt_ba
 
 /* Launch shape of the last egt_batch_step: CTAs per member and grid (host, either may be NULL). */
 EGT_API egt_status egt_batch_launch_shape(const egt_batch* batch, int32_t* group, int32_t* grid);
+
+/* How egt_batch_step (group = 0) splits the device over the active members.
+ *   share:    0-4: CTAs per member in proportion to work^(share / 4), the work
+ *             being the member's per-iteration cost (4: in proportion to it;
+ *             0: equal shares; default 3, the best on a 64-game mix of 20- and
+ *             52-card endgames); at least one CTA, at most the member's widest
+ *             phase.  When the members outnumber the CTAs, one-CTA groups each
+ *             run a least-loaded share of them (loads weighted the same way).
+ *   pairs:    1 (default): a CTA runs two SBR / best-response / product items at
+ *             a time, one per warp half, where shared memory allows and its group
+ *             has two items per CTA; 0: one item at a time.
+ *   grid_pct: percent of the co-resident CTAs launched, 1-100 (default 100).
+ * No choice changes any member's results (they come from exact products and
+ * fixed-order sums); only the speed differs. */
+typedef struct {
+  int32_t share;
+  int32_t pairs;
+  int32_t grid_pct;
+} egt_launch_shape;
+
+/* Set / read the batch's launch shape (host structs).  Set returns
+ * INVALID_ARG for a field outside the ranges above. */
+EGT_API egt_status egt_batch_set_shape(egt_batch* batch, const egt_launch_shape* shape);
+EGT_API egt_status egt_batch_get_shape(const egt_batch* batch, egt_launch_shape* shape);
+
+#define EGT_TUNE_MAX 16
+
+typedef struct {
+  int32_t n;                            /* candidate shapes timed */
+  int32_t best;                         /* index of the fastest (now the batch's shape), -1 if none */
+  egt_launch_shape shape[EGT_TUNE_MAX];
+  double us_per_iter[EGT_TUNE_MAX];     /* launch time (CUDA events) per member-iteration, best rep */
+  int32_t iters[EGT_TUNE_MAX];          /* member-iterations of that rep */
+} egt_tune_report;
+
+/* Autotune the launch shape on the batch's own work: every candidate (share
+ * 4 / 3 / 2 / 1 / 0 x pairs 1 / 0 on all CTAs, and share 4 / 3 / 2 with pairs
+ * on 75 % of them: 13 shapes) runs `reps` (>= 1) egt_batch_step
+ * launches of n_iters iterations, each timed with CUDA events on `stream`, and
+ * the shape with the least time per member-iteration becomes the batch's.  The
+ * trials are real steps: members advance exactly as egt_batch_step advances
+ * them and may finish while tuning.  A candidate that found no active member is
+ * not timed (us_per_iter = 0, iters = 0); if none was timed the shape is
+ * unchanged and best = -1.  rep (host) may be NULL. */
+EGT_API egt_status egt_batch_tune(egt_batch* batch, int32_t n_iters, int32_t reps, egt_tune_report* rep,
+                                  void* stream);
 
 /* ---- serving: continuous batching of solve requests ------------------------
  * A server owns a batch on one device.  Requests (a game description and

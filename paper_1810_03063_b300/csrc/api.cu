@@ -895,9 +895,15 @@ struct egt_batch {
   EngineGroup* plan_host = nullptr;
   int cap = 0;
   int last_group = 0, last_grid = 0;
+  egt_launch_shape shape{3, 1, 100};
+  cudaEvent_t ev[2] = {nullptr, nullptr};   // timing of tuning trials (created on first use)
 };
 
 namespace {
+
+bool shape_ok(const egt_launch_shape& x) {
+  return x.share >= 0 && x.share <= 4 && (x.pairs == 0 || x.pairs == 1) && x.grid_pct >= 1 && x.grid_pct <= 100;
+}
 
 void batch_free_arrays(egt_batch* B) {
   cudaFree(B->ctl_dev);
@@ -1008,6 +1014,113 @@ egt_status check_slot(const egt_batch* B, int32_t slot) {
   if (!B) return fail(EGT_ERR_INVALID_ARG, "batch is NULL");
   if (slot < 0 || slot >= (int)B->members.size() || !B->members[slot].G)
     return fail(EGT_ERR_INVALID_ARG, "no such batch member");
+  return EGT_OK;
+}
+
+// One batch launch under launch shape `sh` (group > 0 overrides its split); with
+// ms != NULL the engine launch is timed with CUDA events and *done gets the
+// member-iterations it ran.
+egt_status batch_launch(egt_batch* B, int32_t n_iters, int32_t group, const egt_launch_shape& sh,
+                        int32_t* n_active, cudaStream_t st, float* ms, long long* done) {
+  if (n_iters <= 0) return fail(EGT_ERR_INVALID_ARG, "n_iters must be > 0");
+  if (group < 0) return fail(EGT_ERR_INVALID_ARG, "group must be >= 0");
+  DeviceGuard guard(B->device);
+  if (done) *done = 0;
+  if (ms) *ms = 0.f;
+  std::vector<int> act;
+  for (int k = 0; k < (int)B->members.size(); ++k)
+    if (B->members[k].G && B->members[k].active) act.push_back(k);
+  const int n = (int)act.size();
+  if (n_active) *n_active = n;
+  if (n == 0) return EGT_OK;
+  EGT_TRY(batch_reserve(B, n));
+  size_t smem = 0;
+  std::vector<double> w(n);
+  std::vector<int> cap(n), pair(n);
+  const int limit = engine_smem_limit(true);
+  for (int i = 0; i < n; ++i) {
+    const egt_game* G = B->members[act[i]].G;
+    // two items per CTA at a time where shared memory allows
+    pair[i] = 0;
+    if (sh.pairs)
+      for (int bit : {kPairTerms, kPairSbr})
+        if (limit > 0 && engine_smem_bytes(G->dg, pair[i] | bit) <= (size_t)limit) pair[i] |= bit;
+    smem = std::max(smem, engine_smem_bytes(G->dg, pair[i]));
+    const double work = iteration_work(G);
+    w[i] = sh.share == 4 ? work : std::pow(work, 0.25 * sh.share);
+    cap[i] = engine_items(G->dg);
+  }
+  const int maxg_all = engine_max_grid(smem, true);
+  if (maxg_all <= 0) return fail(EGT_ERR_CUDA, "the device-resident driver cannot run on this device");
+  const int maxg = std::max(1, maxg_all * sh.grid_pct / 100);
+  std::vector<EngineGroup> plan;
+  std::vector<int> order;
+  int grid = 0;
+  const int n_groups = plan_groups(w, cap, maxg, group, plan, order, &grid);
+  int widest = 0;
+  for (const auto& e : plan) widest = std::max(widest, e.size);
+  B->last_group = widest;
+  B->last_grid = grid;
+  std::vector<int> slot_of(n);
+  for (int i = 0; i < n; ++i) {
+    slot_of[i] = act[order[i]];
+    egt_batch::Member& m = B->members[slot_of[i]];
+    const int left = m.max_iters - m.iters;
+    engine_ctl_init(m.G, B->ctl_host[i], m.variant, m.eps_mbb, m.gap_every, std::min(n_iters, left));
+    // the residual at the member's last iteration, as egt_solve does
+    B->ctl_host[i].max_t = m.G->t + left;
+    EngineJob& j = B->jobs_host[i];
+    std::memset(&j, 0, sizeof(j));
+    j.g = m.G->dg;
+    j.b = engine_bufs(m.G, nullptr, 0);
+    j.ctl = B->ctl_dev + i;
+    j.pair = pair[order[i]];
+  }
+  std::copy(plan.begin(), plan.end(), B->plan_host);
+  const unsigned extra = (unsigned)std::max(0, env_int("EGT_TEST_BARRIER_EXTRA", 0));
+  const unsigned long long limit_ns =
+      1000000ull * (unsigned long long)std::max(1, env_int("EGT_BARRIER_TIMEOUT_MS", 2000));
+  const auto t0 = std::chrono::steady_clock::now();
+  CUDA_TRY(cudaMemcpyAsync(B->ctl_dev, B->ctl_host, (size_t)n * sizeof(EngineCtl), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(B->jobs_dev, B->jobs_host, (size_t)n * sizeof(EngineJob), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(B->plan_dev, B->plan_host, (size_t)n_groups * sizeof(EngineGroup),
+                           cudaMemcpyHostToDevice, st));
+  if (ms) {
+    for (auto& e : B->ev)
+      if (!e) CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(cudaEventRecord(B->ev[0], st));
+  }
+  const cudaError_t le = engine_launch(B->jobs_dev, B->plan_dev, n_groups, grid, smem, extra, limit_ns, st);
+  if (le != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("engine launch: ") + cudaGetErrorString(le));
+  if (ms) CUDA_TRY(cudaEventRecord(B->ev[1], st));
+  CUDA_TRY(cudaMemcpyAsync(B->ctl_host, B->ctl_dev, (size_t)n * sizeof(EngineCtl), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (ms) CUDA_TRY(cudaEventElapsedTime(ms, B->ev[0], B->ev[1]));
+  int still = 0;
+  for (int i = 0; i < n; ++i) {
+    egt_batch::Member& m = B->members[slot_of[i]];
+    const EngineCtl& c = B->ctl_host[i];
+    engine_ctl_apply(m.G, c, nullptr);
+    m.iters += c.done_iters;
+    if (done) *done += c.done_iters;
+    m.products += c.products;
+    m.backoffs += c.backoffs;
+    m.gap_checks += c.gap_checks;
+    m.seconds += sec;
+    if (c.status != 0) {
+      m.active = 0;
+      m.status = c.status;
+    } else if (c.reached) {
+      m.active = 0;
+      m.status = EGT_OK;
+    } else if (m.iters >= m.max_iters) {
+      m.active = 0;
+      m.status = m.eps_mbb > 0 ? EGT_ERR_NOT_CONVERGED : EGT_OK;
+    }
+    still += m.active;
+  }
+  if (n_active) *n_active = still;
   return EGT_OK;
 }
 
@@ -1478,6 +1591,8 @@ egt_status egt_batch_destroy(egt_batch* B) {
   DeviceGuard guard(B->device);
   cudaDeviceSynchronize();
   batch_free_arrays(B);
+  for (auto& e : B->ev)
+    if (e) cudaEventDestroy(e);
   delete B;
   return EGT_OK;
 }
@@ -1515,93 +1630,57 @@ egt_status egt_batch_remove(egt_batch* B, int32_t slot) {
 
 egt_status egt_batch_step(egt_batch* B, int32_t n_iters, int32_t group, int32_t* n_active, void* stream) {
   if (!B) return fail(EGT_ERR_INVALID_ARG, "batch is NULL");
-  if (n_iters <= 0) return fail(EGT_ERR_INVALID_ARG, "n_iters must be > 0");
-  if (group < 0) return fail(EGT_ERR_INVALID_ARG, "group must be >= 0");
+  return batch_launch(B, n_iters, group, B->shape, n_active, S(stream), nullptr, nullptr);
+}
+
+egt_status egt_batch_set_shape(egt_batch* B, const egt_launch_shape* shape) {
+  if (!B || !shape) return fail(EGT_ERR_INVALID_ARG, "NULL argument");
+  if (!shape_ok(*shape)) return fail(EGT_ERR_INVALID_ARG, "launch shape out of range (share 0-4, pairs 0/1, grid_pct 1-100)");
+  B->shape = *shape;
+  return EGT_OK;
+}
+
+egt_status egt_batch_get_shape(const egt_batch* B, egt_launch_shape* shape) {
+  if (!B || !shape) return fail(EGT_ERR_INVALID_ARG, "NULL argument");
+  *shape = B->shape;
+  return EGT_OK;
+}
+
+egt_status egt_batch_tune(egt_batch* B, int32_t n_iters, int32_t reps, egt_tune_report* rep, void* stream) {
+  if (!B) return fail(EGT_ERR_INVALID_ARG, "batch is NULL");
+  if (n_iters <= 0 || reps <= 0) return fail(EGT_ERR_INVALID_ARG, "n_iters and reps must be > 0");
   DeviceGuard guard(B->device);
-  cudaStream_t st = S(stream);
-  std::vector<int> act;
-  for (int k = 0; k < (int)B->members.size(); ++k)
-    if (B->members[k].G && B->members[k].active) act.push_back(k);
-  const int n = (int)act.size();
-  if (n_active) *n_active = n;
-  if (n == 0) return EGT_OK;
-  EGT_TRY(batch_reserve(B, n));
-  size_t smem = 0;
-  std::vector<double> w(n);
-  std::vector<int> cap(n), pair(n);
-  const int limit = engine_smem_limit(true);
-  for (int i = 0; i < n; ++i) {
-    const egt_game* G = B->members[act[i]].G;
-    // two items per CTA at a time where shared memory allows
-    pair[i] = 0;
-    for (int bit : {kPairTerms, kPairSbr})
-      if (limit > 0 && engine_smem_bytes(G->dg, pair[i] | bit) <= (size_t)limit) pair[i] |= bit;
-    smem = std::max(smem, engine_smem_bytes(G->dg, pair[i]));
-    w[i] = iteration_work(G);
-    cap[i] = engine_items(G->dg);
-  }
-  const int maxg = engine_max_grid(smem, true);
-  if (maxg <= 0) return fail(EGT_ERR_CUDA, "the device-resident driver cannot run on this device");
-  std::vector<EngineGroup> plan;
-  std::vector<int> order;
-  int grid = 0;
-  const int n_groups = plan_groups(w, cap, maxg, group, plan, order, &grid);
-  int widest = 0;
-  for (const auto& e : plan) widest = std::max(widest, e.size);
-  B->last_group = widest;
-  B->last_grid = grid;
-  std::vector<int> slot_of(n);
-  for (int i = 0; i < n; ++i) {
-    slot_of[i] = act[order[i]];
-    egt_batch::Member& m = B->members[slot_of[i]];
-    const int left = m.max_iters - m.iters;
-    engine_ctl_init(m.G, B->ctl_host[i], m.variant, m.eps_mbb, m.gap_every, std::min(n_iters, left));
-    // the residual at the member's last iteration, as egt_solve does
-    B->ctl_host[i].max_t = m.G->t + left;
-    EngineJob& j = B->jobs_host[i];
-    std::memset(&j, 0, sizeof(j));
-    j.g = m.G->dg;
-    j.b = engine_bufs(m.G, nullptr, 0);
-    j.ctl = B->ctl_dev + i;
-    j.pair = pair[order[i]];
-  }
-  std::copy(plan.begin(), plan.end(), B->plan_host);
-  const unsigned extra = (unsigned)std::max(0, env_int("EGT_TEST_BARRIER_EXTRA", 0));
-  const unsigned long long limit_ns =
-      1000000ull * (unsigned long long)std::max(1, env_int("EGT_BARRIER_TIMEOUT_MS", 2000));
-  const auto t0 = std::chrono::steady_clock::now();
-  CUDA_TRY(cudaMemcpyAsync(B->ctl_dev, B->ctl_host, (size_t)n * sizeof(EngineCtl), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(B->jobs_dev, B->jobs_host, (size_t)n * sizeof(EngineJob), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(B->plan_dev, B->plan_host, (size_t)n_groups * sizeof(EngineGroup),
-                           cudaMemcpyHostToDevice, st));
-  const cudaError_t le = engine_launch(B->jobs_dev, B->plan_dev, n_groups, grid, smem, extra, limit_ns, st);
-  if (le != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("engine launch: ") + cudaGetErrorString(le));
-  CUDA_TRY(cudaMemcpyAsync(B->ctl_host, B->ctl_dev, (size_t)n * sizeof(EngineCtl), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  int still = 0;
-  for (int i = 0; i < n; ++i) {
-    egt_batch::Member& m = B->members[slot_of[i]];
-    const EngineCtl& c = B->ctl_host[i];
-    engine_ctl_apply(m.G, c, nullptr);
-    m.iters += c.done_iters;
-    m.products += c.products;
-    m.backoffs += c.backoffs;
-    m.gap_checks += c.gap_checks;
-    m.seconds += sec;
-    if (c.status != 0) {
-      m.active = 0;
-      m.status = c.status;
-    } else if (c.reached) {
-      m.active = 0;
-      m.status = EGT_OK;
-    } else if (m.iters >= m.max_iters) {
-      m.active = 0;
-      m.status = m.eps_mbb > 0 ? EGT_ERR_NOT_CONVERGED : EGT_OK;
+  egt_tune_report r;
+  std::memset(&r, 0, sizeof(r));
+  r.best = -1;
+  for (int pairs : {1, 0})
+    for (int share : {4, 3, 2, 1, 0}) r.shape[r.n++] = egt_launch_shape{share, pairs, 100};
+  for (int share : {4, 3, 2}) r.shape[r.n++] = egt_launch_shape{share, 1, 75};
+  double best = 0.0;
+  for (int k = 0; k < r.n; ++k) {
+    double us_best = 0.0;
+    int it_best = 0;
+    for (int q = 0; q < reps; ++q) {
+      float ms = 0.f;
+      long long done = 0;
+      int active = 0;
+      EGT_TRY(batch_launch(B, n_iters, 0, r.shape[k], &active, S(stream), &ms, &done));
+      if (done <= 0) continue;
+      const double us = 1000.0 * (double)ms / (double)done;
+      if (it_best == 0 || us < us_best) {
+        us_best = us;
+        it_best = (int)done;
+      }
     }
-    still += m.active;
+    r.us_per_iter[k] = us_best;
+    r.iters[k] = it_best;
+    if (it_best > 0 && (r.best < 0 || us_best < best)) {
+      best = us_best;
+      r.best = k;
+    }
   }
-  if (n_active) *n_active = still;
+  if (r.best >= 0) B->shape = r.shape[r.best];
+  if (rep) *rep = r;
   return EGT_OK;
 }
 

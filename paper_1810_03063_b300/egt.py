@@ -80,6 +80,18 @@ class BatchMemberInfo(C.Structure):
     _fields_ = [("active", C.c_int32), ("status", C.c_int32), ("rep", SolveReport)]
 
 
+class LaunchShape(C.Structure):
+    _fields_ = [("share", C.c_int32), ("pairs", C.c_int32), ("grid_pct", C.c_int32)]
+
+
+TUNE_MAX = 16
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("shape", LaunchShape * TUNE_MAX),
+                ("us_per_iter", C.c_double * TUNE_MAX), ("iters", C.c_int32 * TUNE_MAX)]
+
+
 class ServerOpts(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_int64), ("max_running", C.c_int32),
                 ("iters_per_step", C.c_int32), ("group", C.c_int32)]
@@ -133,6 +145,9 @@ _SIGS = {
     "egt_batch_step": [_vp, _i32, _i32, C.POINTER(_i32), _vp],
     "egt_batch_member": [_vp, _i32, C.POINTER(BatchMemberInfo)],
     "egt_batch_launch_shape": [_vp, C.POINTER(_i32), C.POINTER(_i32)],
+    "egt_batch_set_shape": [_vp, C.POINTER(LaunchShape)],
+    "egt_batch_get_shape": [_vp, C.POINTER(LaunchShape)],
+    "egt_batch_tune": [_vp, _i32, _i32, C.POINTER(TuneReport), _vp],
     "egt_server_create": [_i32, C.POINTER(ServerOpts), C.POINTER(_vp)],
     "egt_server_destroy": [_vp],
     "egt_server_submit": [_vp, C.POINTER(GameDesc), C.POINTER(SolveOpts), _f64, C.POINTER(C.c_int64)],
@@ -471,6 +486,27 @@ class Batch:
         g, n = C.c_int32(), C.c_int32()
         _check(lib.egt_batch_launch_shape(self._h, C.byref(g), C.byref(n)))
         return g.value, n.value
+
+    @property
+    def shape(self):
+        """The launch shape of group-0 steps: dict(share, pairs, grid_pct)."""
+        x = LaunchShape()
+        _check(lib.egt_batch_get_shape(self._h, C.byref(x)))
+        return dict(share=x.share, pairs=x.pairs, grid_pct=x.grid_pct)
+
+    @shape.setter
+    def shape(self, value):
+        x = LaunchShape(value["share"], value["pairs"], value["grid_pct"])
+        _check(lib.egt_batch_set_shape(self._h, C.byref(x)))
+
+    def tune(self, n_iters=20, reps=1, stream=None):
+        """Autotune the launch shape on real steps of this batch (egt_batch_tune); returns the
+        candidates with their time per member-iteration and the index of the one kept."""
+        r = TuneReport()
+        _check(lib.egt_batch_tune(self._h, n_iters, reps, C.byref(r), _stream(stream)))
+        cands = [dict(share=r.shape[k].share, pairs=r.shape[k].pairs, grid_pct=r.shape[k].grid_pct,
+                      us_per_iter=r.us_per_iter[k], iters=r.iters[k]) for k in range(r.n)]
+        return dict(best=r.best, candidates=cands)
 
     def run(self, n_iters=200, group=0, stream=None):
         """Step until no member is active; returns the number of steps taken."""

@@ -159,3 +159,45 @@ def test_batch_barrier_timeout_is_reported_per_member(egtlib, monkeypatch):
     y = torch.empty((g.S[1], g.ld), device="cuda")
     assert g.solve(x, y, variant=egtlib.EGT_AS, alpha=0.01, eps_mbb=0.0, max_iters=5)["iters"] == 5
     b.close()
+
+
+def test_autotuned_shapes_leave_results_bitwise_unchanged(egtlib):
+    """egt_batch_tune runs real steps under every candidate launch shape (CTA shares by a
+    power 0-1 of the work; items paired on warp halves or not; all or 75 % of the co-resident
+    CTAs) and keeps the fastest; members still end where solo solves end."""
+    specs = mixed_specs()
+    n = 60
+    b = egtlib.Batch(0)
+    games, slots = [], []
+    for sp in specs:
+        g = egtlib.Game(sp, device=0)
+        g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+        slots.append(b.add(g, variant=egtlib.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1))
+        games.append(g)
+    assert b.shape == dict(share=3, pairs=1, grid_pct=100)
+    rep = b.tune(n_iters=3, reps=1)                # 13 candidates x 3 iterations = 39 of the 60
+    cands = rep["candidates"]
+    assert len(cands) == 13 and 0 <= rep["best"] < 13
+    timed = [c for c in cands if c["iters"] > 0]
+    assert all(c["iters"] == 3 * len(specs) for c in timed)    # every member ran every trial
+    best = cands[rep["best"]]
+    assert best["us_per_iter"] == min(c["us_per_iter"] for c in timed) > 0
+    assert b.shape == {k: best[k] for k in ("share", "pairs", "grid_pct")}
+    b.run(n_iters=7)
+    for sp, g, s in zip(specs, games, slots):
+        xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, n, 1)
+        xb, yb, mu = member_state(egtlib, g)
+        m = b.member(s)
+        assert not m["active"] and m["iters"] == rs["iters"] == n
+        assert torch.equal(xb, xs) and torch.equal(yb, ys), sp.name
+        assert mu == rs["mu"] and m["tau"] == rs["tau"] and m["gap_mbb"] == rs["gap_mbb"]
+    # an idle batch: nothing timed, shape kept
+    rep = b.tune(n_iters=3)
+    assert rep["best"] == -1 and all(c["iters"] == 0 for c in rep["candidates"])
+    with pytest.raises(egtlib.EGTError):
+        b.shape = dict(share=5, pairs=1, grid_pct=100)
+    with pytest.raises(egtlib.EGTError):
+        b.shape = dict(share=2, pairs=1, grid_pct=0)
+    b.shape = dict(share=0, pairs=0, grid_pct=50)
+    assert b.shape == dict(share=0, pairs=0, grid_pct=50)
+    b.close()
