@@ -284,6 +284,26 @@ EGT_API egt_status egt_state_get(egt_game* game, float* x, float* y, double* mu,
 EGT_API egt_status egt_state_set(egt_game* game, const float* x, const float* y, const double* mu,
                          void* stream);
 
+/* Checkpoint of a solve: the iterates plus the scalars of the Alg. 1 / 3
+ * bookkeeping.  The cached products are not part of it: they are the exact
+ * products of the iterates, recomputed on restore. */
+typedef struct {
+  int32_t t;         /* iterations accepted since egt_solver_init (tau_t = 2 / (t + 3)) */
+  double tau;        /* EGT/as step size carried to the next iteration */
+  double mu[2];      /* mu_x, mu_y */
+  double gap_mbb;    /* last residual in mbb per hand (NaN if none yet) */
+} egt_checkpoint;
+
+/* Save: iterates to x, y (device [S_p][ld], either may be NULL) and the scalars
+ * to *ck (host).  Restore: a game created from the same description (any
+ * device) takes the iterates and scalars, initialised or not; the solve then
+ * continues bit for bit as the uninterrupted one (same iterates, mu, tau,
+ * residuals).  Restore returns INVALID_ARG for mu <= 0, tau outside (0, 1] or
+ * t < 0. */
+EGT_API egt_status egt_checkpoint_get(egt_game* game, float* x, float* y, egt_checkpoint* ck, void* stream);
+EGT_API egt_status egt_checkpoint_set(egt_game* game, const float* x, const float* y, const egt_checkpoint* ck,
+                                      void* stream);
+
 /* eps_sad of the current iterates in mbb per hand (host out), as egt_gap computes
  * it: the stopping test of Alg. 1 / 3. */
 EGT_API egt_status egt_state_gap(egt_game* game, double* gap_mbb, void* stream);

@@ -1386,6 +1386,27 @@ egt_status egt_state_set(egt_game* G, const float* x, const float* y, const doub
   return EGT_OK;
 }
 
+egt_status egt_checkpoint_get(egt_game* G, float* x, float* y, egt_checkpoint* ck, void* stream) {
+  if (!ck) return fail(EGT_ERR_INVALID_ARG, "ck is NULL");
+  EGT_TRY(egt_state_get(G, x, y, ck->mu, stream));
+  ck->t = G->t;
+  ck->tau = G->tau;
+  ck->gap_mbb = G->last_gap;
+  return EGT_OK;
+}
+
+egt_status egt_checkpoint_set(egt_game* G, const float* x, const float* y, const egt_checkpoint* ck,
+                              void* stream) {
+  if (!ck) return fail(EGT_ERR_INVALID_ARG, "ck is NULL");
+  if (ck->t < 0) return fail(EGT_ERR_INVALID_ARG, "t must be >= 0");
+  if (!(ck->tau > 0 && ck->tau <= 1)) return fail(EGT_ERR_INVALID_ARG, "tau must be in (0, 1]");
+  EGT_TRY(egt_state_set(G, x, y, ck->mu, stream));
+  G->t = ck->t;
+  G->tau = ck->tau;
+  G->last_gap = ck->gap_mbb;
+  return EGT_OK;
+}
+
 egt_status egt_state_gap(egt_game* G, double* gap_mbb, void* stream) {
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");

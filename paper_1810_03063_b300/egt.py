@@ -80,6 +80,10 @@ class BatchMemberInfo(C.Structure):
     _fields_ = [("active", C.c_int32), ("status", C.c_int32), ("rep", SolveReport)]
 
 
+class Checkpoint(C.Structure):
+    _fields_ = [("t", C.c_int32), ("tau", C.c_double), ("mu", C.c_double * 2), ("gap_mbb", C.c_double)]
+
+
 class LaunchShape(C.Structure):
     _fields_ = [("share", C.c_int32), ("pairs", C.c_int32), ("grid_pct", C.c_int32)]
 
@@ -132,6 +136,8 @@ _SIGS = {
     "egt_step": [_vp, _i32, C.POINTER(_f64), _i32, C.POINTER(StepInfo), _vp],
     "egt_state_get": [_vp, _vp, _vp, _vp, _vp],
     "egt_state_set": [_vp, _vp, _vp, _vp, _vp],
+    "egt_checkpoint_get": [_vp, _vp, _vp, C.POINTER(Checkpoint), _vp],
+    "egt_checkpoint_set": [_vp, _vp, _vp, C.POINTER(Checkpoint), _vp],
     "egt_solve": [_vp, C.POINTER(SolveOpts), _vp, _vp, C.POINTER(SolveReport), _vp],
     "egt_state_gap": [_vp, C.POINTER(_f64), _vp],
     "egt_gap_noalloc": [_vp, _vp, _vp, C.POINTER(_f64), _vp],
@@ -380,6 +386,40 @@ class Game:
     def state_set(self, x, y, mu, stream=None):
         m = (C.c_double * 2)(*mu)
         _check(lib.egt_state_set(self._h, _ptr(x), _ptr(y), C.cast(m, C.c_void_p), _stream(stream)))
+
+    def checkpoint(self, x=None, y=None, stream=None):
+        """Save the solve: iterates into x, y (device, may be None) and the scalars, returned as
+        dict(t, tau, mu, gap_mbb) (egt_checkpoint_get)."""
+        ck = Checkpoint()
+        _check(lib.egt_checkpoint_get(self._h, _ptr(x), _ptr(y), C.byref(ck), _stream(stream)))
+        return dict(t=ck.t, tau=ck.tau, mu=(ck.mu[0], ck.mu[1]), gap_mbb=ck.gap_mbb)
+
+    def restore(self, x, y, scalars, stream=None):
+        """Continue a saved solve (egt_checkpoint_set)."""
+        ck = Checkpoint(scalars["t"], scalars["tau"], (C.c_double * 2)(*scalars["mu"]), scalars["gap_mbb"])
+        _check(lib.egt_checkpoint_set(self._h, _ptr(x), _ptr(y), C.byref(ck), _stream(stream)))
+
+    def save(self, path):
+        """Checkpoint to a host .npz file: x, y ([S_p][ld] FP32) and the scalars."""
+        import torch
+        x = torch.empty((self.S[0], self.ld), device=f"cuda:{self.device}")
+        y = torch.empty((self.S[1], self.ld), device=f"cuda:{self.device}")
+        sc = self.checkpoint(x, y)
+        torch.cuda.synchronize(self.device)
+        np.savez(path, x=x.cpu().numpy(), y=y.cpu().numpy(), t=sc["t"], tau=sc["tau"],
+                 mu=np.array(sc["mu"]), gap_mbb=sc["gap_mbb"])
+
+    def load(self, path):
+        """Continue the solve saved by save(path) on this game (same description)."""
+        import torch
+        d = np.load(path)
+        if d["x"].shape != (self.S[0], self.ld) or d["y"].shape != (self.S[1], self.ld):
+            raise EGTError(1, "checkpoint shapes do not match this game")
+        x = torch.from_numpy(d["x"]).to(f"cuda:{self.device}")
+        y = torch.from_numpy(d["y"]).to(f"cuda:{self.device}")
+        self.restore(x, y, dict(t=int(d["t"]), tau=float(d["tau"]), mu=tuple(float(v) for v in d["mu"]),
+                                gap_mbb=float(d["gap_mbb"])))
+        torch.cuda.synchronize(self.device)
 
     ENGINE_PHASES = ("sbr_hat", "grad_1", "sbr_other", "grad_2", "sbr_tilde", "grad_3", "tail",
                      "decisions", "top")

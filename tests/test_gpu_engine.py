@@ -116,3 +116,36 @@ def test_barrier_timeout_is_reported_and_context_survives(egtlib, monkeypatch):
     xd, yd, rd = run(egtlib, g, egtlib.ENGINE_DEVICE, 2, 10)
     xh, yh, rh = run(egtlib, g, egtlib.ENGINE_HOST, 2, 10)
     assert torch.equal(xd, xh)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_checkpoint_resume_in_a_fresh_game_is_bitwise(egtlib, tmp_path, variant):
+    """A solve saved to a host .npz file (iterates + t, tau, mu, residual) and restored into a
+    fresh game built from the same description continues exactly as the uninterrupted solve."""
+    spec = synth.full_deck(seed=synth.BASE_SEED + 7)
+    a = egtlib.Game(spec, device=0)
+    a.solver_init(variant=variant, alpha=0.01)
+    a.iterate(23, variant=variant, gap_every=4)
+    path = str(tmp_path / "solve.npz")
+    a.save(path)
+    ra = a.iterate(31, variant=variant, gap_every=4)
+    xa = torch.empty((a.S[0], a.ld), device="cuda")
+    ya = torch.empty((a.S[1], a.ld), device="cuda")
+    ca = a.checkpoint(xa, ya)
+    b = egtlib.Game(spec, device=0)             # never initialised
+    b.load(path)
+    assert b.checkpoint()["t"] == 23
+    rb = b.iterate(31, variant=variant, gap_every=4)
+    xb = torch.empty_like(xa)
+    yb = torch.empty_like(ya)
+    cb = b.checkpoint(xb, yb)
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xb) and torch.equal(ya, yb)
+    assert ca == cb and ca["t"] == 54
+    assert (ra["iters"], ra["backoffs"], ra["gap_mbb"], ra["mu"], ra["tau"]) == \
+        (rb["iters"], rb["backoffs"], rb["gap_mbb"], rb["mu"], rb["tau"])
+    bad = dict(cb, tau=0.0)
+    with pytest.raises(egtlib.EGTError):
+        b.restore(xb, yb, bad)
+    a.close()
+    b.close()
