@@ -217,9 +217,17 @@ typedef enum {
   EGT_AS = 2          /* "EGT/as": Alg. 3 + 4, aggressive tau with backtracking on EGV < 0 */
 } egt_variant;
 
+/* One accepted iteration: t, the player that stepped, back-offs (Alg. 4), its
+ * tau, mu after it, EGV (EGT/as; NaN otherwise), the last residual computed
+ * before its update (mbb per hand; with gap_every = 1 that of the iterates it
+ * started from; NaN if none), and a clock reading at
+ * acceptance in ns (the device's global timer for the device engine, the
+ * host's steady clock for the host loop): differences within one solve are
+ * elapsed time. */
 typedef struct {
   int32_t t, player, backoffs;
   double tau, mu[2], egv, gap_mbb;
+  uint64_t time_ns;
 } egt_iter_log;
 
 /* alpha: practical variants start from mu = alpha ||A|| sqrt(M_X M_Y) and

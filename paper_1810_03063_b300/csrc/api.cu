@@ -1527,6 +1527,8 @@ egt_status egt_solve(egt_game* G, const egt_solve_opts* o, float* x_out, float* 
       L.mu[1] = G->mu[1];
       L.egv = info.egv;
       L.gap_mbb = gap;
+      L.time_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                      std::chrono::steady_clock::now().time_since_epoch()).count();
     }
     ++t;
   }

@@ -540,6 +540,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
           L.mu[1] = mu1;
           L.egv = check ? egv : 0.0 / 0.0;
           L.gap_mbb = gap;
+          L.time_ns = global_ns();
         }
         cur = 1 - cur;
         t += 1;

@@ -36,6 +36,24 @@ class EGTError(RuntimeError):
         self.status = status
 
 
+def write_log_jsonl(path, log):
+    """One JSON object per accepted iteration of a solve's log (solve(..., log_cap=n)["log"]):
+    t, player, tau, mu_x, mu_y, EGV, the residual before the iteration's update (mbb per hand),
+    back-offs, gradient products so far (3 per Step attempt) and seconds since the first logged
+    iteration."""
+    import json
+    products = 0
+    t0 = log[0]["time_ns"] if log else 0
+    with open(path, "w") as f:
+        for e in log:
+            products += 3 * (1 + e["backoffs"])
+            rec = dict(t=e["t"], player=e["player"], tau=e["tau"], mu_x=e["mu"][0], mu_y=e["mu"][1],
+                       egv=None if e["egv"] != e["egv"] else e["egv"],
+                       gap_mbb=None if e["gap_mbb"] != e["gap_mbb"] else e["gap_mbb"],
+                       backoffs=e["backoffs"], products=products, seconds=(e["time_ns"] - t0) * 1e-9)
+            f.write(json.dumps(rec) + "\n")
+
+
 class Menu(C.Structure):
     _fields_ = [("n", C.c_int32), ("fracs", C.POINTER(C.c_double)), ("allin", C.c_int32),
                 ("fold", C.c_int32)]
@@ -59,7 +77,7 @@ class Dims(C.Structure):
 class IterLog(C.Structure):
     _fields_ = [("t", C.c_int32), ("player", C.c_int32), ("backoffs", C.c_int32),
                 ("tau", C.c_double), ("mu", C.c_double * 2), ("egv", C.c_double),
-                ("gap_mbb", C.c_double)]
+                ("gap_mbb", C.c_double), ("time_ns", C.c_uint64)]
 
 
 class SolveOpts(C.Structure):
@@ -472,7 +490,7 @@ class Game:
             n = min(rep.iters, o.log_cap)
             out["log"] = [dict(t=log[i].t, player=log[i].player, backoffs=log[i].backoffs,
                                tau=log[i].tau, mu=(log[i].mu[0], log[i].mu[1]), egv=log[i].egv,
-                               gap_mbb=log[i].gap_mbb) for i in range(n)]
+                               gap_mbb=log[i].gap_mbb, time_ns=log[i].time_ns) for i in range(n)]
         return out
 
 

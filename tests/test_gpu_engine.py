@@ -149,3 +149,22 @@ def test_checkpoint_resume_in_a_fresh_game_is_bitwise(egtlib, tmp_path, variant)
         b.restore(xb, yb, bad)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_iteration_log_has_times_and_writes_jsonl(egtlib, tmp_path, engine):
+    import json
+    g = game(egtlib, "tiny")
+    _, _, rep = run(egtlib, g, engine, 2, 40, log_cap=40)
+    log = rep["log"]
+    assert len(log) == 40 and [e["t"] for e in log] == list(range(40))
+    times = [e["time_ns"] for e in log]
+    assert all(b >= a for a, b in zip(times, times[1:])) and times[-1] > times[0]
+    path = str(tmp_path / "solve.jsonl")
+    egtlib.write_log_jsonl(path, log)
+    recs = [json.loads(line) for line in open(path)]
+    assert len(recs) == 40 and recs[0]["seconds"] == 0.0 and recs[-1]["seconds"] > 0
+    assert recs[-1]["products"] == 3 * sum(1 + e["backoffs"] for e in log)
+    assert all(r["egv"] is not None and r["egv"] >= 0 for r in recs)     # EGT/as accepts EGV >= 0 only
+    # the residual of the iterates each iteration started from (gap_every = 1)
+    assert all(r["gap_mbb"] is not None and r["gap_mbb"] > 0 for r in recs)
