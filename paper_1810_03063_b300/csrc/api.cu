@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/egt.h"
 #include "egt_internal.cuh"
 #include "engine.cuh"
@@ -495,6 +497,14 @@ void free_game(egt_game* G) {
 }
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// An NVTX range over a public call (shown by Nsight tools; a no-op without one).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 egt_status check_player(int p) {
   if (p != 0 && p != 1) return fail(EGT_ERR_INVALID_ARG, "player must be 0 or 1");
@@ -1131,6 +1141,7 @@ extern "C" {
 const char* egt_last_error(void) { return g_last_error.c_str(); }
 
 egt_status egt_create_game(const egt_game_desc* desc, int32_t device, void* stream, egt_game** out) {
+  Range nvtx_range("egt_create_game");
   if (!out) return fail(EGT_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   EGT_TRY(validate(desc));
@@ -1262,6 +1273,7 @@ egt_status egt_terminal_query(const egt_game* G, int32_t* seq1, int32_t* seq2, i
 }
 
 egt_status egt_grad(egt_game* G, int32_t player, const float* in, float* out, void* stream) {
+  Range nvtx_range("egt_grad");
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
   EGT_TRY(check_player(player));
@@ -1277,6 +1289,7 @@ egt_status egt_grad(egt_game* G, int32_t player, const float* in, float* out, vo
 }
 
 egt_status egt_grad_f64(egt_game* G, int32_t player, const double* in, double* out, void* stream) {
+  Range nvtx_range("egt_grad_f64");
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
   EGT_TRY(check_player(player));
@@ -1293,6 +1306,7 @@ egt_status egt_grad_f64(egt_game* G, int32_t player, const double* in, double* o
 
 egt_status egt_smoothed_br(egt_game* G, int32_t player, const float* g, double mu, float* q_out,
                            double* value_out, void* stream) {
+  Range nvtx_range("egt_smoothed_br");
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
   EGT_TRY(check_player(player));
@@ -1328,6 +1342,7 @@ egt_status egt_best_response_f64(egt_game* G, int32_t player, const double* g, d
 }
 
 egt_status egt_gap(egt_game* G, const float* x, const float* y, double* gap_mbb, void* stream) {
+  Range nvtx_range("egt_gap");
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
   EGT_TRY(check_ptr(x, "x"));
@@ -1338,6 +1353,7 @@ egt_status egt_gap(egt_game* G, const float* x, const float* y, double* gap_mbb,
 }
 
 egt_status egt_solver_init(egt_game* G, const egt_solve_opts* opts, void* stream) {
+  Range nvtx_range("egt_solver_init");
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
   DeviceGuard guard(G->device);
@@ -1346,6 +1362,7 @@ egt_status egt_solver_init(egt_game* G, const egt_solve_opts* opts, void* stream
 
 egt_status egt_step(egt_game* G, int32_t player, double* tau_inout, int32_t mode, egt_step_info* info,
                     void* stream) {
+  Range nvtx_range("egt_step");
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
   DeviceGuard guard(G->device);
@@ -1408,6 +1425,7 @@ egt_status egt_checkpoint_set(egt_game* G, const float* x, const float* y, const
 }
 
 egt_status egt_state_gap(egt_game* G, double* gap_mbb, void* stream) {
+  Range nvtx_range("egt_state_gap");
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
   if (!G->initialised) return fail(EGT_ERR_INVALID_ARG, "egt_solver_init has not been called");
@@ -1418,6 +1436,7 @@ egt_status egt_state_gap(egt_game* G, double* gap_mbb, void* stream) {
 
 egt_status egt_iterate(egt_game* G, const egt_solve_opts* o, int32_t n_iters, egt_solve_report* rep,
                        void* stream) {
+  Range nvtx_range("egt_iterate");
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
   if (!G->initialised) return fail(EGT_ERR_INVALID_ARG, "egt_solver_init has not been called");
@@ -1442,6 +1461,7 @@ egt_status egt_iterate(egt_game* G, const egt_solve_opts* o, int32_t n_iters, eg
 
 egt_status egt_solve(egt_game* G, const egt_solve_opts* o, float* x_out, float* y_out,
                      egt_solve_report* rep, void* stream) {
+  Range nvtx_range("egt_solve");
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
   if (!o) return fail(EGT_ERR_INVALID_ARG, "opts is NULL");
@@ -1652,6 +1672,7 @@ egt_status egt_batch_remove(egt_batch* B, int32_t slot) {
 }
 
 egt_status egt_batch_step(egt_batch* B, int32_t n_iters, int32_t group, int32_t* n_active, void* stream) {
+  Range nvtx_range("egt_batch_step");
   if (!B) return fail(EGT_ERR_INVALID_ARG, "batch is NULL");
   return batch_launch(B, n_iters, group, B->shape, n_active, S(stream), nullptr, nullptr);
 }
@@ -1670,6 +1691,7 @@ egt_status egt_batch_get_shape(const egt_batch* B, egt_launch_shape* shape) {
 }
 
 egt_status egt_batch_tune(egt_batch* B, int32_t n_iters, int32_t reps, egt_tune_report* rep, void* stream) {
+  Range nvtx_range("egt_batch_tune");
   if (!B) return fail(EGT_ERR_INVALID_ARG, "batch is NULL");
   if (n_iters <= 0 || reps <= 0) return fail(EGT_ERR_INVALID_ARG, "n_iters and reps must be > 0");
   DeviceGuard guard(B->device);
