@@ -65,6 +65,10 @@ def parse():
                     help="instead of the iteration benchmark: gap against gradient products for theory EGT, "
                          "practical EGT and EGT/as")
     ap.add_argument("--variant-iters", type=int, default=20000)
+    ap.add_argument("--batch-solve", action="store_true",
+                    help="instead of the iteration benchmark: the batched mix solved to 1 mbb/hand per game, "
+                         "one egt_batch_step launch per --batch-solve-iters iterations, against egt_solve per game")
+    ap.add_argument("--batch-solve-iters", type=int, default=200)
     ap.add_argument("--phases", action="store_true",
                     help="instead of the iteration benchmark: device time per engine phase (egt_engine_trace) "
                          "over 300 EGT/as iterations of the full-deck, large and Libratus-menu games")
@@ -523,6 +527,75 @@ def run_variants(args, local):
             "max_iters": args.variant_iters, "data": "synthetic", "runs": out}
 
 
+def run_batch_solve(args, local):
+    """Solves/s at gap <= 1 mbb/hand: the --batch-games endgame mix solved to 1 mbb/hand each
+    (EGT/as, residual every iteration, 20 000 iterations at most), batched (all games in one
+    egt_batch_step launch per --batch-solve-iters iterations, each game stopping at its own
+    target) against one egt_solve per game in turn.  A member's iterates equal its solo solve's
+    bit for bit, so both runs do the same iterations; completion times are wall clock from the
+    start of each run."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_1810_03063_b300 import egt, synth
+
+    torch.cuda.set_device(local)
+    specs = synth.batch_mix(args.batch_games)
+    games = [egt.Game(sp, device=local) for sp in specs]
+    cap = 20000
+    for g in games:                                    # warm-up (module load, opt-in)
+        g.solve(variant=egt.EGT_AS, alpha=0.01, eps_mbb=1.0, max_iters=5, gap_every=1)
+    torch.cuda.synchronize()
+    seq_done, seq_iters, seq_ok = [], [], 0
+    t0 = time.perf_counter()
+    for g in games:
+        rep = g.solve(variant=egt.EGT_AS, alpha=0.01, eps_mbb=1.0, max_iters=cap, gap_every=1)
+        seq_done.append(time.perf_counter() - t0)
+        seq_iters.append(rep["iters"])
+        seq_ok += rep["status"] == "EGT_OK"
+    seq_s = time.perf_counter() - t0
+
+    for g in games:
+        g.solver_init(variant=egt.EGT_AS, alpha=0.01)
+    torch.cuda.synchronize()
+    bt = egt.Batch(local)
+    slots = [bt.add(g, variant=egt.EGT_AS, eps_mbb=1.0, max_iters=cap, gap_every=1) for g in games]
+    bat_done = [None] * len(games)
+    launches = 0
+    t0 = time.perf_counter()
+    while True:
+        active = bt.step(args.batch_solve_iters)
+        launches += 1
+        now = time.perf_counter() - t0
+        for i, s in enumerate(slots):
+            if bat_done[i] is None and not bt.member(s)["active"]:
+                bat_done[i] = now
+        if active == 0:
+            break
+    bat_s = time.perf_counter() - t0
+    members = [bt.member(s) for s in slots]
+    bt.close()
+    for g in games:
+        g.close()
+    same = all(m["iters"] == n for m, n in zip(members, seq_iters))
+    pct = lambda v, q: round(float(np.percentile(v, q)), 3)
+    return {"metric": "solves/s at gap <= 1 mbb/hand", "unit": "solves/s", "higher_is_better": True,
+            "workload": f"{len(games)} mixed river endgames (20/52-card decks, raise caps 2-4, 1-4 bet sizes), "
+                        "EGT/as to 1 mbb/hand each, FP64 residual every iteration",
+            "batched": {"solves_per_s": round(len(games) / bat_s, 3), "seconds": round(bat_s, 2),
+                        "reached": sum(m["status"] == "EGT_OK" for m in members), "launches": launches,
+                        "iters_per_launch": args.batch_solve_iters,
+                        "completion_p50_s": pct(bat_done, 50), "completion_p99_s": pct(bat_done, 99)},
+            "one_game_per_launch": {"solves_per_s": round(len(games) / seq_s, 3), "seconds": round(seq_s, 2),
+                                    "reached": seq_ok, "completion_p50_s": pct(seq_done, 50),
+                                    "completion_p99_s": pct(seq_done, 99)},
+            "speedup": round(seq_s / bat_s, 3), "same_iterations": same,
+            "iters": {"min": int(min(seq_iters)), "median": int(np.median(seq_iters)), "max": int(max(seq_iters))},
+            "data": "synthetic"}
+
+
 def run_phases(args, local):
     """Per-phase device time of the EGT/as driver, read from the engine's own %globaltimer trace
     (CTA 0): each phase's average and the part before CTA 0 reached the group barrier."""
@@ -628,6 +701,11 @@ def main():
         return
     if args.variants:
         out = run_variants(args, local)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    if args.batch_solve:
+        out = run_batch_solve(args, local)
         if rank == 0:
             print(json.dumps(out))
         return
