@@ -363,7 +363,7 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
   for (int p = 0; p < 2; ++p) {
     bytes += ld * (2 * sizeof(float) + 2 * sizeof(double));
     const Treeplex& T = C.tpx[p];
-    bytes += (4 * T.J + T.L + 1 + T.S + 1 + T.child_idx.size()) * sizeof(int) + T.J * (sizeof(double) + sizeof(float));
+    bytes += (4 * T.J + T.L + 1 + 2 * T.S + 1 + T.child_idx.size()) * sizeof(int) + T.J * (sizeof(double) + sizeof(float));
     bytes += (tptr[p].size() + 2 * topp[p].size()) * sizeof(int) + tcoef[p].size() * (sizeof(float) + sizeof(double));
   }
   bytes += 64 * 256;   // alignment slack
@@ -414,6 +414,10 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
     dt.level_ptr = (const int*)put(T.level_ptr.data(), (T.L + 1) * 4);
     dt.child_ptr = (const int*)put(T.child_ptr.data(), (T.S + 1) * 4);
     dt.child_idx = (const int*)put(T.child_idx.data(), T.child_idx.size() * 4);
+    std::vector<int> seq_par(T.S, -1);
+    for (int j = 0; j < T.J; ++j)
+      for (int i = 0; i < T.inf_n[j]; ++i) seq_par[T.inf_first[j] + i] = T.inf_parent[j];
+    dt.seq_par = (const int*)put(seq_par.data(), T.S * 4);
     dt.beta = (const double*)put(T.beta.data(), T.J * 8);
     dt.log_n = (const float*)put(th[p].log_n.data(), T.J * 4);
     DevTerms& tm = g.terms[p];

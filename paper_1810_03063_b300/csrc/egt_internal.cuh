@@ -19,6 +19,7 @@ struct DevTpx {
   const int* level_ptr;    // [L+1]
   const int* child_ptr;    // [S+1] CSR of D_j^i
   const int* child_idx;
+  const int* seq_par;      // [S] parent sequence of the sequence's simplex, -1 at a root simplex
   const double* beta;      // [J]
   const float* log_n;      // [J] log n_j
 };

@@ -159,7 +159,7 @@ __device__ __forceinline__ TpxTab pick(const Tabs& tb, int p) {
   t.level_ptr = p ? c.level_ptr : a.level_ptr;
   t.inf_first = p ? c.inf_first : a.inf_first;
   t.inf_n = p ? c.inf_n : a.inf_n;
-  t.inf_parent = p ? c.inf_parent : a.inf_parent;
+  t.seq_par = p ? c.seq_par : a.seq_par;
   t.child_ptr = p ? c.child_ptr : a.child_ptr;
   t.child_idx = p ? c.child_idx : a.child_idx;
   t.tptr = p ? c.tptr : a.tptr;

@@ -59,15 +59,15 @@ struct TpxTab {
   const int* level_ptr;    // [L+1]
   const int* inf_first;    // [J]
   const int* inf_n;        // [J]
-  const int* inf_parent;   // [J]
   const int* child_ptr;    // [S+1]
   const int* child_idx;    // [<= J]
+  const int* seq_par;      // [S] (DevTpx::seq_par)
 };
 
 __host__ __device__ inline size_t tpx_tab_bytes(const DevGame& g, int player) {
   const DevTpx& tp = g.tpx[player];
   return gradimpl::align16((size_t)tp.J * sizeof(double)) +
-         gradimpl::align16((size_t)(tp.L + 1 + 4 * tp.J + 2 * (tp.S + 1)) * sizeof(int));
+         gradimpl::align16((size_t)(tp.L + 1 + 3 * tp.J + 2 * (tp.S + 1) + tp.S) * sizeof(int));
 }
 
 // Copy player's tables into dst (all threads; the caller synchronises before use).
@@ -82,18 +82,18 @@ __device__ inline TpxTab stage_tpx_tab(const DevGame& g, int player, unsigned ch
   int* lp = ip;
   int* fi = lp + tp.L + 1;
   int* nn = fi + tp.J;
-  int* pa = nn + tp.J;
-  int* cp = pa + tp.J;
+  int* cp = nn + tp.J;
   int* ci = cp + tp.S + 1;
   const int nchild = tp.child_ptr[tp.S];
   int* tq = ci + nchild;
+  int* sp = tq + tp.S + 1;
   const int* tsrc = player ? g.terms[1].ptr : g.terms[0].ptr;
   for (int i = threadIdx.x; i <= tp.S; i += blockDim.x) tq[i] = tsrc[i];
+  for (int i = threadIdx.x; i < tp.S; i += blockDim.x) sp[i] = tp.seq_par[i];
   for (int i = threadIdx.x; i < tp.J; i += blockDim.x) {
     beta[i] = tp.beta[i];
     fi[i] = tp.inf_first[i];
     nn[i] = tp.inf_n[i];
-    pa[i] = tp.inf_parent[i];
   }
   for (int i = threadIdx.x; i <= tp.L; i += blockDim.x) lp[i] = tp.level_ptr[i];
   for (int i = threadIdx.x; i <= tp.S; i += blockDim.x) cp[i] = tp.child_ptr[i];
@@ -102,10 +102,10 @@ __device__ inline TpxTab stage_tpx_tab(const DevGame& g, int player, unsigned ch
   t.level_ptr = lp;
   t.inf_first = fi;
   t.inf_n = nn;
-  t.inf_parent = pa;
   t.child_ptr = cp;
   t.child_idx = ci;
   t.tptr = tq;
+  t.seq_par = sp;
   return t;
 }
 
@@ -250,22 +250,17 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
   }
 
   if (a.out != nullptr) {
+    // top-down: q(s) = q_bar(s) times q_bar of each ancestor sequence (the parent sequence
+    // of s's simplex, and so on up to a root simplex).  Once the bottom-up pass has
+    // normalised q_bar every (sequence, hand) is independent: no level barriers, and
+    // every warp takes rows
     const float tau = a.tau, omt = 1.f - a.tau;
-    for (int l = 0; l < tp.L; ++l) {
-      for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
-        const int p = tp.inf_parent[j];
-        const float qp = p < 0 ? 1.f : G[p * kH + hl];
-        const int s0 = tp.inf_first[j], n = tp.inf_n[j];
-        for (int i = bl; i < n; i += kSubLanes) {
-          const int s = s0 + i;
-          const float q = qp * G[s * kH + hl];
-          G[s * kH + hl] = q;
-          float o = q;
-          if (a.old != nullptr) o = omt * O[s * kH + hl] + tau * q;
-          a.out[(size_t)s * ld + h] = live ? o : 0.f;
-        }
-      }
-      group_sync(wg);
+    for (int s = kSubLanes * warp + bl; s < S; s += kWarps * kSubLanes) {
+      float q = G[s * kH + hl];
+      for (int p = tp.seq_par[s]; p >= 0; p = tp.seq_par[p]) q *= G[p * kH + hl];
+      float o = q;
+      if (a.old != nullptr) o = omt * O[s * kH + hl] + tau * q;
+      a.out[(size_t)s * ld + h] = live ? o : 0.f;
     }
   }
   group_sync(wg);   // shared memory is reused by the caller's next item
