@@ -9,7 +9,8 @@
 // m - t log(sum_i exp(-(g_hat_i - m) / t)) + t log n_j with m = min g_hat.
 // The value is evaluated as m - t log1p(sum_i expm1(-(g_hat_i - m)/t) / n_j),
 // the same quantity without the cancellation of the two logarithms in FP32.
-// Top-down: q_i = q_{p_j} q_bar_i.
+// Top-down: q_i = q_{p_j} q_bar_i, i.e. q_bar_i times the q_bar of every ancestor
+// sequence, which needs no ordering between simplexes once all q_bar are known.
 //
 // Sec. 6: the per-hand treeplexes form a Cartesian product at the root, so
 // hands are independent.  One item = 16 hands; a warp holds each hand twice
@@ -19,7 +20,8 @@
 // [S][16] tile of g (and of the previous iterate the output is mixed with) is
 // fetched into shared memory before the recursion (two 64-byte row pieces per
 // warp load), which then runs on shared memory: the warps split the simplexes
-// of a level, levels are separated by __syncthreads.
+// of a level, levels are separated by CTA barriers; the top-down products then
+// run on all warps at once, one (sequence, hand) per lane.
 #pragma once
 #include <math.h>
 
