@@ -175,14 +175,14 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
   // per-hand record of flat shared-memory indices used by the product kernels
   std::vector<uint4> hinfo(ld);
   {
-    const unsigned ls = (unsigned)G->lmax + 1;
+    auto at = [&](unsigned slot, unsigned k) { return (unsigned)pc_index((int)slot, (int)k, G->lmax); };
     for (int s = 0; s < ld; ++s) {
       const unsigned a = hcard[s].x, b = hcard[s].y;
       const unsigned la = (unsigned)lists[a].size(), lb = (unsigned)lists[b].size();
       hinfo[s] = make_uint4(grp[s].x | ((unsigned)grp[s].y << 16),
-                            (a * ls + cpos[s].x) | ((a * ls + cpos[s].y) << 16),
-                            (a * ls + la) | ((b * ls + cpos[s].z) << 16),
-                            (b * ls + cpos[s].w) | ((b * ls + lb) << 16));
+                            at(a, cpos[s].x) | (at(a, cpos[s].y) << 16),
+                            at(a, la) | (at(b, cpos[s].z) << 16),
+                            at(b, cpos[s].w) | (at(b, lb) << 16));
     }
   }
   std::vector<int> card_len(G->n_slots);

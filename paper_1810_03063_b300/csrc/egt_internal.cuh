@@ -10,6 +10,14 @@ namespace egt {
 constexpr int kSbrHands = 16;       // hands per SBR / best-response item (two lanes each)
 constexpr int kMaxListLen = 64;     // max hands holding one card (four per lane in a half-warp scan)
 
+// Per-card prefix arrays of a product item in shared memory: card slot c's prefix
+// before its k-th hand (k = 0 .. list length) sits at pc_index(c, k, lmax).  One
+// 16-byte entry of padding after every four keeps the card scan's stores (four
+// consecutive entries per lane) free of bank conflicts.
+__host__ __device__ inline int pc_pad(int k) { return k + (k >> 2); }
+__host__ __device__ inline int pc_stride(int lmax) { return pc_pad(lmax) + 1; }
+__host__ __device__ inline int pc_index(int c, int k, int lmax) { return c * pc_stride(lmax) + pc_pad(k); }
+
 // One player's per-hand treeplex on the device (Sec. 4 notation).
 struct DevTpx {
   int S, J, L;
@@ -43,8 +51,8 @@ struct DevGame {
   const ushort2* grp;      // [ld] tie group [lo, hi) in sorted order
   const uchar4* cpos;      // [ld] hands of card k before lo / hi: (lo0, hi0, lo1, hi1)
   // [ld] per hand, eight uint16: tie group lo, hi; then for each of its two card slots the
-  // flat index (slot * (lmax + 1) + position) of the per-card prefix before lo, before hi,
-  // and of the card's total
+  // flat index (pc_index) of the per-card prefix before lo, before hi, and of the card's
+  // total
   const uint4* hinfo;
   const uint16_t* card_hands;  // [n_slots][lmax] sorted hand indices holding the card
   const int* card_len;     // [n_slots]

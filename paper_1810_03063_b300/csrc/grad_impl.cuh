@@ -363,7 +363,7 @@ __host__ __device__ inline size_t grad_item_smem(const DevGame& g) {
   const size_t fx = sizeof(gradimpl::Fx);
   size_t b = align16((size_t)g.ld * fx);
   b += align16((size_t)(g.ld + 1) * fx);
-  b += align16((size_t)g.n_slots * (g.lmax + 1) * fx);
+  b += align16((size_t)g.n_slots * pc_stride(g.lmax) * fx);
   b += 16 * sizeof(int) + 16 * fx + 16;
   return align16(b);
 }
@@ -426,7 +426,7 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
   constexpr int kWarps = kThreads / 32;
   const int ld = g.ld, H = g.H, opp = 1 - player;
   const int tid = threadIdx.x - first_warp * 32, lane = threadIdx.x & 31, warp = tid >> 5;
-  const int lstride = g.lmax + 1;
+  const int lstride = pc_stride(g.lmax);
 
   Fx* F = reinterpret_cast<Fx*>(smem);
   Fx* P = F + ld;                                                          // [ld + 1]
@@ -512,7 +512,7 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
       if (ok && sl == 0) pc[0] = fx_zero();
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (ok && i0 + j < len) pc[i0 + j + 1] = fx_add(before, a[j]);
+        if (ok && i0 + j < len) pc[pc_pad(i0 + j + 1)] = fx_add(before, a[j]);
     }
   }
   item_sync<kThreads>(bar);
