@@ -201,3 +201,30 @@ def test_autotuned_shapes_leave_results_bitwise_unchanged(egtlib):
     b.shape = dict(share=0, pairs=0, grid_pct=50)
     assert b.shape == dict(share=0, pairs=0, grid_pct=50)
     b.close()
+
+
+def test_tuning_with_members_finishing_midway(egtlib):
+    """Members that reach their budget during tuning drop out of the later trials (which then
+    time fewer member-iterations) and still end exactly where their solo solves end."""
+    specs = [synth.tiny(), synth.full_deck(seed=synth.BASE_SEED + 3)]
+    budgets = [5, 50]
+    b = egtlib.Batch(0)
+    games, slots = [], []
+    for sp, n in zip(specs, budgets):
+        g = egtlib.Game(sp, device=0)
+        g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+        slots.append(b.add(g, variant=egtlib.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1))
+        games.append(g)
+    rep = b.tune(n_iters=3, reps=1)
+    its = [c["iters"] for c in rep["candidates"]]
+    assert its[:3] == [6, 5, 3] and all(i == 3 for i in its[3:])   # 13 trials x 3 = 39 < 50
+    assert not b.member(slots[0])["active"] and b.member(slots[1])["active"]
+    b.run(n_iters=7)
+    for sp, n, g, s in zip(specs, budgets, games, slots):
+        xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, n, 1)
+        xb, yb, mu = member_state(egtlib, g)
+        m = b.member(s)
+        assert m["iters"] == rs["iters"] == n
+        assert torch.equal(xb, xs) and torch.equal(yb, ys), sp.name
+        assert mu == rs["mu"] and m["tau"] == rs["tau"] and m["gap_mbb"] == rs["gap_mbb"]
+    b.close()
