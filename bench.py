@@ -69,6 +69,9 @@ def parse():
                     help="instead of the iteration benchmark: the batched mix solved to 1 mbb/hand per game, "
                          "one egt_batch_step launch per --batch-solve-iters iterations, against egt_solve per game")
     ap.add_argument("--batch-solve-iters", type=int, default=200)
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the iteration benchmark: iter/s and time to 1 mbb/hand of the tiny, "
+                         "full-deck, large and Libratus-menu endgames, one game at a time")
     ap.add_argument("--phases", action="store_true",
                     help="instead of the iteration benchmark: device time per engine phase (egt_engine_trace) "
                          "over 300 EGT/as iterations of the full-deck, large and Libratus-menu games")
@@ -596,6 +599,49 @@ def run_batch_solve(args, local):
             "data": "synthetic"}
 
 
+def run_configs(args, local):
+    """Each synthetic endgame alone: EGT/as iterations per second in launches of 100 iterations
+    (FP64 residual every iteration, L2 flushed before each launch, CUDA events; 10 launches
+    after 3 warm-up), and the time of an egt_solve to 1 mbb/hand from egt_solver_init."""
+    import time
+
+    import torch
+
+    from paper_1810_03063_b300 import egt, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = []
+    for name, spec in [("tiny (20 cards, 105 hands)", synth.tiny()), ("full deck (52 cards, 1081 hands)", synth.full_deck()),
+                       ("large (bets {0.25,0.5,1,2}, cap 4)", synth.large()),
+                       ("Libratus menus (stack 9 pots)", synth.libratus())]:
+        g = egt.Game(spec, device=local)
+        g.solver_init(variant=egt.EGT_AS, alpha=0.01)
+        for _ in range(3):
+            g.iterate(100, variant=egt.EGT_AS, gap_every=1)
+        ms = 0.0
+        for i in range(10):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.iterate(100, variant=egt.EGT_AS, gap_every=1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        t0 = time.perf_counter()
+        rep = g.solve(variant=egt.EGT_AS, alpha=0.01, eps_mbb=1.0, max_iters=20000, gap_every=1)
+        sec = time.perf_counter() - t0
+        out.append({"game": name, "S": list(g.S), "T": g.T, "hands": g.H,
+                    "iter_per_s": round(1000.0 / (ms / 10.0) * 100, 1), "us_per_iter": round(ms * 1e3 / 1000.0, 2),
+                    "time_to_1mbb_s": round(sec, 4), "iters_to_1mbb": rep["iters"], "gap_mbb": round(rep["gap_mbb"], 4),
+                    "status": rep["status"], "backoffs": rep["backoffs"]})
+        g.close()
+    return {"study": "per-config EGT/as throughput and time to 1 mbb/hand, one game on one GPU", "data": "synthetic",
+            "games": out}
+
+
 def run_phases(args, local):
     """Per-phase device time of the EGT/as driver, read from the engine's own %globaltimer trace
     (CTA 0): each phase's average and the part before CTA 0 reached the group barrier."""
@@ -706,6 +752,11 @@ def main():
         return
     if args.batch_solve:
         out = run_batch_solve(args, local)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    if args.configs:
+        out = run_configs(args, local)
         if rank == 0:
             print(json.dumps(out))
         return
