@@ -764,6 +764,17 @@ egt_status engine_status(const EngineCtl& c) {
   return EGT_OK;
 }
 
+// Items the one-game launch runs two at a time on its CTAs' warp halves: the product
+// (terminal) items, when a phase has at least two terminals per CTA and shared memory
+// allows two items side by side (results are the same either way: exact sums).
+int engine_pair_bits(const egt_game* G, int grid) {
+  const int limit = engine_smem_limit(false);
+  if (limit <= 0 || 2 * grid > (int)G->comp.term.size()) return 0;
+  const size_t smem = engine_smem_bytes(G->dg, kPairTerms);
+  if (smem > (size_t)limit || engine_max_grid(smem, false) < grid) return 0;
+  return kPairTerms;
+}
+
 // Run up to n iterations of `variant` from the solver state on the device (one
 // cooperative launch), as the host loop of egt_solve would: Step (with the
 // EGT/as back-off), then the residual every gap_every iterations and at the end.
@@ -777,6 +788,7 @@ egt_status engine_run(egt_game* G, int variant, double eps_mbb, int gap_every, i
   job.g = G->dg;
   job.b = engine_bufs(G, log_dev, log_cap);
   job.ctl = G->ctl_dev;
+  job.pair = engine_pair_bits(G, grid);
   // fault-injection hooks for tests: phantom arrivals make every group barrier wait run
   // out after the time limit instead of completing
   const unsigned extra = (unsigned)std::max(0, env_int("EGT_TEST_BARRIER_EXTRA", 0));
@@ -785,7 +797,7 @@ egt_status engine_run(egt_game* G, int variant, double eps_mbb, int gap_every, i
   CUDA_TRY(cudaMemcpyAsync(G->ctl_dev, &c, sizeof(c), cudaMemcpyHostToDevice, st));
   cudaError_t le = cudaSuccess;
   EGT_TRY(timed(G, EGT_KERNEL_ENGINE, st, "engine kernel", [&] {
-    le = engine_launch_one(job, grid, engine_smem_bytes(G->dg), extra, limit_ns, st);
+    le = engine_launch_one(job, grid, engine_smem_bytes(G->dg, job.pair), extra, limit_ns, st);
   }));
   if (le != cudaSuccess) return fail(EGT_ERR_CUDA, std::string("engine launch: ") + cudaGetErrorString(le));
   CUDA_TRY(cudaMemcpyAsync(&c, G->ctl_dev, sizeof(c), cudaMemcpyDeviceToHost, st));
