@@ -168,3 +168,25 @@ def test_iteration_log_has_times_and_writes_jsonl(egtlib, tmp_path, engine):
     assert all(r["egv"] is not None and r["egv"] >= 0 for r in recs)     # EGT/as accepts EGV >= 0 only
     # the residual of the iterates each iteration started from (gap_every = 1)
     assert all(r["gap_mbb"] is not None and r["gap_mbb"] > 0 for r in recs)
+
+
+def test_whole_solves_are_deterministic(egtlib):
+    """Two solves of the same game in separate game objects, one on a side stream, end with the
+    same bits (iterates, mu, tau, residual, iteration and back-off counts)."""
+    spec = synth.libratus(n_cards=52)
+    runs = []
+    for k in range(2):
+        g = egtlib.Game(spec, device=0)
+        x = torch.empty((g.S[0], g.ld), device="cuda")
+        y = torch.empty((g.S[1], g.ld), device="cuda")
+        s = torch.cuda.Stream() if k else torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            rep = g.solve(x, y, variant=2, alpha=0.01, eps_mbb=0.0, max_iters=400, gap_every=1,
+                          stream=s.cuda_stream)
+        torch.cuda.synchronize()
+        runs.append((x, y, rep))
+        g.close()
+    (x0, y0, r0), (x1, y1, r1) = runs
+    assert torch.equal(x0, x1) and torch.equal(y0, y1)
+    for key in ("iters", "backoffs", "mu", "tau", "gap_mbb", "products"):
+        assert r0[key] == r1[key], key
