@@ -228,3 +228,28 @@ def test_tuning_with_members_finishing_midway(egtlib):
         assert torch.equal(xb, xs) and torch.equal(yb, ys), sp.name
         assert mu == rs["mu"] and m["tau"] == rs["tau"] and m["gap_mbb"] == rs["gap_mbb"]
     b.close()
+
+
+def test_launch_shape_fields_take_effect(egtlib):
+    """grid_pct bounds the grid, share 0 gives equal groups, pairs = 0 keeps results unchanged."""
+    specs = [synth.tiny(seed=synth.BASE_SEED + k) for k in range(4)]
+    b = egtlib.Batch(0)
+    games = []
+    for sp in specs:
+        g = egtlib.Game(sp, device=0)
+        g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+        b.add(g, variant=egtlib.EGT_AS, eps_mbb=0.0, max_iters=30, gap_every=1)
+        games.append(g)
+    b.step(5)
+    half = torch.cuda.get_device_properties(0).multi_processor_count // 2   # one CTA per SM
+    b.shape = dict(share=0, pairs=0, grid_pct=50)
+    b.step(5)
+    group, grid = b.launch_shape()
+    assert len(specs) <= grid <= half and group <= -(-half // len(specs))   # equal shares of half
+    b.shape = dict(share=4, pairs=1, grid_pct=100)
+    b.run(n_iters=7)
+    for sp, g in zip(specs, games):
+        xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, 30, 1)
+        xb, yb, mu = member_state(egtlib, g)
+        assert torch.equal(xb, xs) and torch.equal(yb, ys)
+    b.close()
