@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--configs", action="store_true",
                     help="instead of the iteration benchmark: iter/s and time to 1 mbb/hand of the tiny, "
                          "full-deck, large and Libratus-menu endgames, one game at a time")
+    ap.add_argument("--ops", action="store_true",
+                    help="instead of the iteration benchmark: the C-ABI hot-path operations one call at a time "
+                         "(egt_grad, egt_grad_f64, egt_smoothed_br, egt_best_response_f64, egt_gap)")
     ap.add_argument("--phases", action="store_true",
                     help="instead of the iteration benchmark: device time per engine phase (egt_engine_trace) "
                          "over 300 EGT/as iterations of the full-deck, large and Libratus-menu games")
@@ -599,6 +602,62 @@ def run_batch_solve(args, local):
             "data": "synthetic"}
 
 
+def run_ops(args, local):
+    """The public hot-path operations one call at a time on the full-deck and large games:
+    device time per call (CUDA events on the calling stream, L2 flushed before each call,
+    20 calls after 3 warm-up) and algorithmic GB/s (algorithmic_bytes: each input read and
+    each output written once)."""
+    import numpy as np
+    import torch
+
+    from paper_1810_03063_b300 import egt, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = []
+    for name, spec in [("full deck", synth.full_deck()), ("large", synth.large())]:
+        g = egt.Game(spec, device=local)
+        ab = algorithmic_bytes(g)
+        rng = np.random.default_rng(5)
+        y = torch.tensor(rng.random((g.S[1], g.ld)), dtype=torch.float32, device=dev)
+        x = torch.tensor(rng.random((g.S[0], g.ld)), dtype=torch.float32, device=dev)
+        y64 = y.double()
+        gx = torch.empty((g.S[0], g.ld), dtype=torch.float32, device=dev)
+        gx64 = torch.empty((g.S[0], g.ld), dtype=torch.float64, device=dev)
+        q = torch.empty_like(gx)
+        g.grad(0, y, gx)
+        g.grad_f64(0, y64, gx64)
+        mu = 0.01 * g.normA
+        ops = {"egt_grad (FP32, A y)": (lambda: g.grad(0, y, gx), ab["grad_f32"]),
+               "egt_grad_f64 (A y)": (lambda: g.grad_f64(0, y64, gx64), ab["grad_f64"]),
+               "egt_smoothed_br (player 0, q and value)": (lambda: g.smoothed_br(0, gx, mu, q), ab["sbr"] * 2 / 3),
+               "egt_best_response_f64 (player 0)": (lambda: g.best_response_f64(0, gx64), ab["br_f64"]),
+               "egt_gap (two FP64 products and best responses)": (lambda: g.gap(x, y),
+                                                                  2 * ab["grad_f64"] + 2 * ab["br_f64"])}
+        res = {}
+        for op, (fn, nbytes) in ops.items():
+            for _ in range(3):
+                fn()
+            ms = []
+            for i in range(20):
+                flush.fill_(float(i))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            us = 1e3 * float(np.median(ms))
+            res[op] = {"us": round(us, 2), "alg_bytes": int(nbytes), "gbs": round(nbytes / (us * 1e-6) / 1e9, 1)}
+        out.append({"game": name, "S": list(g.S), "T": g.T, "ops": res})
+        g.close()
+    return {"study": "C-ABI hot-path operations, one call at a time (median of 20, L2 flushed)",
+            "note": "calls that return a host value (smoothed_br value, best response, gap) include the readback",
+            "data": "synthetic", "games": out}
+
+
 def run_configs(args, local):
     """Each synthetic endgame alone: EGT/as iterations per second in launches of 100 iterations
     (FP64 residual every iteration, L2 flushed before each launch, CUDA events; 10 launches
@@ -752,6 +811,11 @@ def main():
         return
     if args.batch_solve:
         out = run_batch_solve(args, local)
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    if args.ops:
+        out = run_ops(args, local)
         if rank == 0:
             print(json.dumps(out))
         return
