@@ -29,6 +29,7 @@
 #pragma once
 #include <climits>
 #include <cstring>
+#include <type_traits>
 
 #include "egt_internal.cuh"
 
@@ -46,6 +47,13 @@ __host__ __device__ __forceinline__ int clz64(unsigned long long x) {
   return __clzll((long long)x);
 #else
   return x ? __builtin_clzll(x) : 64;
+#endif
+}
+__host__ __device__ __forceinline__ int clz32(unsigned x) {
+#ifdef __CUDA_ARCH__
+  return __clz((int)x);
+#else
+  return x ? __builtin_clz(x) : 32;
 #endif
 }
 __host__ __device__ __forceinline__ unsigned long long umul64hi(unsigned long long a, unsigned long long b) {
@@ -192,6 +200,22 @@ __host__ __device__ __forceinline__ WBits wprod(double r, double y) {
   x.E = e - 1075;
   x.lg = x.E + (64 - clz64(m)) - 1;
   return x;
+}
+
+// An upper bound on floor(log2 |r y|) for FP32 y from the two exponents alone (the
+// significand product is below 4, so the bound is the true value or one more);
+// INT_MIN when r y = 0.  Enough to choose a column's fixed-point scale (scale_of)
+// without forming the products twice.
+__host__ __device__ __forceinline__ int lg_bound(double r, float y) {
+  const unsigned long long rb = f64_bits(r);
+  const unsigned yb = f32_bits(y);
+  const int er = (int)((rb >> 52) & 0x7ffull), ey = (int)((yb >> 23) & 0xffu);
+  const unsigned long long mr = rb & ((1ull << 52) - 1);
+  const unsigned my = yb & 0x7fffffu;
+  if ((er == 0 && mr == 0) || (ey == 0 && my == 0)) return INT_MIN;
+  const int lr = er ? er - 1023 : (63 - clz64(mr)) - 1074;   // floor(log2 |r|), subnormals too
+  const int ly = ey ? ey - 127 : (31 - clz32(my)) - 149;
+  return lr + ly + 1;
 }
 
 // |w| 2^ex as integer part + 40 truncated fraction bits, signed
@@ -444,7 +468,8 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
   const double coef64 = tm.coef64[e];
   const TIn* col = in + (size_t)os * ld;
 
-  // pass 1: all of this thread's inputs loaded at once, largest exponent of |w| (w exact)
+  // pass 1: all of this thread's inputs loaded at once, the column's largest exponent of
+  // |w| (for FP32 inputs an upper bound from the exponents, at most one too large)
   TIn y[kMaxHandsPerThread];
 #pragma unroll
   for (int k = 0; k < kMaxHandsPerThread; ++k) {
@@ -455,7 +480,10 @@ __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player
 #pragma unroll
   for (int k = 0; k < kMaxHandsPerThread; ++k) {
     const int h = tid + k * kThreads;
-    if (h < ld) mlg = max(mlg, wprod(r_opp[h], y[k]).lg);
+    if (h < ld) {
+      if constexpr (std::is_same<TIn, float>::value) mlg = max(mlg, lg_bound(r_opp[h], y[k]));
+      else mlg = max(mlg, wprod(r_opp[h], y[k]).lg);   // (FP64 y: rounded product, exact lg)
+    }
   }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) mlg = max(mlg, __shfl_xor_sync(0xffffffffu, mlg, d));

@@ -5,6 +5,7 @@
 //   W <double bits> <double bits>  -> hi lo E lg neg         (w = r y, FP64 y)
 //   x <double bits> <float bits> <ex> -> v0 v1               (to_fx of r y at scale ex)
 //   c <v0> <v1> <ex>               -> <FP64 bits> <FP32 bits> (fx_to_f32_f64)
+//   l <double bits> <float bits>   -> lg_bound
 #include <cstdio>
 
 #include "grad_impl.cuh"
@@ -27,6 +28,10 @@ int main() {
       } else {
         std::printf("%llu %llu %d %d %d\n", w.hi, w.lo, w.E, w.lg, w.neg);
       }
+    } else if (op == 'l') {
+      unsigned long long rb, yb;
+      if (std::scanf("%llu %llu", &rb, &yb) != 2) return 2;
+      std::printf("%d\n", lg_bound(bits_f64(rb), bits_f32((unsigned)yb)));
     } else if (op == 'c') {
       long long v0, v1;
       int ex;

@@ -135,6 +135,26 @@ def test_w_is_the_exact_product(host):
             assert Fraction(2) ** int(lg) <= abs(exact) < Fraction(2) ** (int(lg) + 1)
 
 
+def test_scale_bound_is_the_binade_or_one_more(host):
+    """The column scale of FP32 inputs comes from lg_bound: floor(log2 |r y|) or that plus
+    one (never less, or the fixed point could overflow), INT_MIN for a zero product."""
+    rng = random.Random(3)
+    cases = [(random_double(rng), random_float(rng)) for _ in range(4000)]
+    cases += [(1.0, 1.0), (1.9999999999999998, 1.9999999), (2.0 ** -1074, 2.0 ** -149), (0.0, 1.0), (1.0, 0.0)]
+    res = host([f"l {d_bits(r)} {f_bits(y)}" for r, y in cases])
+    for (r, y), (lg,) in zip(cases, res):
+        w = abs(Fraction(r) * Fraction(y))
+        if w == 0:
+            assert int(lg) == INT_MIN
+            continue
+        e = w.numerator.bit_length() - w.denominator.bit_length()
+        while Fraction(2) ** e > w:
+            e -= 1
+        while Fraction(2) ** (e + 1) <= w:
+            e += 1
+        assert int(lg) in (e, e + 1), (r, y, lg, e)
+
+
 def test_w_with_fp64_y_is_the_rounded_product(host):
     rng = random.Random(7)
     cases = [(random_double(rng), random_double(rng)) for _ in range(2000)]
