@@ -391,12 +391,22 @@ EGT_API egt_status egt_batch_launch_shape(const egt_batch* batch, int32_t* group
  *             a time, one per warp half, where shared memory allows and its group
  *             has two items per CTA; 0: one item at a time.
  *   grid_pct: percent of the co-resident CTAs launched, 1-100 (default 100).
+ *   pack:     1: a makespan-balanced plan instead of share: members heavier than
+ *             the balanced makespan get CTAs of their own in proportion to their
+ *             work, the lighter ones share one-CTA groups that run them in turn
+ *             (for batches with many small members); 0 (default): share.
+ *   wave_mb:  > 0: the active members run in k = ceil(their device bytes
+ *             (egt_dims.device_bytes) / wave_mb MB) consecutive waves of about
+ *             equal bytes, one launch each, so that a wave's state can stay in
+ *             L2 (default 128, about the B300's 126 MB L2); 0: all in one launch.
  * No choice changes any member's results (they come from exact products and
  * fixed-order sums); only the speed differs. */
 typedef struct {
   int32_t share;
   int32_t pairs;
   int32_t grid_pct;
+  int32_t pack;
+  int32_t wave_mb;
 } egt_launch_shape;
 
 /* Set / read the batch's launch shape (host structs).  Set returns
@@ -415,8 +425,9 @@ typedef struct {
 } egt_tune_report;
 
 /* Autotune the launch shape on the batch's own work: every candidate (share
- * 4 / 3 / 2 / 1 / 0 x pairs 1 / 0 on all CTAs, and share 4 / 3 / 2 with pairs
- * on 75 % of them: 13 shapes) runs `reps` (>= 1) egt_batch_step
+ * 4 / 3 / 2 / 1 / 0 with pairs, share 4 / 3 / 2 without, share 3 on 75 % of
+ * the CTAs, the packed plan, and share 3 in waves of 64 / 96 / 128 MB: 13
+ * shapes) runs `reps` (>= 1) egt_batch_step
  * launches of n_iters iterations, each timed with CUDA events on `stream`, and
  * the shape with the least time per member-iteration becomes the batch's.  The
  * trials are real steps: members advance exactly as egt_batch_step advances

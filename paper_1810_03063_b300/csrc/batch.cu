@@ -32,14 +32,15 @@ struct egt_batch {
   EngineGroup* plan_host = nullptr;
   int cap = 0;
   int last_group = 0, last_grid = 0;
-  egt_launch_shape shape{3, 1, 100};
+  egt_launch_shape shape{3, 1, 100, 0, 128};
   cudaEvent_t ev[2] = {nullptr, nullptr};   // timing of tuning trials (created on first use)
 };
 
 namespace {
 
 bool shape_ok(const egt_launch_shape& x) {
-  return x.share >= 0 && x.share <= 4 && (x.pairs == 0 || x.pairs == 1) && x.grid_pct >= 1 && x.grid_pct <= 100;
+  return x.share >= 0 && x.share <= 4 && (x.pairs == 0 || x.pairs == 1) && x.grid_pct >= 1 && x.grid_pct <= 100 &&
+         (x.pack == 0 || x.pack == 1) && x.wave_mb >= 0;
 }
 
 void batch_free_arrays(egt_batch* B) {
@@ -147,6 +148,87 @@ int plan_groups(const std::vector<double>& w, const std::vector<int>& cap, int m
   return n;
 }
 
+// Makespan-balanced plan over maxg CTAs (launch shape pack = 1): with a member's
+// time modelled as its work over its CTAs, find (bisection) the least makespan M
+// for which every member heavier than M gets ceil(w / M) CTAs of its own (at most
+// its widest phase) and the lighter ones, packed first-fit by decreasing work,
+// share one-CTA groups that run them in turn, all within maxg CTAs; CTAs left
+// over go to the heavy members with the most work per CTA.  Same outputs as
+// plan_groups.
+int plan_groups_packed(const std::vector<double>& w, const std::vector<int>& cap, int maxg,
+                       std::vector<EngineGroup>& plan, std::vector<int>& order, int* grid) {
+  const int n = (int)w.size();
+  std::vector<int> by_w(n);
+  std::iota(by_w.begin(), by_w.end(), 0);
+  std::stable_sort(by_w.begin(), by_w.end(), [&](int a, int b) { return w[a] > w[b]; });
+  std::vector<int> c;
+  std::vector<std::vector<int>> bins;
+  auto fit = [&](double M) {   // CTAs the plan for makespan M needs (maxg + 1: infeasible)
+    c.assign(n, 0);
+    bins.clear();
+    std::vector<double> load;
+    int total = 0;
+    for (int j : by_w) {
+      if (w[j] > M) {
+        c[j] = (int)std::ceil(w[j] / M);
+        if (c[j] > cap[j]) return maxg + 1;
+        total += c[j];
+      } else {
+        size_t b = 0;
+        while (b < load.size() && load[b] + w[j] > M) ++b;
+        if (b == load.size()) {
+          load.push_back(0.0);
+          bins.emplace_back();
+        }
+        load[b] += w[j];
+        bins[b].push_back(j);
+      }
+      if (total + (int)bins.size() > maxg) return maxg + 1;
+    }
+    return total + (int)bins.size();
+  };
+  double lo = 0.0, hi = 0.0;
+  for (int j = 0; j < n; ++j) {
+    lo = std::max(lo, w[j] / std::max(1, cap[j]));
+    hi += w[j];
+  }
+  hi = std::max(hi, lo);
+  for (int it = 0; it < 60 && hi - lo > 1e-9 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    (fit(mid) <= maxg ? hi : lo) = mid;
+  }
+  fit(hi);
+  int used = 0;
+  for (int j = 0; j < n; ++j) used += c[j];
+  used += (int)bins.size();
+  while (used < maxg) {   // leftovers to the heavy member with the most work per CTA that can use one
+    int best = -1;
+    for (int j = 0; j < n; ++j)
+      if (c[j] > 0 && c[j] < cap[j] && (best < 0 || w[j] / c[j] > w[best] / c[best])) best = j;
+    if (best < 0) break;
+    ++c[best];
+    ++used;
+  }
+  plan.clear();
+  order.clear();
+  int first = 0;
+  for (int j : by_w)
+    if (c[j] > 0) {
+      plan.push_back(EngineGroup{first, c[j], (int)order.size(), (int)order.size() + 1});
+      order.push_back(j);
+      first += c[j];
+    }
+  for (const auto& b : bins) {
+    EngineGroup e{first, 1, (int)order.size(), 0};
+    for (int j : b) order.push_back(j);
+    e.job1 = (int)order.size();
+    plan.push_back(e);
+    first += 1;
+  }
+  *grid = first;
+  return (int)plan.size();
+}
+
 egt_status check_slot(const egt_batch* B, int32_t slot) {
   if (!B) return fail(EGT_ERR_INVALID_ARG, "batch is NULL");
   if (slot < 0 || slot >= (int)B->members.size() || !B->members[slot].G)
@@ -157,22 +239,17 @@ egt_status check_slot(const egt_batch* B, int32_t slot) {
 // One batch launch under launch shape `sh` (group > 0 overrides its split); with
 // ms != NULL the engine launch is timed with CUDA events and *done gets the
 // member-iterations it ran.
-egt_status batch_launch(egt_batch* B, int32_t n_iters, int32_t group, const egt_launch_shape& sh,
-                        int32_t* n_active, cudaStream_t st, float* ms, long long* done) {
-  if (n_iters <= 0) return fail(EGT_ERR_INVALID_ARG, "n_iters must be > 0");
-  if (group < 0) return fail(EGT_ERR_INVALID_ARG, "group must be >= 0");
-  DeviceGuard guard(B->device);
+egt_status launch_members(egt_batch* B, const std::vector<int>& act, int32_t n_iters, int32_t group,
+                          const egt_launch_shape& sh, int32_t* n_active, cudaStream_t st, float* ms,
+                          long long* done) {
   if (done) *done = 0;
   if (ms) *ms = 0.f;
-  std::vector<int> act;
-  for (int k = 0; k < (int)B->members.size(); ++k)
-    if (B->members[k].G && B->members[k].active) act.push_back(k);
   const int n = (int)act.size();
   if (n_active) *n_active = n;
   if (n == 0) return EGT_OK;
   EGT_TRY(batch_reserve(B, n));
   size_t smem = 0;
-  std::vector<double> w(n);
+  std::vector<double> w(n), wraw(n);
   std::vector<int> cap(n), pair(n);
   const int limit = engine_smem_limit(true);
   for (int i = 0; i < n; ++i) {
@@ -184,6 +261,7 @@ egt_status batch_launch(egt_batch* B, int32_t n_iters, int32_t group, const egt_
         if (limit > 0 && engine_smem_bytes(G->dg, pair[i] | bit) <= (size_t)limit) pair[i] |= bit;
     smem = std::max(smem, engine_smem_bytes(G->dg, pair[i]));
     const double work = iteration_work(G);
+    wraw[i] = work;
     w[i] = sh.share == 4 ? work : std::pow(work, 0.25 * sh.share);
     cap[i] = engine_items(G->dg);
   }
@@ -193,7 +271,8 @@ egt_status batch_launch(egt_batch* B, int32_t n_iters, int32_t group, const egt_
   std::vector<EngineGroup> plan;
   std::vector<int> order;
   int grid = 0;
-  const int n_groups = plan_groups(w, cap, maxg, group, plan, order, &grid);
+  const int n_groups = group == 0 && sh.pack ? plan_groups_packed(wraw, cap, maxg, plan, order, &grid)
+                                             : plan_groups(w, cap, maxg, group, plan, order, &grid);
   int widest = 0;
   for (const auto& e : plan) widest = std::max(widest, e.size);
   B->last_group = widest;
@@ -256,6 +335,47 @@ egt_status batch_launch(egt_batch* B, int32_t n_iters, int32_t group, const egt_
       m.status = m.eps_mbb > 0 ? EGT_ERR_NOT_CONVERGED : EGT_OK;
     }
     still += m.active;
+  }
+  if (n_active) *n_active = still;
+  return EGT_OK;
+}
+
+// One batch step under launch shape `sh`: the active members in one launch, or
+// (sh.wave_mb > 0) in k = ceil(total device bytes / wave_mb MB) consecutive waves of
+// about equal bytes, one launch each, so that a wave's state can stay in L2.  ms /
+// done add up over the waves.
+egt_status batch_launch(egt_batch* B, int32_t n_iters, int32_t group, const egt_launch_shape& sh,
+                        int32_t* n_active, cudaStream_t st, float* ms, long long* done) {
+  if (n_iters <= 0) return fail(EGT_ERR_INVALID_ARG, "n_iters must be > 0");
+  if (group < 0) return fail(EGT_ERR_INVALID_ARG, "group must be >= 0");
+  DeviceGuard guard(B->device);
+  std::vector<int> act;
+  for (int k = 0; k < (int)B->members.size(); ++k)
+    if (B->members[k].G && B->members[k].active) act.push_back(k);
+  if (sh.wave_mb <= 0) return launch_members(B, act, n_iters, group, sh, n_active, st, ms, done);
+  const double budget = (double)((size_t)sh.wave_mb << 20);
+  double total = 0.0;
+  for (int k : act) total += (double)B->members[k].G->device_bytes;
+  const int waves = std::max(1, (int)std::ceil(total / budget));
+  const double target = total / waves;
+  if (done) *done = 0;
+  if (ms) *ms = 0.f;
+  int still = 0;
+  double before = 0.0;   // bytes of the members in earlier waves
+  for (size_t i = 0; i < act.size();) {
+    std::vector<int> wave;
+    const int q = std::min(waves - 1, (int)(before / target));
+    while (i < act.size() && (wave.empty() || std::min(waves - 1, (int)(before / target)) == q)) {
+      before += (double)B->members[act[i]].G->device_bytes;
+      wave.push_back(act[i++]);
+    }
+    float w_ms = 0.f;
+    long long w_done = 0;
+    int32_t w_active = 0;
+    EGT_TRY(launch_members(B, wave, n_iters, group, sh, &w_active, st, ms ? &w_ms : nullptr, &w_done));
+    if (ms) *ms += w_ms;
+    if (done) *done += w_done;
+    still += w_active;
   }
   if (n_active) *n_active = still;
   return EGT_OK;
@@ -347,9 +467,12 @@ egt_status egt_batch_tune(egt_batch* B, int32_t n_iters, int32_t reps, egt_tune_
   egt_tune_report r;
   std::memset(&r, 0, sizeof(r));
   r.best = -1;
-  for (int pairs : {1, 0})
-    for (int share : {4, 3, 2, 1, 0}) r.shape[r.n++] = egt_launch_shape{share, pairs, 100};
-  for (int share : {4, 3, 2}) r.shape[r.n++] = egt_launch_shape{share, 1, 75};
+  for (int share : {4, 3, 2, 1, 0}) r.shape[r.n++] = egt_launch_shape{share, 1, 100, 0, 0};
+  for (int share : {4, 3, 2}) r.shape[r.n++] = egt_launch_shape{share, 0, 100, 0, 0};
+  r.shape[r.n++] = egt_launch_shape{3, 1, 75, 0, 0};
+  r.shape[r.n++] = egt_launch_shape{4, 1, 100, 1, 0};
+  for (int mb : {64, 96, 128}) r.shape[r.n++] = egt_launch_shape{3, 1, 100, 0, mb};   // L2: 126 MB
+  static_assert(5 + 3 + 1 + 1 + 3 <= EGT_TUNE_MAX, "tuning candidates");
   double best = 0.0;
   for (int k = 0; k < r.n; ++k) {
     double us_best = 0.0;

@@ -103,7 +103,8 @@ class Checkpoint(C.Structure):
 
 
 class LaunchShape(C.Structure):
-    _fields_ = [("share", C.c_int32), ("pairs", C.c_int32), ("grid_pct", C.c_int32)]
+    _fields_ = [("share", C.c_int32), ("pairs", C.c_int32), ("grid_pct", C.c_int32), ("pack", C.c_int32),
+                ("wave_mb", C.c_int32)]
 
 
 TUNE_MAX = 16
@@ -547,14 +548,15 @@ class Batch:
 
     @property
     def shape(self):
-        """The launch shape of group-0 steps: dict(share, pairs, grid_pct)."""
+        """The launch shape of group-0 steps: dict(share, pairs, grid_pct, pack, wave_mb)."""
         x = LaunchShape()
         _check(lib.egt_batch_get_shape(self._h, C.byref(x)))
-        return dict(share=x.share, pairs=x.pairs, grid_pct=x.grid_pct)
+        return dict(share=x.share, pairs=x.pairs, grid_pct=x.grid_pct, pack=x.pack, wave_mb=x.wave_mb)
 
     @shape.setter
     def shape(self, value):
-        x = LaunchShape(value["share"], value["pairs"], value["grid_pct"])
+        x = LaunchShape(value["share"], value["pairs"], value["grid_pct"], value.get("pack", 0),
+                        value.get("wave_mb", 0))
         _check(lib.egt_batch_set_shape(self._h, C.byref(x)))
 
     def tune(self, n_iters=20, reps=1, stream=None):
@@ -563,7 +565,8 @@ class Batch:
         r = TuneReport()
         _check(lib.egt_batch_tune(self._h, n_iters, reps, C.byref(r), _stream(stream)))
         cands = [dict(share=r.shape[k].share, pairs=r.shape[k].pairs, grid_pct=r.shape[k].grid_pct,
-                      us_per_iter=r.us_per_iter[k], iters=r.iters[k]) for k in range(r.n)]
+                      pack=r.shape[k].pack, wave_mb=r.shape[k].wave_mb, us_per_iter=r.us_per_iter[k],
+                      iters=r.iters[k]) for k in range(r.n)]
         return dict(best=r.best, candidates=cands)
 
     def run(self, n_iters=200, group=0, stream=None):

@@ -174,7 +174,7 @@ def test_autotuned_shapes_leave_results_bitwise_unchanged(egtlib):
         g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
         slots.append(b.add(g, variant=egtlib.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1))
         games.append(g)
-    assert b.shape == dict(share=3, pairs=1, grid_pct=100)
+    assert b.shape == dict(share=3, pairs=1, grid_pct=100, pack=0, wave_mb=128)
     rep = b.tune(n_iters=3, reps=1)                # 13 candidates x 3 iterations = 39 of the 60
     cands = rep["candidates"]
     assert len(cands) == 13 and 0 <= rep["best"] < 13
@@ -182,7 +182,7 @@ def test_autotuned_shapes_leave_results_bitwise_unchanged(egtlib):
     assert all(c["iters"] == 3 * len(specs) for c in timed)    # every member ran every trial
     best = cands[rep["best"]]
     assert best["us_per_iter"] == min(c["us_per_iter"] for c in timed) > 0
-    assert b.shape == {k: best[k] for k in ("share", "pairs", "grid_pct")}
+    assert b.shape == {k: best[k] for k in ("share", "pairs", "grid_pct", "pack", "wave_mb")}
     b.run(n_iters=7)
     for sp, g, s in zip(specs, games, slots):
         xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, n, 1)
@@ -198,8 +198,8 @@ def test_autotuned_shapes_leave_results_bitwise_unchanged(egtlib):
         b.shape = dict(share=5, pairs=1, grid_pct=100)
     with pytest.raises(egtlib.EGTError):
         b.shape = dict(share=2, pairs=1, grid_pct=0)
-    b.shape = dict(share=0, pairs=0, grid_pct=50)
-    assert b.shape == dict(share=0, pairs=0, grid_pct=50)
+    b.shape = dict(share=0, pairs=0, grid_pct=50, pack=1, wave_mb=3)
+    assert b.shape == dict(share=0, pairs=0, grid_pct=50, pack=1, wave_mb=3)
     b.close()
 
 
@@ -252,4 +252,49 @@ def test_launch_shape_fields_take_effect(egtlib):
         xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, 30, 1)
         xb, yb, mu = member_state(egtlib, g)
         assert torch.equal(xb, xs) and torch.equal(yb, ys)
+    b.close()
+
+
+def test_packed_plan_runs_small_members_in_turn(egtlib):
+    """pack = 1: members lighter than the balanced makespan share one-CTA groups run in turn
+    (here many small games beside a large one); results still equal solo solves."""
+    specs = [synth.large()] + [synth.tiny(seed=synth.BASE_SEED + k) for k in range(40)]
+    n = 12
+    b = egtlib.Batch(0)
+    b.shape = dict(share=4, pairs=1, grid_pct=100, pack=1)
+    games = []
+    for sp in specs:
+        g = egtlib.Game(sp, device=0)
+        g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+        b.add(g, variant=egtlib.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1)
+        games.append(g)
+    b.step(4)
+    group, grid = b.launch_shape()
+    assert grid <= torch.cuda.get_device_properties(0).multi_processor_count and group > 1
+    b.run(n_iters=4)
+    for sp, g in list(zip(specs, games))[:6]:
+        xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, n, 1)
+        xb, yb, mu = member_state(egtlib, g)
+        assert torch.equal(xb, xs) and torch.equal(yb, ys), sp.name
+        assert mu == rs["mu"]
+    b.close()
+
+
+def test_waves_keep_results(egtlib):
+    """wave_mb: members in consecutive launches of bounded device bytes; same results."""
+    specs = [synth.tiny(seed=synth.BASE_SEED + k) for k in range(6)] + [synth.full_deck()]
+    n = 20
+    b = egtlib.Batch(0)
+    games = []
+    for sp in specs:
+        g = egtlib.Game(sp, device=0)
+        g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
+        b.add(g, variant=egtlib.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1)
+        games.append(g)
+    b.shape = dict(share=3, pairs=1, grid_pct=100, pack=0, wave_mb=1)   # about one member per wave
+    b.run(n_iters=6)
+    for sp, g in zip(specs, games):
+        xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, n, 1)
+        xb, yb, mu = member_state(egtlib, g)
+        assert torch.equal(xb, xs) and torch.equal(yb, ys), sp.name
     b.close()
