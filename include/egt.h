@@ -377,7 +377,8 @@ typedef struct {
 
 EGT_API egt_status egt_batch_member(const egt_batch* batch, int32_t slot, egt_batch_member_info* out);
 
-/* Launch shape of the last egt_batch_step: CTAs per member and grid (host, either may be NULL). */
+/* Launch shape of the last egt_batch_step (of its last launch when it ran in waves): the widest
+ * group's CTAs and the grid (host, either may be NULL). */
 EGT_API egt_status egt_batch_launch_shape(const egt_batch* batch, int32_t* group, int32_t* grid);
 
 /* How egt_batch_step (group = 0) splits the device over the active members.
