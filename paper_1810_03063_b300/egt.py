@@ -555,8 +555,10 @@ class Batch:
 
     @shape.setter
     def shape(self, value):
-        x = LaunchShape(value["share"], value["pairs"], value["grid_pct"], value.get("pack", 0),
-                        value.get("wave_mb", 0))
+        """Set some or all of the fields; the others keep their current values."""
+        cur = self.shape
+        cur.update(value)
+        x = LaunchShape(cur["share"], cur["pairs"], cur["grid_pct"], cur["pack"], cur["wave_mb"])
         _check(lib.egt_batch_set_shape(self._h, C.byref(x)))
 
     def tune(self, n_iters=20, reps=1, stream=None):
