@@ -527,12 +527,14 @@ EGT_API egt_status egt_profile_read(egt_game* game, double* ms, int64_t* launche
  * SBR / product / SBR / product / SBR / product phases (phase 0 is skipped when
  * the previous iteration computed this v_hat ahead; phase 5 then may carry the
  * next iteration's v_hat), 6 the phase after the Step (the other player's EGV
- * part, the residual's FP64 best responses, the next v_hat), 7 the sums
- * behind the EGV and residual decisions (fixed-order sums of the per-item
- * partials that every CTA reads after phase 6; no barrier).  phase_us: from
+ * part, the residual's FP64 best responses, the next v_hat), 7 CTA 0's time
+ * from the top of the iteration loop to its first phase (the fixed-order sums
+ * of the per-item partials and the EGV / residual decisions when CTA 0 is the
+ * group's deciding CTA, its last rank; the other CTAs start the next attempt
+ * meanwhile), 8 from there to its first product phase.  phase_us: from
  * one mark to the next (for 0-6, barrier exits: the phase's slowest CTA and the
  * barrier included); work_us: for 0-6, from that exit to CTA 0's arrival at the
- * next barrier (its own items); phase_count: phases timed.  Host arrays of 8
+ * next barrier (its own items); phase_count: phases timed.  Host arrays of 9
  * entries, any may be NULL; reset != 0 clears the sums after reading. */
 EGT_API egt_status egt_engine_trace(egt_game* game, int32_t reset, double* phase_us, double* work_us,
                                     int64_t* phase_count);

@@ -9,12 +9,16 @@
 // spread over the group's CTAs.  Products stay
 // in terminal-contribution form; the SBR items add a sequence's contributions
 // while they load their tile.
-// Every CTA keeps its own copy of the solver state (t, mu, tau, buffer index)
-// and takes every decision (EGV sign, tau back-off, gap target) itself from
-// the same per-item FP64 partials, summed in the same fixed order as the
-// standalone kernels: all CTAs of a group agree without a broadcast, a run here
-// reproduces the host-driven loop of api.cu bit for bit, and a game's iterates
-// do not depend on the group size or on the other games of the launch.
+// One CTA of the group (the last rank, which holds the fewest items of a phase)
+// keeps the solver state (t, mu, tau, buffer index) and takes every decision
+// (EGV sign, tau back-off, gap target) from the per-item FP64 partials, summed in
+// the same fixed order as the standalone kernels; it publishes each verdict and
+// the next schedule in the control block, and the others read them at the next
+// attempt's first product barrier.  The group starts each attempt before the
+// verdict on the previous one is known (see engine_job), so the sums and the FP64
+// decisions are off the other CTAs' critical path.  A run here reproduces the
+// host-driven loop of api.cu bit for bit, and a game's iterates do not depend on
+// the group size or on the other games of the launch.
 //
 // The group barrier is a monotone 64-bit arrival counter in the job's control
 // block: barrier k completes when it reaches k x (CTAs of the group).  Waits are bounded in time: if one runs
@@ -104,6 +108,68 @@ __device__ bool grid_sync(const GridBar& b, unsigned long long& k, PhaseClock* c
   }
   __syncthreads();
   return ok_s != 0;
+}
+
+// Verdicts the deciding CTA publishes on the previous attempt.
+constexpr int kGo = 0;      // accepted (or none pending): the running attempt stands
+constexpr int kRedo = 1;    // rejected: the running attempt is void, run EngineCtl::redo
+constexpr int kStop = 2;    // leave the iteration loop
+
+// grid_sync that also waits for the verdict word of epoch `tag` (published by the
+// deciding CTA before its arrival, so the barrier completes with it in sight: the
+// word is polled beside the arrival counter) and returns its verdict in *code.
+__device__ __forceinline__ bool grid_sync_verdict(const GridBar& b, unsigned long long& k, PhaseClock* clk, bool clock_cta,
+                                  const unsigned long long* word, unsigned long long tag, int* code) {
+  __shared__ int ok_s, code_s;
+  __syncthreads();
+  ++k;
+  if (threadIdx.x == 0) {
+    if (clock_cta) clk->arrive = global_ns();
+    const bool group = b.expected != 1;
+    int ok = 1;
+    if (group) asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(b.arrive) : "memory");
+    const unsigned long long target = k * b.expected;
+    unsigned long long w = 0;
+    unsigned int polls = 0;
+    unsigned long long t0 = 0;
+    for (;;) {
+      const bool all = !group || ld_acquire(b.arrive) >= target;
+      w = ld_acquire(word);
+      if (all && (w >> 8) == tag) break;
+      if ((++polls & 1023u) == 0) {
+        const unsigned long long now = global_ns();
+        if (t0 == 0) {
+          t0 = now;
+        } else if (now - t0 > b.limit_ns) {
+          atomicCAS(b.status, 0, (int)EGT_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        if (ld_volatile(b.status) != 0) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    if (group && ld_volatile(b.status) != 0) ok = 0;
+    ok_s = ok;
+    code_s = (int)(w & 0xffu);
+  }
+  __syncthreads();
+  *code = code_s;
+  return ok_s != 0;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Copy a schedule published in the control block (read at L2: another CTA wrote it).
+__device__ __forceinline__ void load_sched(EngineSched& dst, const EngineSched* src) {
+  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(EngineSched) / 8); ++i) d[i] = __ldcg(s + i);
 }
 
 // CTA 0 books the time since the last mark to `phase` (work done without a barrier).
@@ -282,20 +348,170 @@ __device__ __forceinline__ void choose(int variant, int t, double mu0, double mu
   }
 }
 
-// Decisions of the current attempt, written by thread 0 of the CTA (the only
-// thread that runs the solver's FP64 bookkeeping: FP64 is a narrow pipe on this
-// part, and 512 redundant copies of it cost microseconds per iteration) and read
-// by all threads after a CTA barrier.
-struct Sched {
-  int stop;             // leave the iteration loop
-  int cur, me, gap_due, spec, pre;
-  float tau, tau2;      // this attempt's tau, the next iteration's (FP32, for the mixing)
-  double mu_me, mu_ot;  // mu of the stepping player and of the other
-  double mu_tilde;      // (1 - tau) mu_me
+using Sched = EngineSched;
+
+// The solver's scalar state (t, mu, tau, buffer index, counters, the attempt in
+// flight), kept in shared memory by thread 0 of the group's deciding CTA.  Every CTA
+// starts from the control block and plans the first attempt itself; after that only
+// the decider advances the state and publishes each verdict and schedule (FP64 is a
+// narrow pipe on this part: one thread of one CTA takes the decisions, off the
+// critical path of the other CTAs).
+struct Solver {
+  double mu0, mu1, tau_as, gap, eps_mbb, mbb_scale;
+  double tau, egv, mu_next, last_tau, last_egv;
+  int t, cur, it, done, backoffs_total, products, gap_checks, reached, status;
+  int last_player, last_backoffs, me, backoffs, spec, gap_due, pre, new_iter;
 };
+
+struct LoopCfg {
+  int variant, n_iters, gap_every, max_t;
+  bool check;   // EGT/as: the excessive-gap check decides acceptance
+};
+
+// Start an attempt from the state: the loop's stop test, the player and tau of a new
+// iteration, and the attempt's schedule.  The next iteration's choice if this attempt
+// is accepted decides where its v_hat is computed ahead: with the last product when
+// the same player steps again (its gradient and iterate are final there), else in the
+// last phase, from the same smoothed best response as the other's EGV part (same
+// gradient, same mu).
+__device__ __forceinline__ Sched plan_attempt(Solver& s, const LoopCfg& k) {
+  Sched sc;
+  sc.stop = !(s.it < k.n_iters && s.status == 0) || (s.it > 0 && s.new_iter && (s.reached || s.t >= k.max_t));
+  sc.cur = sc.me = sc.gap_due = sc.spec = sc.pre = 0;
+  sc.tau = sc.tau2 = 0.f;
+  sc.mu_me = sc.mu_ot = sc.mu_tilde = 0.0;
+  if (sc.stop) return sc;
+  if (s.new_iter) {
+    choose(k.variant, s.t, s.mu0, s.mu1, s.tau_as, s.me, s.tau);
+    s.backoffs = 0;
+    s.egv = 0.0 / 0.0;
+  }
+  const bool xs = s.me == 0;
+  s.gap_due = (s.t + 1) % k.gap_every == 0 || s.t + 1 >= k.max_t;
+  s.mu_next = (1 - s.tau) * (xs ? s.mu0 : s.mu1);   // mu of the stepping player if accepted
+  int me2;
+  double tau2;
+  choose(k.variant, s.t + 1, xs ? s.mu_next : s.mu0, xs ? s.mu1 : s.mu_next, s.tau, me2, tau2);
+  s.spec = me2 == s.me ? 1 : (k.check || s.gap_due ? 2 : 0);
+  sc.cur = s.cur;
+  sc.me = s.me;
+  sc.gap_due = s.gap_due;
+  sc.spec = s.spec;
+  sc.pre = s.pre;
+  sc.tau = (float)s.tau;
+  sc.tau2 = (float)tau2;
+  sc.mu_me = xs ? s.mu0 : s.mu1;
+  sc.mu_ot = xs ? s.mu1 : s.mu0;
+  sc.mu_tilde = s.mu_next;
+  return sc;
+}
+
+// Alg. 2's last lines for an accepted attempt: mu_me^+ = (1 - tau) mu_me (computed with
+// the attempt), swap the iterate buffers, count.
+__device__ __forceinline__ void accept_attempt(Solver& s, int variant) {
+  if (s.me == 0) s.mu0 = s.mu_next;
+  else s.mu1 = s.mu_next;
+  if (variant == EGT_AS) s.tau_as = s.tau;
+  s.cur = 1 - s.cur;
+  s.t += 1;
+  s.backoffs_total += s.backoffs;
+  s.done += 1;
+  s.last_player = s.me;
+  s.last_backoffs = s.backoffs;
+  s.last_tau = s.tau;
+  s.last_egv = s.egv;
+  s.pre = s.spec != 0;
+  s.it += 1;
+  s.new_iter = 1;
+}
+
+// The verdict on the attempt in flight from its sums red (EGV parts, residual values):
+// accept (Alg. 2, then the residual of the new point when it was due), or halve tau and
+// retry (Alg. 4's Decr).  Returns true if accepted.
+__device__ __forceinline__ bool decide(Solver& s, const LoopCfg& k, const double* red, const EngineBufs& b) {
+  s.products += 3;
+  bool accept = true;
+  if (k.check) {
+    const double phi = s.me == 0 ? red[0] : red[1], negf = s.me == 0 ? red[1] : red[0];
+    s.egv = phi + negf;
+    if (!isfinite(s.egv)) {
+      s.status = EGT_ERR_NUMERIC;
+      accept = false;
+    } else if (s.egv < 0) {
+      accept = false;
+      s.tau *= 0.5;
+      if (s.tau < 1.0 / (1u << 30)) s.status = EGT_ERR_TAU_UNDERFLOW;
+      else ++s.backoffs;
+    }
+  }
+  if (!accept) {
+    s.pre = 0;
+    s.new_iter = 0;
+    return false;
+  }
+  if (b.log != nullptr && s.it < b.log_cap) {
+    egt_iter_log& L = b.log[s.it];
+    L.t = s.t;
+    L.player = s.me;
+    L.backoffs = s.backoffs;
+    L.tau = s.tau;
+    L.mu[0] = s.me == 0 ? s.mu_next : s.mu0;
+    L.mu[1] = s.me == 0 ? s.mu1 : s.mu_next;
+    L.egv = k.check ? s.egv : 0.0 / 0.0;
+    L.gap_mbb = s.gap;
+    L.time_ns = global_ns();
+  }
+  const int gap_due = s.gap_due;
+  accept_attempt(s, k.variant);
+  if (gap_due) {
+    // eps_sad of the new iterates from the FP64 products of the Step:
+    // max_y <y, A^T x> - min_x <x, A y>
+    s.gap = (red[3] - red[2]) * s.mbb_scale;
+    s.gap_checks += 1;
+    if (!isfinite(s.gap)) s.status = EGT_ERR_NUMERIC;
+    else s.reached = s.eps_mbb > 0 && s.gap <= s.eps_mbb ? 1 : 0;
+  }
+  return true;
+}
+
+// The deciding CTA's thread 0: the verdict on the pending attempt (if any) from its
+// sums red, then, unless that voids or ends the running attempt, the schedule of the
+// attempt after the running one (as if the running one is accepted); published with
+// the verdict word of epoch ep.
+__device__ __forceinline__ void settle(Solver& S, Solver& S2, EngineCtl* ctl, const EngineBufs& b, const double* red,
+                                    bool pending, bool stop_now, unsigned int ep) {
+  const LoopCfg kc{ctl->variant, ctl->n_iters, ctl->gap_every, ctl->max_t, ctl->variant == EGT_AS};
+  int code = kGo;
+  if (pending) {
+    const bool acc = decide(S, kc, red, b);
+    const Sched x = plan_attempt(S, kc);
+    if (x.stop) {
+      code = kStop;
+    } else if (!acc) {
+      code = kRedo;
+      ctl->redo = x;
+    }
+  }
+  if (code == kGo && !stop_now) {
+    S2 = S;
+    accept_attempt(S2, kc.variant);
+    ctl->next = plan_attempt(S2, kc);
+  }
+  st_release(&ctl->verdict, ((unsigned long long)ep << 8) | (unsigned long long)code);
+}
 
 // One job (game) run by the group `gr`: its tables staged in smem_all, then up to
 // ctl->n_iters iterations.  Returns when the job stops or fails (status recorded).
+//
+// The verdict on an attempt (its EGV sign, the residual against the target) needs the
+// sums of the attempt's last phase.  The group does not wait for it: right after that
+// phase every CTA starts the next attempt as if the verdict were "accepted, continue"
+// (its schedule was published one attempt ahead), while the deciding CTA (the last
+// rank, which holds the fewest items of a phase) sums the partials, takes the
+// verdict and publishes it before it arrives at the new attempt's first product
+// barrier.  Everything the new attempt writes before that barrier is scratch (the
+// v_hat buffer and the other player's gradient at v_hat), so a rejected attempt is
+// retried from unchanged iterates, and a stop discards only scratch.
 __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b, EngineCtl* ctl, Grp gr,
                                            int pair_bits, unsigned long long expected,
                                            unsigned long long limit_ns, unsigned char* smem_all) {
@@ -309,9 +525,19 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
   const GridBar bar{&ctl->bar_arrive, &ctl->status, expected, limit_ns};
   unsigned long long bk = 0;                      // barriers passed by this CTA
   __shared__ PhaseClock clk_s;
-  __shared__ Sched sc;
+  __shared__ Sched sc, sc_next;                   // the running attempt; the one after it
+  __shared__ Solver S, S2;                        // thread 0 (advanced by the decider only)
   PhaseClock* clk = &clk_s;
   const bool lead = threadIdx.x == 0;
+  const bool clock_cta = gr.rank == 0;
+  const bool decider = gr.rank == gr.size - 1;
+  const int NB = g.ld / kSbrHands;
+  double* partA = b.partials;
+  double* partB = b.partials + NB;
+  double* partBR0 = b.partials + 2 * NB;
+  double* partBR1 = b.partials + 3 * NB;
+  const bool check = ctl->variant == EGT_AS;
+
   if (lead) {
     clk->last = global_ns();
     clk->arrive = clk->last;
@@ -320,76 +546,57 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
       clk->work[k] = 0;
       clk->n[k] = 0;
     }
-  }
-  const bool clock_cta = gr.rank == 0;
-  const bool writer = clock_cta && lead;
-  const int NB = g.ld / kSbrHands;
-  double* partA = b.partials;
-  double* partB = b.partials + NB;
-  double* partBR0 = b.partials + 2 * NB;
-  double* partBR1 = b.partials + 3 * NB;
-  const int variant = ctl->variant, n_iters = ctl->n_iters, gap_every = ctl->gap_every;
-  const int max_t = ctl->max_t;
-  const bool check = variant == EGT_AS;
-
-  // solver state: meaningful in thread 0 only (identical in every CTA)
-  int t = 0, cur = 0, done = 0, backoffs_total = 0, products = 0, gap_checks = 0, reached = 0;
-  int status = 0, last_player = -1, last_backoffs = 0, it = 0, me = 0, backoffs = 0, spec = 0;
-  double mu0 = 0, mu1 = 0, tau_as = 0, gap = 0, tau = 0, eps_mbb = 0, mbb_scale = 1;
-  double last_tau = 0.0 / 0.0, last_egv = 0.0 / 0.0, egv = 0.0 / 0.0, mu_next = 0;
-  bool pre = false;        // v_hat of this iteration already computed (ahead, by the previous one)
-  bool new_iter = true;    // the next attempt starts an iteration (else it retries with tau / 2)
-  if (lead) {
-    t = ctl->t;
-    cur = ctl->cur;
-    mu0 = ctl->mu[0];
-    mu1 = ctl->mu[1];
-    tau_as = ctl->tau;
-    gap = ctl->gap_mbb;
-    eps_mbb = ctl->eps_mbb;
-    mbb_scale = ctl->mbb_scale;
+    S.t = ctl->t;
+    S.cur = ctl->cur;
+    S.mu0 = ctl->mu[0];
+    S.mu1 = ctl->mu[1];
+    S.tau_as = ctl->tau;
+    S.gap = ctl->gap_mbb;
+    S.eps_mbb = ctl->eps_mbb;
+    S.mbb_scale = ctl->mbb_scale;
+    S.tau = 0;
+    S.egv = S.last_tau = S.last_egv = 0.0 / 0.0;
+    S.mu_next = 0;
+    S.it = S.done = S.backoffs_total = S.products = S.gap_checks = S.reached = S.status = 0;
+    S.last_player = -1;
+    S.last_backoffs = S.me = S.backoffs = S.spec = S.gap_due = S.pre = 0;
+    S.new_iter = 1;
+    const LoopCfg kc{ctl->variant, ctl->n_iters, ctl->gap_every, ctl->max_t, check};
+    sc = plan_attempt(S, kc);   // the same in every CTA
   }
 
+  bool pending = false;      // the previous attempt awaits its verdict
+  bool pend_sums = false;    // ... and its verdict needs the sums of its last phase
+  int pend_gap = 0;          // ... which include the residual's best responses
+  unsigned int ep = 0;       // verdict epochs (one per attempt)
   for (;;) {
-    if (lead) {
-      int stop = !(it < n_iters && status == 0) || (it > 0 && new_iter && (reached || t >= max_t));
-      if (!stop) {
-        if (new_iter) {
-          choose(variant, t, mu0, mu1, tau_as, me, tau);
-          backoffs = 0;
-          egv = 0.0 / 0.0;
-        }
-        const bool xs = me == 0;
-        const int gap_due = (t + 1) % gap_every == 0 || t + 1 >= max_t;
-        // The next iteration's choice if this attempt is accepted, and its v_hat computed
-        // ahead: with the last product when the same player steps again (its gradient and
-        // iterate are final there), else in the last phase, from the same smoothed best
-        // response as the other's EGV part (same gradient, same mu).
-        int me2;
-        double tau2;
-        mu_next = (1 - tau) * (xs ? mu0 : mu1);   // mu of the stepping player if accepted
-        choose(variant, t + 1, xs ? mu_next : mu0, xs ? mu1 : mu_next, tau, me2, tau2);
-        spec = me2 == me ? 1 : (check || gap_due ? 2 : 0);
-        sc.cur = cur;
-        sc.me = me;
-        sc.gap_due = gap_due;
-        sc.spec = spec;
-        sc.pre = pre;
-        sc.tau = (float)tau;
-        sc.tau2 = (float)tau2;
-        sc.mu_me = xs ? mu0 : mu1;
-        sc.mu_ot = xs ? mu1 : mu0;
-        sc.mu_tilde = mu_next;
-      }
-      sc.stop = stop;
-    }
     __syncthreads();
-    if (sc.stop) break;
+    const bool stop_now = sc.stop != 0;
+    if (stop_now && !pending) break;
+    ++ep;
     const int c = sc.cur, m = sc.me, gap_due = sc.gap_due, sp = sc.spec;
     const bool have_hat = sc.pre != 0;
-    const float tau_f = sc.tau, tau2_f = sc.tau2;
-    const double mu_me = sc.mu_me, mu_ot = sc.mu_ot, mu_tilde = sc.mu_tilde;
     const bool tail = check || gap_due;              // a phase after the Step's last product
+
+    // the decider: the verdict on the previous attempt, then (unless it voids or ends
+    // the running one) the schedule of the attempt after the running one
+    if (decider) {
+      double red[4] = {0.0, 0.0, 0.0, 0.0};
+      // the EGV parts (partA, partB) and the residual's values (partBR0, partBR1) in one pass
+      if (pending && pend_sums) reduce_arrays(b.partials, NB, check ? 0 : 2, pend_gap ? 4 : 2, red);
+      if (lead) settle(S, S2, ctl, b, red, pending, stop_now, ep);
+    }
+    phase_cut(clk, 7, clock_cta);
+    if (stop_now) {
+      // the schedule said stop if the previous attempt is accepted: its verdict decides
+      // between stopping and retrying it
+      int code = kStop;
+      if (!grid_sync_verdict(bar, bk, clk, clock_cta, &ctl->verdict, ep, &code)) return;
+      if (code != kRedo) break;
+      if (lead) load_sched(sc, &ctl->redo);
+      pending = false;
+      continue;
+    }
 
     // Alg. 2 Step focused on m (the y-focused step swaps roles, A -> -A^T)
     const int ot = 1 - m;
@@ -418,14 +625,32 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
 
     // v_hat = (1 - tau) v + tau v_mu(other)
     if (!have_hat) {
-      run_sbr(g, tb, gr, pair_ok, m, g_me, mu_me, v_me, tau_f, t_me, nullptr, sm);
+      run_sbr(g, tb, gr, pair_ok, m, g_me, sc.mu_me, v_me, sc.tau, t_me, nullptr, sm);
       if (!phase_end(bar, bk, clk, 0, clock_cta)) return;
     }
     phase_cut(clk, 8, clock_cta);
     run_grad(g, tb, gr, pair_terms, ot, t_me, t_ot, nullptr, sm);   // the other's loss gradient at v_hat
-    if (!phase_end(bar, bk, clk, 1, clock_cta)) return;
+    {
+      int code = kGo;
+      if (!grid_sync_verdict(bar, bk, clk, clock_cta, &ctl->verdict, ep, &code)) return;
+      if (clock_cta && lead) {
+        const unsigned long long now = global_ns();
+        clk->ns[1] += now - clk->last;
+        clk->work[1] += clk->arrive - clk->last;
+        clk->n[1] += 1;
+        clk->last = now;
+      }
+      if (code == kStop) break;
+      if (code == kRedo) {
+        // the previous attempt was rejected: this one is void (it wrote scratch only)
+        if (lead) load_sched(sc, &ctl->redo);
+        pending = false;
+        continue;
+      }
+      if (lead) load_sched(sc_next, &ctl->next);   // (first read at the end of the attempt)
+    }
     // other_+ = (1 - tau) other + tau other_mu(v_hat)
-    run_sbr(g, tb, gr, pair_ok, ot, t_ot, mu_ot, v_ot, tau_f, v_ot_n, nullptr, sm);
+    run_sbr(g, tb, gr, pair_ok, ot, t_ot, sc.mu_ot, v_ot, sc.tau, v_ot_n, nullptr, sm);
     if (!phase_end(bar, bk, clk, 2, clock_cta)) return;
     run_grad(g, tb, gr, pair_terms, m, v_ot_n, g_me_n, g64_me, sm);   // my loss gradient at other_+
     if (!phase_end(bar, bk, clk, 3, clock_cta)) return;
@@ -442,9 +667,9 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
           a.contrib = true;
           a.grz = m ? g.rz[1] : g.rz[0];
           a.sign = m == 0 ? 1.f : -1.f;
-          a.mu = mu_tilde;
+          a.mu = sc.mu_tilde;
           a.old = v_me;
-          a.tau = tau_f;
+          a.tau = sc.tau;
           a.out = v_me_n;
           a.value_partial = partA + item;
           sbr_item(g, tp, item, a, reinterpret_cast<float*>(ism), wg);
@@ -469,9 +694,9 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
           a.contrib = true;
           a.grz = m ? g.rz[1] : g.rz[0];
           a.sign = m == 0 ? 1.f : -1.f;
-          a.mu = mu_tilde;
+          a.mu = sc.mu_tilde;
           a.old = v_me_n;
-          a.tau = tau2_f;
+          a.tau = sc.tau2;
           a.out = t_me;
           a.value_partial = nullptr;
           sbr_item(g, pick(tb, m), item - T, a, reinterpret_cast<float*>(sm));
@@ -479,7 +704,6 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
       }
     }
     if (!phase_end(bar, bk, clk, 5, clock_cta)) return;
-    double red[4] = {0.0, 0.0, 0.0, 0.0};
     if (tail) {
       // the other's EGV part and / or the next v_hat (items [0, NB)), the other's FP64
       // best response when the residual is due (the following NB items)
@@ -493,9 +717,9 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
           a.contrib = true;
           a.grz = ot ? g.rz[1] : g.rz[0];
           a.sign = ot == 0 ? 1.f : -1.f;
-          a.mu = mu_ot;
+          a.mu = sc.mu_ot;
           a.old = sp == 2 ? v_ot_n : nullptr;
-          a.tau = sp == 2 ? tau2_f : 0.f;
+          a.tau = sp == 2 ? sc.tau2 : 0.f;
           a.out = sp == 2 ? t_ot : nullptr;
           a.value_partial = check ? partB + item : nullptr;
           sbr_item(g, tp, item, a, reinterpret_cast<float*>(ism), wg);
@@ -504,87 +728,33 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
         }
       });
       if (!phase_end(bar, bk, clk, 6, clock_cta)) return;
-      // the EGV parts (partA, partB) and the residual's values (partBR0, partBR1) in one pass
-      reduce_arrays(b.partials, NB, check ? 0 : 2, gap_due ? 4 : 2, red);
-      phase_cut(clk, 7, clock_cta);
     }
-
-    if (lead) {
-      products += 3;
-      bool accept = true;
-      if (check) {
-        const double phi = xs ? red[0] : red[1], negf = xs ? red[1] : red[0];
-        egv = phi + negf;
-        if (!isfinite(egv)) {
-          status = EGT_ERR_NUMERIC;
-          accept = false;
-        } else if (egv < 0) {
-          accept = false;
-          tau *= 0.5;
-          if (tau < 1.0 / (1u << 30)) status = EGT_ERR_TAU_UNDERFLOW;
-          else ++backoffs;
-        }
-      }
-      if (accept) {
-        // accept (Alg. 2 last lines): mu_me^+ = (1 - tau) mu_me, swap the iterate buffers
-        if (xs) mu0 = mu_next;   // (1 - tau) mu_x, computed with the attempt
-        else mu1 = mu_next;
-        if (variant == EGT_AS) tau_as = tau;
-        if (writer && b.log != nullptr && it < b.log_cap) {
-          egt_iter_log& L = b.log[it];
-          L.t = t;
-          L.player = me;
-          L.backoffs = backoffs;
-          L.tau = tau;
-          L.mu[0] = mu0;
-          L.mu[1] = mu1;
-          L.egv = check ? egv : 0.0 / 0.0;
-          L.gap_mbb = gap;
-          L.time_ns = global_ns();
-        }
-        cur = 1 - cur;
-        t += 1;
-        backoffs_total += backoffs;
-        done += 1;
-        last_player = me;
-        last_backoffs = backoffs;
-        last_tau = tau;
-        last_egv = egv;
-        pre = spec != 0;
-        if (gap_due) {
-          // eps_sad of the new iterates from the FP64 products of the Step:
-          // max_y <y, A^T x> - min_x <x, A y>
-          gap = (red[3] - red[2]) * mbb_scale;
-          gap_checks += 1;
-          if (!isfinite(gap)) status = EGT_ERR_NUMERIC;
-          else reached = eps_mbb > 0 && gap <= eps_mbb ? 1 : 0;
-        }
-        it += 1;
-        new_iter = true;
-      } else {
-        pre = false;
-        new_iter = false;
-      }
-    }
+    // the next attempt starts at once, on the schedule published for "accepted"
+    pending = true;
+    pend_sums = tail;
+    pend_gap = gap_due;
+    if (lead) sc = sc_next;
   }
 
-  if (writer) {
-    ctl->t = t;
-    ctl->cur = cur;
-    ctl->mu[0] = mu0;
-    ctl->mu[1] = mu1;
-    ctl->tau = tau_as;
-    ctl->gap_mbb = gap;
-    ctl->reached = reached;
-    ctl->done_iters = done;
-    ctl->backoffs = backoffs_total;
-    ctl->products = products;
-    ctl->gap_checks = gap_checks;
-    ctl->last_player = last_player;
-    ctl->last_backoffs = last_backoffs;
-    ctl->last_tau = last_tau;
-    ctl->last_egv = last_egv;
-    if (status != 0) atomicCAS(&ctl->status, 0, status);
+  if (decider && lead) {
+    ctl->t = S.t;
+    ctl->cur = S.cur;
+    ctl->mu[0] = S.mu0;
+    ctl->mu[1] = S.mu1;
+    ctl->tau = S.tau_as;
+    ctl->gap_mbb = S.gap;
+    ctl->reached = S.reached;
+    ctl->done_iters = S.done;
+    ctl->backoffs = S.backoffs_total;
+    ctl->products = S.products;
+    ctl->gap_checks = S.gap_checks;
+    ctl->last_player = S.last_player;
+    ctl->last_tau = S.last_tau;
+    ctl->last_backoffs = S.last_backoffs;
+    ctl->last_egv = S.last_egv;
+    if (S.status != 0) atomicCAS(&ctl->status, 0, S.status);
+  }
+  if (clock_cta && lead) {
 #pragma unroll
     for (int k = 0; k < kEnginePhases; ++k) {
       ctl->phase_ns[k] = clk->ns[k];

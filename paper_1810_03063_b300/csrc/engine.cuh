@@ -10,9 +10,22 @@ namespace egt {
 // Phases of an iteration timed by the engine (egt_engine_trace): the Step's
 // three SBR and three product phases (the last one may carry the next v_hat), and
 // the last phase (the other's EGV part, the residual's FP64 best responses, the
-// next v_hat when the other player steps next), then CTA 0's time on the sums
-// behind the EGV and residual decisions (no barrier).
+// next v_hat when the other player steps next), then CTA 0's time from the top of
+// the iteration loop to its first phase (the sums behind the EGV and residual
+// decisions and the decisions themselves when CTA 0 is the deciding CTA), then to
+// its first product phase (no barrier).
 constexpr int kEnginePhases = 9;
+
+// Schedule of one attempt of Alg. 2's Step (with Alg. 4's back-off): what every CTA
+// of the group needs to run its phases.
+struct EngineSched {
+  int stop;             // leave the iteration loop
+  int cur, me, gap_due, spec, pre;
+  float tau, tau2;      // this attempt's tau, the next iteration's (FP32, for the mixing)
+  double mu_me, mu_ot;  // mu of the stepping player and of the other
+  double mu_tilde;      // (1 - tau) mu_me
+};
+static_assert(sizeof(EngineSched) % 8 == 0, "EngineSched is copied in 8-byte words");
 
 // Control block in device memory, one per game.  The host writes the
 // configuration and the solver state before a launch and reads everything back
@@ -31,6 +44,12 @@ struct EngineCtl {
   double gap_mbb, egv, last_tau, last_egv;
   // grid barrier: monotone arrival counter
   unsigned long long bar_arrive;
+  // published by the group's deciding CTA before it arrives at an attempt's first
+  // product barrier: (epoch << 8) | verdict on the previous attempt, the schedule of
+  // the attempt after the running one (if the running one is accepted) and the
+  // schedule of a retry
+  unsigned long long verdict;
+  EngineSched next, redo;
   // device time per phase (CTA 0, between consecutive barrier exits), ns
   unsigned long long phase_ns[kEnginePhases];
   unsigned long long phase_work_ns[kEnginePhases];   // CTA 0's own work (to its barrier arrival)
