@@ -713,7 +713,9 @@ def run_phases(args, local):
     for name, spec in [("full deck", synth.full_deck()), ("large", synth.large()),
                        ("Libratus menus", synth.libratus())]:
         g = egt.Game(spec, device=local)
+        g.profile(1)                      # the engine's phase clock runs while profiling is on
         rep = g.solve(variant=egt.EGT_AS, alpha=0.01, eps_mbb=0.0, max_iters=300, gap_every=1)
+        g.profile(0)
         tr = g.engine_trace()
         tot = sum(v["us"] for v in tr.values())
         out.append({"game": name, "S": list(g.S), "T": g.T, "iters": rep["iters"],

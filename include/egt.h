@@ -522,8 +522,10 @@ EGT_API egt_status egt_profile(egt_game* game, int32_t enable);
  * entries, either may be NULL).  Waits for the recorded launches to finish. */
 EGT_API egt_status egt_profile_read(egt_game* game, double* ms, int64_t* launches);
 
-/* Device time of the device-resident driver (egt_iterate / egt_solve) by phase,
- * measured by CTA 0 and summed since the last reset.  Phases: 0-5 the Step's
+/* Device time of the device-resident driver (egt_iterate / egt_solve, and the
+ * game's batch steps) by phase, measured by CTA 0 while egt_profile timing is on
+ * for the game (the clock reads cost about 2 % of the iteration rate, so they
+ * are off otherwise) and summed since the last reset.  Phases: 0-5 the Step's
  * SBR / product / SBR / product / SBR / product phases (phase 0 is skipped when
  * the previous iteration computed this v_hat ahead; phase 5 then may carry the
  * next iteration's v_hat), 6 the phase after the Step (the other player's EGV

@@ -714,6 +714,7 @@ void engine_ctl_init(const egt_game* G, EngineCtl& c, int variant, double eps_mb
   c.n_iters = n;
   c.gap_every = std::max(1, gap_every);
   c.max_t = G->t + n;
+  c.trace = G->prof_on ? 1 : 0;
   c.eps_mbb = eps_mbb;
   c.mbb_scale = 1000.0 / G->bb;
   c.mu[0] = G->mu[0];

@@ -529,7 +529,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
   __shared__ Solver S, S2;                        // thread 0 (advanced by the decider only)
   PhaseClock* clk = &clk_s;
   const bool lead = threadIdx.x == 0;
-  const bool clock_cta = gr.rank == 0;
+  const bool clock_cta = gr.rank == 0 && ctl->trace != 0;
   const bool decider = gr.rank == gr.size - 1;
   const int NB = g.ld / kSbrHands;
   double* partA = b.partials;

@@ -33,6 +33,8 @@ static_assert(sizeof(EngineSched) % 8 == 0, "EngineSched is copied in 8-byte wor
 struct EngineCtl {
   // configuration
   int variant, n_iters, gap_every, max_t;
+  int trace;                   // CTA 0 times the phases (phase_ns ...): costs ~2 % of the rate
+  int pad0;
   double eps_mbb, mbb_scale;   // gap target; 1000 / bb (mbb per unit of payoff)
   // solver state (persists between launches)
   double mu[2];

@@ -445,7 +445,8 @@ class Game:
 
     def engine_trace(self, reset=True):
         """Per-phase device time of the device-resident driver: total (us), CTA 0's
-        own work (work_us), phases timed (n), average per phase (avg_us)."""
+        own work (work_us), phases timed (n), average per phase (avg_us).  Recorded
+        only while ``profile(1)`` is on for the game."""
         k = len(self.ENGINE_PHASES)
         us = np.zeros(k, np.float64)
         work = np.zeros(k, np.float64)
