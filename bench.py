@@ -40,7 +40,7 @@ METRIC = "EGT iter/s"
 # L2 flush), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
 # -k regex:engine_kernel_one -s 3 -c 1 python bench.py --steps 3 --warmup 3 --no-ttg --cpu-seconds 0
 # --batch-games 0`; to be re-taken (or set to None) whenever the engine kernel changes.
-ENGINE_TRAFFIC_BYTES = 1601024   # dram read 1 252 608 + write 348 416 B, one ncu pass over one timed launch
+ENGINE_TRAFFIC_BYTES = 1642752   # dram read 1 253 632 + write 389 120 B, one ncu pass over one timed launch
 UNIT = "iter/s"
 WORKLOAD = "full-deck river endgame: 52 cards, 1081 hands/player, bets {0.5,1}xpot + all-in, raise cap 3, stack 10, pot 1, EGT/as"
 
