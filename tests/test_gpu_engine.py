@@ -88,6 +88,30 @@ def test_iterate_in_chunks_equals_one_launch(egtlib):
     assert torch.equal(x1, x2)
 
 
+def test_one_iteration_launches_with_backoffs_equal_one_launch(egtlib):
+    """Every one-iteration launch ends with the deciding CTA's verdict on its last attempt
+    pending: a rejection there must be redone inside the same launch (Alg. 4), so a run of
+    one-iteration launches equals one launch bit for bit, back-offs included."""
+    g = game(egtlib, "full")
+    g.solver_init(variant=2, alpha=0.01)
+    backoffs = 0
+    for _ in range(200):
+        rep = g.iterate(1, variant=2, gap_every=1)
+        assert rep["iters"] == 1
+        backoffs += rep["backoffs"]
+    x1 = torch.empty((g.S[0], g.ld), device="cuda")
+    y1 = torch.empty((g.S[1], g.ld), device="cuda")
+    g.state_get(x1, y1)
+    g.solver_init(variant=2, alpha=0.01)
+    rep = g.iterate(200, variant=2, gap_every=1)
+    x2 = torch.empty_like(x1)
+    y2 = torch.empty_like(y1)
+    g.state_get(x2, y2)
+    assert rep["iters"] == 200 and rep["backoffs"] == backoffs
+    assert backoffs > 0, "the window should contain a back-off"
+    assert torch.equal(x1, x2) and torch.equal(y1, y2)
+
+
 def test_iterate_gap_matches_state_gap(egtlib):
     g = game(egtlib, "full")
     g.solver_init(variant=2, alpha=0.01)
