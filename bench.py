@@ -78,6 +78,10 @@ def parse():
     ap.add_argument("--phases", action="store_true",
                     help="instead of the iteration benchmark: device time per engine phase (egt_engine_trace) "
                          "over 300 EGT/as iterations of the full-deck, large and Libratus-menu games")
+    ap.add_argument("--served-requests", type=int, default=32,
+                    help="requests of the short served stream in the default line (0: skip)")
+    ap.add_argument("--served-rate", type=float, default=100.0, help="its arrival rate (requests/s)")
+    ap.add_argument("--no-large", action="store_true", help="skip the large endgame in the default line")
     ap.add_argument("--serve-rates", default="10,100,500", help="arrival rates (requests/s)")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests per rate")
     ap.add_argument("--serve-iters", type=int, default=200, help="iterations per server launch")
@@ -399,21 +403,96 @@ def run_batched(args, local):
     tun_s, (tun_steps, tun_launch) = timed(lambda: batched(tuned_shape))
     total = len(games) * n
     state_bytes = sum(4 * g.ld * (2 * g.S[0] + 2 * g.S[1] + 4 * g.T) for g in games)
+    alg = sum(algorithmic_bytes(g)["engine"] for g in games) * n
+    peak, peak_kind = peaks()
     for g in games:
         g.close()
+
+    def roof(sec):
+        gbs = alg / sec / 1e9
+        return {"bound": "hbm", "achieved": round(gbs, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs / peak, 5), "peak_source": peak_kind, "alg_bytes": int(alg),
+                "how": "sum over members of the engine's algorithmic bytes per iteration x iterations, "
+                       "over the pass's CUDA-event time"}
     return {"workload": f"{len(games)} mixed river endgames (20/52-card decks, raise caps 2-4, "
                         f"1-4 bet sizes), {n} EGT/as iterations each with the FP64 gap every iteration",
             "value": round(total / bat_s, 1), "unit": UNIT,
             "one_game_per_launch": round(total / seq_s, 1), "speedup": round(seq_s / bat_s, 3),
             "launches": steps, "grid": shape[1], "widest_group": shape[0],
             "state_mb": round(state_bytes / 2 ** 20, 1), "seconds": round(bat_s, 4),
+            "roofline": roof(bat_s),
             "tuned": {"value": round(total / tun_s, 1), "speedup": round(seq_s / tun_s, 3),
+                      "roofline": roof(tun_s),
                       "shape": tuned_shape, "grid": tun_launch[1], "widest_group": tun_launch[0],
                       "candidates": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in c.items()}
                                      for c in tune_rep["candidates"]],
                       "how": "egt_batch_tune over 13 launch shapes on real steps of the batch "
                              f"({max(1, n // 20)} iterations per trial), then the timed pass with the kept shape"},
             "l2": "flushed before each timed pass"}
+
+
+def run_large(args, local):
+    """The large endgame (bets {0.25, 0.5, 1, 2} x pot + all-in, raise cap 4: 508 sequences and
+    677 terminals per player) alone: EGT/as iterations per second in launches of 100 iterations
+    (FP64 residual every iteration, L2 flushed before each launch, CUDA events, 10 launches after
+    3 warm-up), the engine's roofline, and an egt_solve to 1 mbb/hand from egt_solver_init."""
+    import torch
+
+    from paper_1810_03063_b300 import egt, synth
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    g = egt.Game(synth.large(), device=local)
+    g.solver_init(variant=egt.EGT_AS, alpha=0.01)
+    for _ in range(3):
+        g.iterate(100, variant=egt.EGT_AS, gap_every=1)
+    ms = 0.0
+    for i in range(10):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.iterate(100, variant=egt.EGT_AS, gap_every=1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+    launch_ms = ms / 10
+    alg = algorithmic_bytes(g)["engine"] * 100
+    peak, peak_kind = peaks()
+    t0 = time.perf_counter()
+    rep = g.solve(variant=egt.EGT_AS, alpha=0.01, eps_mbb=1.0, max_iters=args.ttg_max_iters, gap_every=1)
+    sec = time.perf_counter() - t0
+    out = {"workload": "large river endgame: 52 cards, 1081 hands/player, bets {0.25,0.5,1,2}xpot + all-in, "
+                       "raise cap 4, stack 10, pot 1, EGT/as",
+           "S": list(g.S), "terminals": g.T, "value": round(100.0 / (launch_ms * 1e-3), 1), "unit": UNIT,
+           "us_per_iter": round(launch_ms * 10.0, 2),
+           "roofline": {"bound": "hbm", "kernel": "engine", "achieved": round(alg / (launch_ms * 1e-3) / 1e9, 2),
+                        "peak": peak, "unit": "GB/s", "frac": round(alg / (launch_ms * 1e-3) / 1e9 / peak, 5),
+                        "peak_source": peak_kind, "alg_bytes_per_launch": int(alg),
+                        "avg_launch_us": round(launch_ms * 1e3, 2)},
+           "time_to_gap": {"reached": rep["status"] == "EGT_OK", "iters": rep["iters"],
+                           "gap_mbb": round(rep["gap_mbb"], 4), "backoffs": rep["backoffs"],
+                           "seconds": round(sec, 3)}}
+    g.close()
+    return out
+
+
+def run_served_short(args, local):
+    """A short served stream for the default line: --served-requests requests arriving as a
+    Poisson stream at --served-rate through egt_server_* (continuous batching), against the same
+    requests solved one at a time with egt_solve."""
+    import argparse as _ap
+    sub = _ap.Namespace(**vars(args))
+    sub.serve_rates = str(args.served_rate)
+    sub.serve_requests = args.served_requests
+    r = run_serve(sub, local)
+    rate = r["rates"][0]
+    seq = r["one_game_per_launch"]["solves_per_s"]
+    return {"metric": "served solves/s, p50/p99 latency", "workload": r["workload"], "rate": rate["rate"],
+            "requests": rate["requests"], "reached": rate["reached"], "solves_per_s": rate["solves_per_s"],
+            "latency_p50_s": rate["latency_p50_s"], "latency_p99_s": rate["latency_p99_s"],
+            "iters_per_launch": r["iters_per_launch"], "one_game_per_launch_solves_per_s": seq,
+            "speedup": round(rate["solves_per_s"] / seq, 3) if seq else None}
 
 
 def serve_requests(n, rate, seed):
@@ -838,6 +917,8 @@ def main():
         return
     r = run_ours(args, world, rank, local)
     batched = run_batched(args, local) if args.batch_games > 0 else None
+    large = run_large(args, local) if not args.no_large and world == 1 else None
+    served = run_served_short(args, local) if args.served_requests > 0 and world == 1 else None
     if rank != 0:
         return
     # bounded oracle sample on the host cores (rank 0 at N=1 only)
@@ -874,6 +955,8 @@ def main():
         "e2e": r["e2e"],
         "time_to_gap": r["ttg"],
         "batched": batched,
+        "large": large,
+        "served": served,
         "gpu_launches": r["gpu_launches"],
         "clocks": r["clocks"],
         "backoffs_in_timed_region": r["backoffs"],

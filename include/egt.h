@@ -201,11 +201,13 @@ EGT_API egt_status egt_gap(egt_game* game, const float* x, const float* y, doubl
  * product vectors and reduction scratch live in one static device array of
  * 2 MiB that every GPU loading the library holds until exit, so games needing
  * more (2 * T * ld * 8 bytes for T terminals, plus about 9 KB) are rejected with
- * INVALID_ARG and a message giving both sizes.  The first call on a device
- * looks up the array's address with that device current: make it before any
- * stream capture.  All calls share the array (each clears what must start at
- * zero); calls that overlap on the GPU race, so serialise them (one stream).
- * The game is only read.  x, y device [S_p][ld]; gap_mbb host. */
+ * INVALID_ARG and a message giving both sizes.  The first call on each device
+ * does a one-time set-up, looking up the array's address with that device
+ * current; make that first call before any stream capture.  Every call copies
+ * the residual to the host and waits for its stream before returning.  All
+ * calls share the array (each clears what must start at zero); calls that
+ * overlap on the GPU race, so serialise them (one stream).  The game is only
+ * read.  x, y device [S_p][ld]; gap_mbb host. */
 EGT_API egt_status egt_gap_noalloc(const egt_game* game, const float* x, const float* y,
                                    double* gap_mbb, void* stream);
 
@@ -284,6 +286,15 @@ typedef struct {
  * step size (Decr writes back the accepted one).  info (host) may be NULL. */
 EGT_API egt_status egt_step(egt_game* game, int32_t player, double* tau_inout, int32_t mode,
                     egt_step_info* info, void* stream);
+
+/* The intermediate point of the last Step attempt that egt_step ran (Alg. 2,
+ * Sec. 3): x_hat = (1 - tau) x + tau x_{mu_x}(y) when x stepped, y_hat
+ * likewise when y stepped, in FP32 as the Step used it.  v_hat: device
+ * [S_p][ld] of that player (caller-owned); *player (host) receives 0 or 1.
+ * A diagnostic for checking each stage of a Step on its own.  INVALID_ARG if
+ * no egt_step ran since the last call that reuses the scratch (egt_solver_init,
+ * egt_state_set, egt_iterate, egt_solve, a batch step of this game). */
+EGT_API egt_status egt_step_point(egt_game* game, float* v_hat, int32_t* player, void* stream);
 
 /* Copy the current iterates (device [S_p][ld], NULL to skip) and mu (host [2]). */
 EGT_API egt_status egt_state_get(egt_game* game, float* x, float* y, double* mu, void* stream);

@@ -113,6 +113,29 @@ def step(P: Problem, me: int, mu_me: float, mu_other: float, v_me, v_other, tau:
     return (1.0 - tau) * mu_me, v_me_plus, v_other_plus
 
 
+def decr(P: Problem, me: int, mux: float, muy: float, x, y, tau: float, prox: str = "closed"):
+    """Alg. 4 Decr focused on player ``me``: Step at tau, halving tau while the excessive gap
+    condition fails at the new point (reading: EGV of (x^+, y^+) with mu_me^+ and the other
+    player's unchanged mu; every retry starts again from (x, y)).
+
+    Returns (mux^+, muy^+, x^+, y^+, tau, attempts) with attempts = [(tau_k, EGV_k)] in order.
+    """
+    mu_me, mu_other = (mux, muy) if me == 0 else (muy, mux)
+    v_me, v_other = (x, y) if me == 0 else (y, x)
+    attempts = []
+    while True:
+        mu_me_p, v_me_p, v_other_p = step(P, me, mu_me, mu_other, v_me, v_other, tau, prox)
+        xx, yy = (v_me_p, v_other_p) if me == 0 else (v_other_p, v_me_p)
+        mx, my = (mu_me_p, mu_other) if me == 0 else (mu_other, mu_me_p)
+        egv = P.egv(xx, yy, mx, my)
+        attempts.append((tau, egv))
+        if egv >= 0:
+            return mx, my, xx, yy, tau, attempts
+        tau *= 0.5
+        if tau < TAU_MIN:
+            raise FloatingPointError("tau underflow in Decr")
+
+
 def initial_point(P: Problem, mux: float, muy: float):
     """Alg. 1 / 3 first two lines (sign reading in the module docstring)."""
     x_omega = uniform_behavioural(P.tpx[0], P.H)
@@ -170,28 +193,19 @@ def solve(P: Problem, variant: str = "egt_as", alpha: float = 0.01, eps_mbb: flo
         else:
             me = 0 if mux > muy else 1
             tau_t = 2.0 / (t + 3) if variant == "egt" else tau
-        mu_me, mu_other = (mux, muy) if me == 0 else (muy, mux)
-        v_me, v_other = (x, y) if me == 0 else (y, x)
-        new = step(P, me, mu_me, mu_other, v_me, v_other, tau_t, prox)
         if variant == "egt_as" and replay is None:
             # Alg. 4 Decr: halve tau until the excessive gap condition holds at the new point
-            while True:
-                mu_me_p, v_me_p, v_other_p = new
-                xx, yy = (v_me_p, v_other_p) if me == 0 else (v_other_p, v_me_p)
-                mx, my = (mu_me_p, mu_other) if me == 0 else (mu_other, mu_me_p)
-                if P.egv(xx, yy, mx, my) >= 0:
-                    break
-                tau_t *= 0.5
-                backoffs += 1
-                if tau_t < TAU_MIN:
-                    raise FloatingPointError("tau underflow in Decr")
-                new = step(P, me, mu_me, mu_other, v_me, v_other, tau_t, prox)
+            mux, muy, x, y, tau_t, attempts = decr(P, me, mux, muy, x, y, tau_t, prox)
+            backoffs += len(attempts) - 1
             tau = tau_t
-        mu_me_p, v_me_p, v_other_p = new
-        if me == 0:
-            mux, x, y = mu_me_p, v_me_p, v_other_p
         else:
-            muy, y, x = mu_me_p, v_me_p, v_other_p
+            mu_me, mu_other = (mux, muy) if me == 0 else (muy, mux)
+            v_me, v_other = (x, y) if me == 0 else (y, x)
+            mu_me_p, v_me_p, v_other_p = step(P, me, mu_me, mu_other, v_me, v_other, tau_t, prox)
+            if me == 0:
+                mux, x, y = mu_me_p, v_me_p, v_other_p
+            else:
+                muy, y, x = mu_me_p, v_me_p, v_other_p
         res.schedule.append((me, tau_t))
         entry = dict(t=t, player=me, tau=tau_t, mux=mux, muy=muy, gap_mbb=gap, products=P.products)
         if log_egv:

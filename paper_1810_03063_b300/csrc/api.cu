@@ -545,6 +545,7 @@ egt_status gap_internal(egt_game* G, const float* x, const float* y, double* gap
 
 // Initial point (Alg. 1 / 3 first lines) at the given mu; leaves x, y, Ay, A^T x in slot cur.
 egt_status init_point(egt_game* G, cudaStream_t st) {
+  G->vhat_player = -1;
   const int c = G->cur;
   EGT_TRY(sbr(G, 0, nullptr, 1.0, nullptr, 0, G->tx, -1, st));          // x_omega (uniform)
   EGT_TRY(grad32(G, 1, G->tx, G->gy[c], st));                            // A^T x_omega
@@ -620,6 +621,7 @@ egt_status do_step(egt_game* G, int player, double* tau_io, int mode, egt_step_i
     ++backoffs;
     if (tau < kTauMin) return fail(EGT_ERR_TAU_UNDERFLOW, "Decr halved tau below 2^-30");
   }
+  G->vhat_player = me;
   if (accepted) {
     G->mu[me] *= (1.0 - tau);
     G->cur = 1 - G->cur;
@@ -692,6 +694,7 @@ namespace egtapi {
 // The game's buffers as the device-resident driver sees them.
 EngineBufs engine_bufs(const egt_game* G, egt_iter_log* log_dev, int log_cap) {
   EngineBufs b{};
+  G->vhat_player = -1;           // the driver reuses the Step scratch
   for (int i = 0; i < 2; ++i) {
     b.x[i] = G->x[i];
     b.y[i] = G->y[i];
@@ -1055,6 +1058,20 @@ egt_status egt_step(egt_game* G, int32_t player, double* tau_inout, int32_t mode
   return do_step(G, player, tau_inout, mode, info, S(stream));
 }
 
+egt_status egt_step_point(egt_game* G, float* v_hat, int32_t* player, void* stream) {
+  if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
+  if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
+  if (!player) return fail(EGT_ERR_INVALID_ARG, "player is NULL");
+  EGT_TRY(check_ptr(v_hat, "v_hat"));
+  const int me = G->vhat_player;
+  if (me != 0 && me != 1) return fail(EGT_ERR_INVALID_ARG, "no egt_step since the scratch was last reused");
+  DeviceGuard guard(G->device);
+  CUDA_TRY(cudaMemcpyAsync(v_hat, me == 0 ? G->tx : G->ty, vec_elems(G, me) * 4, cudaMemcpyDeviceToDevice,
+                           S(stream)));
+  *player = me;
+  return EGT_OK;
+}
+
 egt_status egt_state_get(egt_game* G, float* x, float* y, double* mu, void* stream) {
   if (!G) return fail(EGT_ERR_INVALID_ARG, "game is NULL");
   if (G->host_only) return fail(EGT_ERR_INVALID_ARG, "host-only game (device -1) has no device state");
@@ -1083,6 +1100,7 @@ egt_status egt_state_set(egt_game* G, const float* x, const float* y, const doub
   CUDA_TRY(cudaMemcpyAsync(G->y[c], y, vec_elems(G, 1) * 4, cudaMemcpyDeviceToDevice, st));
   G->mu[0] = mu[0];
   G->mu[1] = mu[1];
+  G->vhat_player = -1;
   EGT_TRY(grad32(G, 0, G->y[c], G->gx[c], st));
   EGT_TRY(grad32(G, 1, G->x[c], G->gy[c], st));
   G->initialised = true;

@@ -76,6 +76,9 @@ struct egt_game {
   // scratch tx [max(S0, T)][ld], ty [max(S1, T)][ld]
   float *x[2], *y[2], *gx[2], *gy[2], *tx, *ty;
   int cur = 0;                   // index of the current iterate / cached products
+  // player whose Step intermediate point (x_hat in tx / y_hat in ty) the last egt_step left in
+  // the scratch; -1 once another call reused it (the device-resident driver writes it too)
+  mutable int vhat_player = -1;
   double* g64[2] = {nullptr, nullptr};   // FP64 products for the gap (contributions)
   double* pub = nullptr;         // [T][ld] contributions of the public egt_grad / egt_grad_f64
   double* partials = nullptr;    // per-CTA value partials

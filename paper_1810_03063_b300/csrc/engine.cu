@@ -834,10 +834,8 @@ cudaError_t engine_launch(const EngineJob* jobs_dev, const EngineGroup* plan_dev
 }
 
 int engine_smem_limit(bool batch) {
-  static int limit_one = 0, limit_batch = 0;
-  if (limit_one == 0) limit_one = opt_in_dynamic_smem((const void*)engine_kernel_one);
-  if (limit_batch == 0) limit_batch = opt_in_dynamic_smem((const void*)engine_kernel);
-  return batch ? limit_batch : limit_one;
+  return batch ? opt_in_dynamic_smem((const void*)engine_kernel)
+               : opt_in_dynamic_smem((const void*)engine_kernel_one);
 }
 
 int engine_max_grid(size_t smem, bool batch) {

@@ -45,8 +45,7 @@ __global__ void __launch_bounds__(256) combine_kernel(DevGame g, int player, con
 
 template <typename TIn>
 void launch_t(const DevGame& g, int player, const TIn* in, float* c32, double* c64, cudaStream_t st) {
-  static int limit = 0;   // one process-wide opt-in per instantiation
-  if (limit == 0) limit = opt_in_dynamic_smem((const void*)term_kernel<TIn>);
+  opt_in_dynamic_smem((const void*)term_kernel<TIn>);   // once per device
   const int T = player ? g.terms[1].n : g.terms[0].n;
   if (T == 0) return;
   term_kernel<TIn><<<T, kItemThreads, grad_smem_bytes(g), st>>>(g, player, in, c32, c64);

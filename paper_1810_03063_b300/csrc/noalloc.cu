@@ -14,7 +14,8 @@
 // array's device address with cudaGetSymbolAddress (in host code the array's
 // name is only a host-side stand-in, never a device address) and caches it.
 // That first call on each device should therefore come before any stream
-// capture.  Every call shares the one array and it keeps the last call's
+// capture.  Every call ends by copying the residual to the host and waiting
+// for its stream.  Every call shares the one array and it keeps the last call's
 // contents: each call clears the parts that must start at zero (the value
 // slots and the arrival counter of the reductions), and calls whose work
 // overlaps on the GPU (different streams, no ordering) race on it.

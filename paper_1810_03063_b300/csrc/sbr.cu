@@ -2,6 +2,10 @@
 // 16 hands running the shared bodies of sbr_impl.cuh (Sec. 5 recursion).  The
 // value summed over hands and root simplexes is reduced in FP64: per-CTA
 // partials, the last CTA to finish adds them in a fixed order (deterministic).
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "egt_internal.cuh"
 #include "sbr_impl.cuh"
 
@@ -72,30 +76,39 @@ size_t br_smem_bytes(const DevGame& g, int player) {
   return tpx_tab_bytes(g, player) + br_item_smem(g, player);
 }
 
+// The opt-in is a property of (kernel, device): cudaFuncSetAttribute acts on the
+// device current at the call.  Successful opt-ins are remembered per pair under a
+// lock (host threads may launch concurrently); a failed one is retried next time.
 int opt_in_dynamic_smem(const void* kernel) {
-  int dev = 0, optin = 0;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(kernel, dev);
+  const auto it = done.find(key);
+  if (it != done.end()) return it->second;
+  int optin = 0;
   cudaFuncAttributes fa{};
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
       cudaFuncGetAttributes(&fa, kernel) != cudaSuccess)
     return -1;
   const int limit = optin - (int)fa.sharedSizeBytes;
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess)
     return -1;
+  done[key] = limit;
   return limit;
 }
 
 void launch_sbr(const DevGame& g, int player, const SbrArgs& a, cudaStream_t st) {
-  static int limit = 0;
-  if (limit == 0) limit = opt_in_dynamic_smem((const void*)sbr_kernel);
+  opt_in_dynamic_smem((const void*)sbr_kernel);
   const int grid = g.ld / kSbrHands;
   sbr_kernel<<<grid, kItemThreads, sbr_smem_bytes(g, player), st>>>(g, player, a);
 }
 
 void launch_br64(const DevGame& g, int player, const double* gv, bool contrib, double sign, double* value_dev,
                  double* partials, unsigned int* counter, cudaStream_t st) {
-  static int limit = 0;
-  if (limit == 0) limit = opt_in_dynamic_smem((const void*)br64_kernel);
+  opt_in_dynamic_smem((const void*)br64_kernel);
   const int grid = g.ld / kSbrHands;
   br64_kernel<<<grid, kItemThreads, br_smem_bytes(g, player), st>>>(g, player, gv, contrib, sign,
                                                                      value_dev, partials, counter);

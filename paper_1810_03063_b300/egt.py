@@ -153,6 +153,7 @@ _SIGS = {
     "egt_gap": [_vp, _vp, _vp, C.POINTER(_f64), _vp],
     "egt_solver_init": [_vp, C.POINTER(SolveOpts), _vp],
     "egt_step": [_vp, _i32, C.POINTER(_f64), _i32, C.POINTER(StepInfo), _vp],
+    "egt_step_point": [_vp, _vp, C.POINTER(_i32), _vp],
     "egt_state_get": [_vp, _vp, _vp, _vp, _vp],
     "egt_state_set": [_vp, _vp, _vp, _vp, _vp],
     "egt_checkpoint_get": [_vp, _vp, _vp, C.POINTER(Checkpoint), _vp],
@@ -397,6 +398,13 @@ class Game:
         return dict(player=info.player, accepted=bool(info.accepted), backoffs=info.backoffs,
                     products=info.products, tau=info.tau, egv=info.egv, mu=(info.mu[0], info.mu[1]))
 
+    def step_point(self, v_hat, stream=None):
+        """Copy the last egt_step attempt's intermediate point (x_hat or y_hat) into v_hat;
+        returns the player it belongs to (egt_step_point)."""
+        p = C.c_int32()
+        _check(lib.egt_step_point(self._h, _ptr(v_hat), C.byref(p), _stream(stream)))
+        return p.value
+
     def state_get(self, x=None, y=None, stream=None):
         mu = (C.c_double * 2)()
         _check(lib.egt_state_get(self._h, _ptr(x), _ptr(y), C.cast(mu, C.c_void_p), _stream(stream)))
@@ -605,9 +613,9 @@ class Server:
         return lib.egt_server_clock(self._h)
 
     def submit(self, spec, arrival=-1.0, variant=EGT_AS, alpha=0.01, eps_mbb=1.0, max_iters=20000,
-               gap_every=1):
+               gap_every=1, mu0=None):
         d, keep = _desc(spec)
-        o, _, _ = Game._opts(variant=variant, alpha=alpha, eps_mbb=eps_mbb, max_iters=max_iters,
+        o, _, _ = Game._opts(variant=variant, alpha=alpha, mu0=mu0, eps_mbb=eps_mbb, max_iters=max_iters,
                              gap_every=gap_every)
         rid = C.c_int64()
         _check(lib.egt_server_submit(self._h, C.byref(d), C.byref(o), float(arrival), C.byref(rid)))

@@ -30,7 +30,7 @@ def test_reference_arm_line():
 @pytest.mark.gpu
 def test_gpu_arm_line_has_every_key():
     r = subprocess.run([sys.executable, "bench.py", "--steps", "3", "--warmup", "3", "--cpu-seconds", "1",
-                        "--batch-games", "4", "--batch-iters", "20"],
+                        "--batch-games", "4", "--batch-iters", "20", "--served-requests", "3"],
                        cwd=ROOT, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     d = last_json_line(r.stdout)
@@ -48,3 +48,8 @@ def test_gpu_arm_line_has_every_key():
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
     assert d["batched"]["value"] > 0 and d["batched"]["tuned"]["shape"]["share"] in range(5)
+    assert 0 < d["batched"]["roofline"]["frac"] < 1.5
+    assert d["large"]["value"] > 0 and 0 < d["large"]["roofline"]["frac"] < 1.5
+    assert d["large"]["time_to_gap"]["iters"] > 0
+    sv = d["served"]
+    assert sv["requests"] == 3 and sv["solves_per_s"] > 0 and sv["latency_p99_s"] >= sv["latency_p50_s"] > 0

@@ -6,9 +6,13 @@ member must end bit for bit where egt_solve takes the same game alone: same
 iterates, mu, tau, residual and iteration count.  Each member stops at its own
 target or iteration budget with its own status.
 """
+import numpy as np
 import pytest
 
+from oracle import egt as OE
+from oracle import payoff
 from paper_1810_03063_b300 import synth
+from tests import bounds as B
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -297,4 +301,53 @@ def test_waves_keep_results(egtlib):
         xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, n, 1)
         xb, yb, mu = member_state(egtlib, g)
         assert torch.equal(xb, xs) and torch.equal(yb, ys), sp.name
+    b.close()
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+ORACLE_MIX = {"tiny": synth.tiny, "full": lambda: synth.full_deck(seed=synth.BASE_SEED + 3),
+              "libratus20": lambda: synth.libratus(n_cards=20, stack=2.0), "large": synth.large}
+
+
+@pytest.mark.parametrize("variant, n_iters", [("egt", 100), ("egt_as", 30)])
+def test_batch_members_match_the_oracle(egtlib, variant, n_iters):
+    """A mixed batch (tiny, full deck, 20-card Libratus menus, large) runs in batch launches of
+    unequal length; every member's iterates match the FP64 oracle's solve of the same game at
+    rel-L_inf 1e-5, mu to 1e-14 and the FP64 residual of its state to 1e-3: practical EGT for
+    100 iterations, and free-running EGT/as for 30 iterations, where its smoothing is still well
+    conditioned; there the iterate tolerance is 1e-5 or 3x the drift of the oracle's own run
+    under FP32-sized noise on the same decisions, whichever is larger (that drift reaches a few
+    1e-6 on the full deck by then, as in the solo tau-replay test)."""
+    code = {"egt": egtlib.PRACTICAL, "egt_as": egtlib.EGT_AS}[variant]
+    b = egtlib.Batch(0)
+    members = []
+    for name, make in ORACLE_MIX.items():
+        spec = make()
+        og = payoff.make_game(spec)
+        P = OE.Problem(og)
+        mu0 = ((0.05 if variant == "egt" else 0.01) * P.theory_mu(),) * 2
+        g = egtlib.Game(spec, device=0)
+        g.solver_init(variant=code, mu0=mu0)
+        members.append((name, og, P, g, mu0, b.add(g, variant=code, eps_mbb=0.0, max_iters=n_iters,
+                                                    gap_every=n_iters)))
+    b.run(n_iters=17)
+    for name, og, P, g, mu0, slot in members:
+        r = OE.solve(P, variant=variant, eps_mbb=0.0, max_iters=n_iters, mu0=mu0, gap_every=10 ** 6)
+        tx = ty = 1e-5
+        if variant == "egt_as":
+            runs = [B.fp32_noise_floor(P, mu0, r.schedule, seed) for seed in range(3)]
+            tx = max(tx, 3 * max(rel_linf(f.x, r.x) for f in runs))
+            ty = max(ty, 3 * max(rel_linf(f.y, r.y) for f in runs))
+        m = b.member(slot)
+        assert m["iters"] == n_iters
+        xb, yb, mu = member_state(egtlib, g)
+        xh, yh = g.unpack(xb.double().cpu().numpy()), g.unpack(yb.double().cpu().numpy())
+        assert rel_linf(xh, r.x) <= tx, (name, rel_linf(xh, r.x), tx)
+        assert rel_linf(yh, r.y) <= ty, (name, rel_linf(yh, r.y), ty)
+        assert np.isclose(mu[0], r.mux, rtol=1e-14) and np.isclose(mu[1], r.muy, rtol=1e-14), name
+        ref_gap = P.to_mbb(P.eps_sad(r.x, r.y))
+        assert abs(g.state_gap() - ref_gap) <= 1e-3 * ref_gap, name
     b.close()

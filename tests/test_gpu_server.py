@@ -111,3 +111,39 @@ def test_unreachable_target_finishes_not_converged(egtlib):
     r = srv.result(rid)
     assert r["status"] == "EGT_ERR_NOT_CONVERGED" and r["iters"] == 120
     srv.close()
+
+
+def test_served_requests_match_the_oracle(egtlib):
+    """Requests served in a mix (a tiny and a full-deck game under practical EGT for 100
+    iterations, admitted while an EGT/as request of another game is running) end where the
+    FP64 oracle's solve of the same game ends: rel-L_inf 1e-5, mu to 1e-14, and the reported
+    residual equal to the oracle's eps_sad of the returned iterates (1e-9) and within 1e-3 of
+    the oracle trajectory's."""
+    from oracle import egt as OE
+    from oracle import payoff
+
+    srv = egtlib.Server(0, iters_per_step=23)
+    srv.submit(synth.tiny(seed=synth.BASE_SEED + 4), eps_mbb=20.0, max_iters=5000)
+    srv.step()
+    reqs = []
+    for spec in (synth.tiny(), synth.full_deck(seed=synth.BASE_SEED + 6)):
+        og = payoff.make_game(spec)
+        P = OE.Problem(og)
+        mu0 = (0.05 * P.theory_mu(),) * 2
+        rid = srv.submit(spec, variant=egtlib.PRACTICAL, mu0=mu0, eps_mbb=0.0, max_iters=100, gap_every=1)
+        reqs.append((rid, spec, og, P, mu0))
+    drain(srv)
+    for rid, spec, og, P, mu0 in reqs:
+        r = srv.result(rid)
+        assert r["iters"] == 100
+        g = egtlib.Game(spec, device=-1)                       # host-only: the hand order
+        xh, yh = g.unpack(r["x"].astype(np.float64)), g.unpack(r["y"].astype(np.float64))
+        ref = OE.solve(P, variant="egt", eps_mbb=0.0, max_iters=100, mu0=mu0, gap_every=10 ** 6)
+        rel = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
+        assert rel(xh, ref.x) <= 1e-5 and rel(yh, ref.y) <= 1e-5, (spec.name, rel(xh, ref.x), rel(yh, ref.y))
+        assert np.isclose(r["mu"][0], ref.mux, rtol=1e-14) and np.isclose(r["mu"][1], ref.muy, rtol=1e-14)
+        own = P.to_mbb(P.eps_sad(xh, yh))
+        assert abs(r["gap_mbb"] - own) <= 1e-9 * own
+        ref_gap = P.to_mbb(P.eps_sad(ref.x, ref.y))
+        assert abs(r["gap_mbb"] - ref_gap) <= 1e-3 * ref_gap
+    srv.close()
