@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--ops", action="store_true",
                     help="instead of the iteration benchmark: the C-ABI hot-path operations one call at a time "
                          "(egt_grad, egt_grad_f64, egt_smoothed_br, egt_best_response_f64, egt_gap)")
+    ap.add_argument("--cpu-configs", action="store_true",
+                    help="CPU side of every config: the FP64 oracle (bounded sample) and the C++/OpenMP "
+                         "comparator (iter/s on 1 thread and all cores, time to 1 mbb/hand)")
     ap.add_argument("--phases", action="store_true",
                     help="instead of the iteration benchmark: device time per engine phase (egt_engine_trace) "
                          "over 300 EGT/as iterations of the full-deck, large and Libratus-menu games")
@@ -82,6 +85,7 @@ def parse():
                     help="requests of the short served stream in the default line (0: skip)")
     ap.add_argument("--served-rate", type=float, default=100.0, help="its arrival rate (requests/s)")
     ap.add_argument("--no-large", action="store_true", help="skip the large endgame in the default line")
+    ap.add_argument("--no-cpu-fast", action="store_true", help="skip the C++/OpenMP CPU comparator")
     ap.add_argument("--serve-rates", default="10,100,500", help="arrival rates (requests/s)")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests per rate")
     ap.add_argument("--serve-iters", type=int, default=200, help="iterations per server launch")
@@ -851,6 +855,64 @@ def oracle_iterations(seconds, max_iters=None, seed=None):
     return n, time.perf_counter() - t0, step_times
 
 
+def run_cpu_fast(args):
+    """The FP64 multi-core CPU comparator (libegt_cpu: the same EGT/as on the structured
+    O(T H) products, C++ and OpenMP on every host core) on the bench's game: iterations per
+    second over a 200-iteration run, and a solve to 1 mbb/hand from the initial point."""
+    from paper_1810_03063_b300 import synth
+    from paper_1810_03063_b300.egt_cpu import CpuGame
+
+    g = CpuGame(synth.full_deck(seed=synth.BASE_SEED))
+    g.solve(alpha=0.01, eps_mbb=0.0, max_iters=5, gap_every=1)               # warm-up
+    rate = g.solve(alpha=0.01, eps_mbb=0.0, max_iters=200, gap_every=1)
+    ttg = g.solve(alpha=0.01, eps_mbb=1.0, max_iters=args.ttg_max_iters, gap_every=1)
+    g.close()
+    return {"kind": "FP64 C++/OpenMP comparator (structured O(T H) products)", "value": round(200 / rate["seconds"], 2),
+            "unit": UNIT, "cores": rate["threads"],
+            "sample": "200 EGT/as iterations (+ FP64 gap each) of the same game from the initial point",
+            "time_to_gap": {"reached": ttg["status"] == "EGT_OK", "iters": ttg["iters"],
+                            "gap_mbb": round(ttg["gap_mbb"], 4), "backoffs": ttg["backoffs"],
+                            "seconds": round(ttg["seconds"], 3)}}
+
+
+def run_cpu_configs(args):
+    """Each synthetic endgame on the host: the FP64 oracle's EGT/as iterations per second on a
+    bounded sample (about 10 s, the numpy BLAS on every core) and the C++/OpenMP comparator's
+    on 1 thread and on every core (200 iterations), and the comparator's time to 1 mbb/hand."""
+    from oracle import egt as OE
+    from oracle import payoff
+    from paper_1810_03063_b300 import synth
+    from paper_1810_03063_b300.egt_cpu import CpuGame
+
+    out = []
+    for name, spec in [("tiny (20 cards, 105 hands)", synth.tiny()),
+                       ("full deck (52 cards, 1081 hands)", synth.full_deck()),
+                       ("large (bets {0.25,0.5,1,2}, cap 4)", synth.large())]:
+        P = OE.Problem(payoff.make_game(spec))
+        mu = 0.01 * P.theory_mu()
+        t0 = time.perf_counter()
+        r = OE.solve(P, variant="egt_as", eps_mbb=0.0, max_iters=1, mu0=(mu, mu), gap_every=1)
+        per = time.perf_counter() - t0
+        n = max(2, min(2000, int(10.0 / max(per, 1e-3))))
+        t0 = time.perf_counter()
+        r = OE.solve(P, variant="egt_as", eps_mbb=0.0, max_iters=n, mu0=(mu, mu), gap_every=1)
+        o_rate = r.iters / (time.perf_counter() - t0)
+        g = CpuGame(spec)
+        g.solve(alpha=0.01, eps_mbb=0.0, max_iters=5, gap_every=1)
+        one = g.solve(alpha=0.01, eps_mbb=0.0, max_iters=200, gap_every=1, threads=1)
+        allc = g.solve(alpha=0.01, eps_mbb=0.0, max_iters=200, gap_every=1, threads=0)
+        ttg = g.solve(alpha=0.01, eps_mbb=1.0, max_iters=args.ttg_max_iters, gap_every=1, threads=0)
+        g.close()
+        out.append({"game": name, "oracle_iter_per_s": round(o_rate, 3), "oracle_sample_iters": r.iters,
+                    "oracle_threads": threads_used(),
+                    "comparator_iter_per_s_1_thread": round(200 / one["seconds"], 1),
+                    "comparator_iter_per_s_all": round(200 / allc["seconds"], 1), "comparator_threads": allc["threads"],
+                    "comparator_time_to_1mbb_s": round(ttg["seconds"], 3), "comparator_iters_to_1mbb": ttg["iters"],
+                    "comparator_status": ttg["status"]})
+    return {"study": "CPU side of each config (FP64 oracle, FP64 C++/OpenMP comparator)", "data": "synthetic",
+            "host_cores": os.cpu_count(), "games": out}
+
+
 def threads_used():
     try:
         from threadpoolctl import threadpool_info
@@ -905,6 +967,11 @@ def main():
         if rank == 0:
             print(json.dumps(out))
         return
+    if args.cpu_configs:
+        out = run_cpu_configs(args)
+        if rank == 0:
+            print(json.dumps(out))
+        return
     if args.phases:
         out = run_phases(args, local)
         if rank == 0:
@@ -927,6 +994,7 @@ def main():
         n, sec, _ = oracle_iterations(args.cpu_seconds)
         cpu = {"value": round(n / sec, 4), "unit": UNIT, "cores": threads_used(), "kind": "oracle",
                "sample": f"first {n} EGT/as iterations (+ FP64 gap each) of the same game, {sec:.1f} s"}
+    cpu_fast = run_cpu_fast(args) if world == 1 and not args.no_cpu_fast else None
     value = r["total_iters"] / (r["ms"] * 1e-3)
     g = r["g"]
     out = {
@@ -952,6 +1020,7 @@ def main():
                      "avg_launch_us": round(r["avg_ms"] * 1e3, 3)},
         "kernels": r["kernels"],
         "cpu_baseline": cpu,
+        "cpu_fast": cpu_fast,
         "e2e": r["e2e"],
         "time_to_gap": r["ttg"],
         "batched": batched,

@@ -1,8 +1,9 @@
-"""Build libegt.so in-tree with nvcc for sm_103a (B300).
+"""Build libegt.so in-tree with nvcc for sm_103a (B300), and libegt_cpu.so (the
+FP64 multi-core CPU comparator) with g++ and OpenMP.
 
 Usage: ``python -m paper_1810_03063_b300.build [--force]``.  Objects go to
-``_build/`` at the repository root; the shared library is written next to
-this file so that it travels with the source tree.
+``_build/`` at the repository root; the shared libraries are written next to
+this file so that they travel with the source tree.
 """
 from __future__ import annotations
 
@@ -40,6 +41,25 @@ def headers():
     return hs
 
 
+CPU_LIB = os.path.join(PKG, "libegt_cpu.so")
+CPU_SRC = [os.path.join(PKG, "cpu", "egt_cpu.cpp"), os.path.join(CSRC, "tree.cpp")]
+CPU_HDR = [os.path.join(INCLUDE, "egt.h"), os.path.join(INCLUDE, "egt_cpu.h"), os.path.join(CSRC, "tree.hpp")]
+
+
+def build_cpu(force: bool = False) -> str:
+    """The FP64 multi-core CPU comparator (include/egt_cpu.h): g++ with OpenMP, x86-64-v3."""
+    newest = max(os.path.getmtime(f) for f in CPU_SRC + CPU_HDR)
+    if not force and os.path.exists(CPU_LIB) and os.path.getmtime(CPU_LIB) >= newest:
+        return CPU_LIB
+    cxx = os.environ.get("CXX") or shutil.which("g++") or "g++"
+    cmd = [cxx, "-O3", "-march=x86-64-v3", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-fvisibility=hidden",
+           "-I", INCLUDE, *CPU_SRC, "-o", CPU_LIB]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"g++ failed on the CPU comparator:\n{res.stdout}\n{res.stderr}")
+    return CPU_LIB
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
@@ -59,6 +79,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{res.stdout}\n{res.stderr}")
         if verbose:
             sys.stderr.write(res.stderr)
+    build_cpu(force)
     if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs]
         res = subprocess.run(cmd, capture_output=True, text=True)

@@ -261,6 +261,23 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
       tcoef[p][e] = (float)c;
     }
   }
+  // merged product items: the showdown and fold terminals of each opponent column
+  std::vector<int> tcol[2];
+  for (int p = 0; p < 2; ++p) {
+    const int S_opp = C.tpx[1 - p].S;
+    std::vector<int> at(S_opp, -1);
+    const int n = (int)C.term.size();
+    for (int e = 0; e < n; ++e) {
+      const int o = topp[p][e];
+      if (at[o] < 0) {
+        at[o] = (int)tcol[p].size() / 4;
+        tcol[p].insert(tcol[p].end(), {-1, -1, o, 0});
+      }
+      int& slot = tcol[p][4 * at[o] + (tkind[p][e] ? 0 : 1)];
+      if (slot >= 0) return fail(EGT_ERR_INVALID_ARG, "internal: two terminals of one kind read one column");
+      slot = e;
+    }
+  }
 
   // sizes of the arena
   std::vector<float> rf[2], rzf[2];
@@ -290,7 +307,8 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
     bytes += ld * (2 * sizeof(float) + 2 * sizeof(double));
     const Treeplex& T = C.tpx[p];
     bytes += (4 * T.J + T.L + 1 + 2 * T.S + 1 + T.child_idx.size()) * sizeof(int) + T.J * (sizeof(double) + sizeof(float));
-    bytes += (tptr[p].size() + 2 * topp[p].size()) * sizeof(int) + tcoef[p].size() * (sizeof(float) + sizeof(double));
+    bytes += (tptr[p].size() + 2 * topp[p].size() + tcol[p].size()) * sizeof(int) +
+             tcoef[p].size() * (sizeof(float) + sizeof(double));
   }
   bytes += 64 * 256;   // alignment slack
   G->device_bytes = bytes + state_bytes(G);
@@ -353,6 +371,8 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
     tm.kind = (const int*)put(tkind[p].data(), tkind[p].size() * 4);
     tm.coef = (const float*)put(tcoef[p].data(), tcoef[p].size() * 4);
     tm.coef64 = (const double*)put(tcoef64[p].data(), tcoef64[p].size() * 8);
+    tm.n_col = (int)tcol[p].size() / 4;
+    tm.col = (const int4*)put(tcol[p].data(), tcol[p].size() * 4);
   }
   const size_t used = reinterpret_cast<uintptr_t>(hp) - base_h;
   if (overflow || used > bytes) return fail(EGT_ERR_INVALID_ARG, "internal: table arena overflow");

@@ -40,6 +40,11 @@ struct DevTerms {
   const int* kind;         // [n] 0 fold, 1 showdown
   const float* coef;       // [n] signed: fold payoff to player 2, showdown +-stake
   const double* coef64;
+  // Product items with merged terminals: one per opponent column the terminals read,
+  // (showdown terminal, fold terminal, the column, 0), -1 where the column has no
+  // terminal of a kind (every column has at most one of each)
+  int n_col;
+  const int4* col;         // [n_col]
 };
 
 struct DevGame {

@@ -281,24 +281,55 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, Grp gr
   });
 }
 
+// Product items of a phase of `player`: one per terminal when the group has a CTA for
+// every terminal (the phase then lasts one item), else one per opponent column, whose
+// showdown and fold terminals share the column's sums (less work per phase).  The
+// results are the same bits either way (the sums are exact).
+__device__ __forceinline__ int prod_items(const DevTerms& tm, Grp gr, bool& merged) {
+  merged = gr.size < tm.n;
+  return merged ? tm.n_col : tm.n;
+}
+
 // One product phase: every terminal of `player`'s grouping; c64 (FP64 contributions
 // for the residual) may be NULL.  With pairs (the job allows them and the group has at
-// least two terminals per CTA) each warp half takes its own terminals.
+// least two items per CTA) each warp half takes its own items.
+// kProd selects the product item body: 0 term_item_whole (one terminal per item),
+// 1 prod_item with one terminal per item, 2 prod_item, merged when the group is small.
+template <int kProd>
+__device__ __forceinline__ void one_prod_item(const DevGame& g, const GradTab& tb, int player, int item,
+                                              bool merged, const float* in, float* c32, double* c64,
+                                              unsigned char* sm) {
+  if constexpr (kProd == 0) term_item_whole<float>(g, tb, player, item, in, c32, c64, sm);
+  else prod_item<float>(g, tb, player, item, kProd == 2 && merged, in, c32, c64, sm);
+}
+
+template <int kProd>
 __device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, Grp gr, bool pair_ok, int player,
                                          const float* in, float* c32, double* c64, unsigned char* sm) {
-  const int T = player ? g.terms[1].n : g.terms[0].n;
-  if (!(pair_ok && 2 * gr.size <= T)) {
-    for (int item = gr.rank; item < T; item += gr.size)
-      term_item<float>(g, tb.grad, player, item, in, c32, c64, sm);
+  const DevTerms tm = player ? g.terms[1] : g.terms[0];
+  bool merged;
+  int n = prod_items(tm, gr, merged);
+  if (kProd != 2 && merged) {
+    merged = false;
+    n = tm.n;
+  }
+  if (!(pair_ok && 2 * gr.size <= n)) {
+    for (int item = gr.rank; item < n; item += gr.size)
+      one_prod_item<kProd>(g, tb.grad, player, item, merged, in, c32, c64, sm);
     return;
   }
   constexpr int kHalf = kItemThreads / 64;
   const int half = (int)(threadIdx.x >> 5) >= kHalf ? 1 : 0;
   unsigned char* hs = sm + half * gradimpl::align16(grad_item_smem(g));
-  for (int base = 2 * gr.rank; base < T; base += 2 * gr.size)
-    if (base + half < T)
-      term_item<float, kItemThreads / 2>(g, tb.grad, player, base + half, in, c32, c64, hs, half * kHalf,
-                                         1 + half);
+  for (int base = 2 * gr.rank; base < n; base += 2 * gr.size)
+    if (base + half < n) {
+      if constexpr (kProd == 0)
+        term_item_whole<float, kItemThreads / 2>(g, tb.grad, player, base + half, in, c32, c64, hs,
+                                                 half * kHalf, 1 + half);
+      else
+        prod_item<float, kItemThreads / 2>(g, tb.grad, player, base + half, kProd == 2 && merged, in, c32,
+                                           c64, hs, half * kHalf, 1 + half);
+    }
 }
 
 // Item `item` of player p's FP64 best response of the residual (player 0: min over x of
@@ -512,6 +543,7 @@ __device__ __forceinline__ void settle(Solver& S, Solver& S2, EngineCtl* ctl, co
 // barrier.  Everything the new attempt writes before that barrier is scratch (the
 // v_hat buffer and the other player's gradient at v_hat), so a rejected attempt is
 // retried from unchanged iterates, and a stop discards only scratch.
+template <int kProd>
 __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b, EngineCtl* ctl, Grp gr,
                                            int pair_bits, unsigned long long expected,
                                            unsigned long long limit_ns, unsigned char* smem_all) {
@@ -629,7 +661,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
       if (!phase_end(bar, bk, clk, 0, clock_cta)) return;
     }
     phase_cut(clk, 8, clock_cta);
-    run_grad(g, tb, gr, pair_terms, ot, t_me, t_ot, nullptr, sm);   // the other's loss gradient at v_hat
+    run_grad<kProd>(g, tb, gr, pair_terms, ot, t_me, t_ot, nullptr, sm);   // the other's loss gradient at v_hat
     {
       int code = kGo;
       if (!grid_sync_verdict(bar, bk, clk, clock_cta, &ctl->verdict, ep, &code)) return;
@@ -652,7 +684,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
     // other_+ = (1 - tau) other + tau other_mu(v_hat)
     run_sbr(g, tb, gr, pair_ok, ot, t_ot, sc.mu_ot, v_ot, sc.tau, v_ot_n, nullptr, sm);
     if (!phase_end(bar, bk, clk, 2, clock_cta)) return;
-    run_grad(g, tb, gr, pair_terms, m, v_ot_n, g_me_n, g64_me, sm);   // my loss gradient at other_+
+    run_grad<kProd>(g, tb, gr, pair_terms, m, v_ot_n, g_me_n, g64_me, sm);   // my loss gradient at other_+
     if (!phase_end(bar, bk, clk, 3, clock_cta)) return;
     // v_tilde = v_{(1-tau) mu}(other_+), v_+ = (1 - tau) v + tau v_tilde; value: my EGV part.
     // When the residual is due, my FP64 best response (on the FP64 product of the last
@@ -680,14 +712,20 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
     }
     if (!phase_end(bar, bk, clk, 4, clock_cta)) return;
     if (sp != 1) {
-      run_grad(g, tb, gr, pair_terms, ot, v_me_n, g_ot_n, g64_ot, sm);   // the other's at v_+
+      run_grad<kProd>(g, tb, gr, pair_terms, ot, v_me_n, g_ot_n, g64_ot, sm);   // the other's at v_+
     } else {
       // the other's loss gradient at v_+, and the next v_hat (the same player steps again)
-      const int T = ot ? g.terms[1].n : g.terms[0].n;
+      const DevTerms tmo = ot ? g.terms[1] : g.terms[0];
+      bool merged;
+      int T = prod_items(tmo, gr, merged);
+      if (kProd != 2 && merged) {
+        merged = false;
+        T = tmo.n;
+      }
       const int n_items = T + NB;
       for (int item = gr.rank; item < n_items; item += gr.size) {
         if (item < T) {
-          term_item<float>(g, tb.grad, ot, item, v_me_n, g_ot_n, g64_ot, sm);
+          one_prod_item<kProd>(g, tb.grad, ot, item, merged, v_me_n, g_ot_n, g64_ot, sm);
         } else {
           SbrItemArgs a;
           a.g = g_me_n;
@@ -764,11 +802,16 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
   }
 }
 
+#ifndef EGT_ONE_GAME_PROD
+#define EGT_ONE_GAME_PROD 2
+#endif
+constexpr int kOneGameProd = EGT_ONE_GAME_PROD;
+
 // One job on the whole grid, its description in the kernel parameters.
 __global__ void __launch_bounds__(kItemThreads, 1)
     engine_kernel_one(EngineJob job, unsigned int extra, unsigned long long limit_ns) {
   extern __shared__ __align__(16) unsigned char smem_all[];
-  engine_job(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x}, job.pair,
+  engine_job<kOneGameProd>(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x}, job.pair,
              (unsigned long long)gridDim.x + extra, limit_ns, smem_all);
 }
 
@@ -794,7 +837,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
       for (int i = threadIdx.x; i < (int)(sizeof(EngineJob) / 8); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    engine_job(job_s.g, job_s.b, job_s.ctl, gr, job_s.pair, (unsigned long long)pg.size + extra, limit_ns,
+    engine_job<2>(job_s.g, job_s.b, job_s.ctl, gr, job_s.pair, (unsigned long long)pg.size + extra, limit_ns,
                smem_all);
   }
 }

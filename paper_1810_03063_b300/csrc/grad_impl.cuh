@@ -433,15 +433,212 @@ __device__ inline GradTab stage_grad_tab(const DevGame& g, unsigned char* dst) {
   return t;
 }
 
-// Contribution of terminal e (index in player `player`'s grouping, DevTerms) to that
-// player's product: c32[e][h] and / or c64[e][h] (either may be NULL) = coef_b x the
-// card-removal / strength sum of w = r_opp (.) in[sigma_opp(b)], without the r_me / Z
-// factor.  Run by kThreads threads: the whole CTA, or the warp half starting at warp
-// first_warp with named barrier `bar`; the result does not depend on which (the sums
-// are exact).  `in` is read through L2 (it may have been written earlier in the same
-// launch by other CTAs).
+// Product item `item` of player `player`'s grouping (DevTerms): terminal `item` alone,
+// or with `merged` the showdown and / or fold terminal of the item-th opponent column
+// (DevTerms::col).  For each terminal e of the item, c32[e][h] and / or c64[e][h]
+// (either may be NULL) = coef_e x the
+// card-removal / strength sum of w = r_opp (.) in[sigma_opp], without the r_me / Z factor.
+// The exact sums are formed once for both terminals: the fold needs only the column
+// total and the per-card totals, the showdown the strength prefix and the per-card
+// prefixes as well (whose last entries are the per-card totals), so a fold that has no
+// showdown beside it skips the prefixes.  The sums are exact integers, so the results
+// do not depend on which terminals share an item, nor on kThreads: the whole CTA, or
+// the warp half starting at warp first_warp with named barrier `bar`.  `in` is read
+// through L2 (it may have been written earlier in the same launch by other CTAs).
+template <typename TIn, int kThreads = kItemThreads>
+__device__ inline void prod_item(const DevGame& g, const GradTab& tb, int player, int item, bool merged,
+                                 const TIn* __restrict__ in, float* __restrict__ c32,
+                                 double* __restrict__ c64, unsigned char* smem, int first_warp = 0,
+                                 int bar = 0) {
+  using namespace gradimpl;
+  constexpr int kMaxHandsPerThread = (kMaxLd + kThreads - 1) / kThreads;
+  constexpr int kWarps = kThreads / 32;
+  const int ld = g.ld, H = g.H, opp = 1 - player;
+  const int tid = threadIdx.x - first_warp * 32, lane = threadIdx.x & 31, warp = tid >> 5;
+  const int lstride = pc_stride(g.lmax);
+
+  Fx* F = reinterpret_cast<Fx*>(smem);
+  Fx* P = F + ld;                                                          // [ld + 1]
+  Fx* PC = reinterpret_cast<Fx*>(reinterpret_cast<unsigned char*>(P) + align16((size_t)(ld + 1) * sizeof(Fx)));
+  int* wmax = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(PC) +
+                                     align16((size_t)g.n_slots * lstride * sizeof(Fx)));
+  Fx* wtot = reinterpret_cast<Fx*>(wmax + 16);
+
+  // (selects instead of runtime indices into struct arrays, which would go to local memory)
+  const DevTerms tm = player ? g.terms[1] : g.terms[0];
+  const double* __restrict__ r_opp = opp ? tb.r64[1] : tb.r64[0];
+  // the item's terminals and opponent column (loads independent of each other: the column
+  // is not kept waiting for the terminals' kinds)
+  int os, e_sd, e_fold;
+  if (merged) {
+    const int4 c = tm.col[item];
+    e_sd = c.x;
+    e_fold = c.y;
+    os = c.z;
+  } else {
+    os = tm.opp_seq[item];
+    const bool showdown = tm.kind[item] != 0;
+    e_sd = showdown ? item : -1;
+    e_fold = showdown ? -1 : item;
+  }
+  const bool sd = e_sd >= 0;
+  const TIn* col = in + (size_t)os * ld;
+  // the coefficients are first read after the sums: fetch their lines into L1 now
+  if (tid == 0) {
+    if (sd) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(tm.coef + e_sd));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(tm.coef64 + e_sd));
+    }
+    if (e_fold >= 0) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(tm.coef + e_fold));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(tm.coef64 + e_fold));
+    }
+  }
+
+  // pass 1: all of this thread's inputs loaded at once, the column's largest exponent of
+  // |w| (for FP32 inputs an upper bound from the exponents, at most one too large)
+  TIn y[kMaxHandsPerThread];
+#pragma unroll
+  for (int k = 0; k < kMaxHandsPerThread; ++k) {
+    const int h = tid + k * kThreads;
+    y[k] = h < H ? __ldcg(col + h) : TIn(0);
+  }
+  int mlg = INT_MIN;
+#pragma unroll
+  for (int k = 0; k < kMaxHandsPerThread; ++k) {
+    const int h = tid + k * kThreads;
+    if (h < ld) {
+      if constexpr (std::is_same<TIn, float>::value) mlg = max(mlg, lg_bound(r_opp[h], y[k]));
+      else mlg = max(mlg, wprod(r_opp[h], y[k]).lg);   // (FP64 y: rounded product, exact lg)
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) mlg = max(mlg, __shfl_xor_sync(0xffffffffu, mlg, d));
+  if (lane == 0) wmax[warp] = mlg;
+  item_sync<kThreads>(bar);
+  int M = INT_MIN;
+#pragma unroll
+  for (int q = 0; q < kWarps; ++q) M = max(M, wmax[q]);
+  const int ex = scale_of(M);
+  // pass 2: exact fixed point
+#pragma unroll
+  for (int k = 0; k < kMaxHandsPerThread; ++k) {
+    const int h = tid + k * kThreads;
+    if (h < ld) F[h] = to_fx(wprod(r_opp[h], y[k]), ex);
+  }
+  item_sync<kThreads>(bar);
+
+  // the column total W; with a showdown the exclusive prefix over ascending strength:
+  // P[i] = sum_{k < i} w[k], P[ld] = W
+  const int K = (ld + kThreads - 1) / kThreads;   // raking chunk
+  const int k0 = min(tid * K, ld), k1 = min(k0 + K, ld);
+  Fx loc = fx_zero();
+  for (int i = k0; i < k1; ++i) loc = fx_add(loc, F[i]);
+  const Fx inc = fx_scan(loc, lane);
+  if (lane == 31) wtot[warp] = inc;
+  item_sync<kThreads>(bar);
+  if (sd) {
+    Fx run = fx_shfl_up(inc, 1);
+    if (lane == 0) run = fx_zero();
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q)   // (unrolled: the loads issue together)
+      if (q < warp) run = fx_add(run, wtot[q]);
+    for (int i = k0; i < k1; ++i) {
+      P[i] = run;
+      run = fx_add(run, F[i]);
+    }
+    if (k0 < ld && k1 == ld) P[ld] = run;
+  }
+
+  // per-card sums: a card slot per 16-lane half warp, four consecutive list entries (at
+  // most 64) per lane, summed serially; with a showdown one half-warp scan gives the
+  // exclusive prefixes (the last one is the card's total), else a half-warp sum gives
+  // the total alone, stored where the prefixes would end
+  {
+    const int sub = lane >> 4, sl = lane & 15, i0 = 4 * sl;
+    for (int c0 = 2 * warp; c0 < g.n_slots; c0 += 2 * kWarps) {   // (warp-uniform trip count)
+      const int c = c0 + sub;
+      const bool ok = c < g.n_slots;
+      const int len = ok ? tb.card_len[c] : 0;
+      const uint16_t* lst = tb.card_hands + (size_t)(ok ? c : 0) * g.lmax;
+      Fx a[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[j] = i0 + j < len ? F[lst[i0 + j]] : fx_zero();
+#pragma unroll
+      for (int j = 1; j < 4; ++j) a[j] = fx_add(a[j - 1], a[j]);
+      Fx* pc = PC + (size_t)(ok ? c : 0) * lstride;
+      const Fx inc4 = fx_scan16(a[3], sl);
+      if (sd) {
+        const Fx before = fx_sub(inc4, a[3]);
+        if (ok && sl == 0) pc[0] = fx_zero();
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (ok && i0 + j < len) pc[pc_pad(i0 + j + 1)] = fx_add(before, a[j]);
+      } else if (ok && sl == 15) {
+        pc[pc_pad(len)] = inc4;   // the card's total (lane 15 holds the sum of the list)
+      }
+    }
+  }
+  item_sync<kThreads>(bar);
+  Fx W;
+  if (sd) {
+    W = P[ld];
+  } else {
+    W = fx_zero();
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) W = fx_add(W, wtot[q]);
+  }
+
+  // the showdown terminal's contributions, then the fold's (one copy of the conversion)
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const int e = pass == 0 ? e_sd : e_fold;
+    if (e < 0) continue;
+    const float coef32 = tm.coef[e];
+    const double coef64 = tm.coef64[e];
+#pragma unroll
+    for (int k = 0; k < kMaxHandsPerThread; ++k) {
+      const int h = tid + k * kThreads;
+      if (h >= ld) break;
+      const uint4 hi = tb.hinfo[h];
+      const Fx C0 = PC[hi.z & 0xffffu];
+      const Fx C1 = PC[hi.w >> 16];
+      Fx val;
+      if (pass == 1) {
+        val = fx_sub(fx_sub(W, C0), C1);
+        if (g.hand_size == 2) val = fx_add(val, F[h]);
+      } else {
+        const Fx lt = fx_sub(fx_sub(P[hi.x & 0xffffu], PC[hi.y & 0xffffu]), PC[hi.z >> 16]);
+        const Fx gt = fx_sub(fx_sub(fx_sub(W, P[hi.x >> 16]), fx_sub(C0, PC[hi.y >> 16])),
+                             fx_sub(C1, PC[hi.w & 0xffffu]));
+        val = fx_sub(gt, lt);
+      }
+      const bool live = h < H;
+      float v32;
+      double v64;
+      fx_to_f32_f64(val, ex, v32, v64);
+      if (c32 != nullptr) c32[(size_t)e * ld + h] = live ? coef32 * v32 : 0.f;
+      if (c64 != nullptr) c64[(size_t)e * ld + h] = live ? coef64 * v64 : 0.0;
+    }
+  }
+  item_sync<kThreads>(bar);   // shared memory is reused by the caller's next item
+}
+
+// Contribution of terminal e alone (the standalone product kernels, one CTA per terminal).
 template <typename TIn, int kThreads = kItemThreads>
 __device__ inline void term_item(const DevGame& g, const GradTab& tb, int player, int e,
+                                 const TIn* __restrict__ in, float* __restrict__ c32,
+                                 double* __restrict__ c64, unsigned char* smem, int first_warp = 0,
+                                 int bar = 0) {
+  prod_item<TIn, kThreads>(g, tb, player, e, false, in, c32, c64, smem, first_warp, bar);
+}
+
+// One terminal per item with the strength and per-card prefixes formed for every
+// terminal kind (the one-game driver's product items: a fold item is never the longest
+// of its phase there, and this body keeps that driver's code smaller).  Same results
+// as prod_item.
+template <typename TIn, int kThreads = kItemThreads>
+__device__ inline void term_item_whole(const DevGame& g, const GradTab& tb, int player, int e,
                                  const TIn* __restrict__ in, float* __restrict__ c32,
                                  double* __restrict__ c64, unsigned char* smem, int first_warp = 0,
                                  int bar = 0) {

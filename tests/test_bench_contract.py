@@ -51,5 +51,7 @@ def test_gpu_arm_line_has_every_key():
     assert 0 < d["batched"]["roofline"]["frac"] < 1.5
     assert d["large"]["value"] > 0 and 0 < d["large"]["roofline"]["frac"] < 1.5
     assert d["large"]["time_to_gap"]["iters"] > 0
+    cf = d["cpu_fast"]
+    assert cf["value"] > 0 and cf["cores"] >= 1 and cf["time_to_gap"]["iters"] > 0
     sv = d["served"]
     assert sv["requests"] == 3 and sv["solves_per_s"] > 0 and sv["latency_p99_s"] >= sv["latency_p50_s"] > 0
