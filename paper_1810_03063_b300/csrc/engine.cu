@@ -293,14 +293,16 @@ __device__ __forceinline__ int prod_items(const DevTerms& tm, Grp gr, bool& merg
 // One product phase: every terminal of `player`'s grouping; c64 (FP64 contributions
 // for the residual) may be NULL.  With pairs (the job allows them and the group has at
 // least two items per CTA) each warp half takes its own items.
-// kProd selects the product item body: 0 term_item_whole (one terminal per item),
-// 1 prod_item with one terminal per item, 2 prod_item, merged when the group is small.
+// kProd selects the product items: 0, one terminal per item (term_item_whole), the
+// one-game kernel's items when every terminal of a phase has its own CTA; 2,
+// prod_item, merged per opponent column when the group has fewer CTAs than
+// terminals.  The results are the same bits either way.
 template <int kProd>
 __device__ __forceinline__ void one_prod_item(const DevGame& g, const GradTab& tb, int player, int item,
                                               bool merged, const float* in, float* c32, double* c64,
                                               unsigned char* sm) {
   if constexpr (kProd == 0) term_item_whole<float>(g, tb, player, item, in, c32, c64, sm);
-  else prod_item<float>(g, tb, player, item, kProd == 2 && merged, in, c32, c64, sm);
+  else prod_item<float>(g, tb, player, item, merged, in, c32, c64, sm);
 }
 
 template <int kProd>
@@ -309,7 +311,7 @@ __device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, Grp g
   const DevTerms tm = player ? g.terms[1] : g.terms[0];
   bool merged;
   int n = prod_items(tm, gr, merged);
-  if (kProd != 2 && merged) {
+  if (kProd == 0 && merged) {
     merged = false;
     n = tm.n;
   }
@@ -327,8 +329,8 @@ __device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, Grp g
         term_item_whole<float, kItemThreads / 2>(g, tb.grad, player, base + half, in, c32, c64, hs,
                                                  half * kHalf, 1 + half);
       else
-        prod_item<float, kItemThreads / 2>(g, tb.grad, player, base + half, kProd == 2 && merged, in, c32,
-                                           c64, hs, half * kHalf, 1 + half);
+        prod_item<float, kItemThreads / 2>(g, tb.grad, player, base + half, merged, in, c32, c64, hs,
+                                           half * kHalf, 1 + half);
     }
 }
 
@@ -718,7 +720,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
       const DevTerms tmo = ot ? g.terms[1] : g.terms[0];
       bool merged;
       int T = prod_items(tmo, gr, merged);
-      if (kProd != 2 && merged) {
+      if (kProd == 0 && merged) {
         merged = false;
         T = tmo.n;
       }
@@ -802,17 +804,23 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
   }
 }
 
-#ifndef EGT_ONE_GAME_PROD
-#define EGT_ONE_GAME_PROD 2
-#endif
-constexpr int kOneGameProd = EGT_ONE_GAME_PROD;
-
-// One job on the whole grid, its description in the kernel parameters.
+// One job on the whole grid, its description in the kernel parameters: a CTA for every
+// terminal of a product phase (one terminal per item) ...
 __global__ void __launch_bounds__(kItemThreads, 1)
     engine_kernel_one(EngineJob job, unsigned int extra, unsigned long long limit_ns) {
   extern __shared__ __align__(16) unsigned char smem_all[];
-  engine_job<kOneGameProd>(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x}, job.pair,
-             (unsigned long long)gridDim.x + extra, limit_ns, smem_all);
+  engine_job<0>(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x}, job.pair,
+                (unsigned long long)gridDim.x + extra, limit_ns, smem_all);
+}
+
+// ... or fewer CTAs than terminals (items merged per opponent column).  Two kernels
+// rather than one with both item bodies: the second body in the first kernel cost
+// its games 1.4 % of their iteration rate.
+__global__ void __launch_bounds__(kItemThreads, 1)
+    engine_kernel_one_merged(EngineJob job, unsigned int extra, unsigned long long limit_ns) {
+  extern __shared__ __align__(16) unsigned char smem_all[];
+  engine_job<2>(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x}, job.pair,
+                (unsigned long long)gridDim.x + extra, limit_ns, smem_all);
 }
 
 // CTA groups of a launch as the plan gives them (group q: CTAs [first, first +
@@ -862,8 +870,9 @@ cudaError_t engine_launch_one(const EngineJob& job, int grid, size_t smem, unsig
   unsigned int ex = extra;
   unsigned long long lim = limit_ns;
   void* args[] = {&j, &ex, &lim};
-  return cudaLaunchCooperativeKernel((const void*)engine_kernel_one, dim3(grid), dim3(kItemThreads), args,
-                                     smem, st);
+  const bool merged = grid < std::max(job.g.terms[0].n, job.g.terms[1].n);
+  return cudaLaunchCooperativeKernel(merged ? (const void*)engine_kernel_one_merged : (const void*)engine_kernel_one,
+                                     dim3(grid), dim3(kItemThreads), args, smem, st);
 }
 
 cudaError_t engine_launch(const EngineJob* jobs_dev, const EngineGroup* plan_dev, int n_groups, int grid,
@@ -877,8 +886,9 @@ cudaError_t engine_launch(const EngineJob* jobs_dev, const EngineGroup* plan_dev
 }
 
 int engine_smem_limit(bool batch) {
-  return batch ? opt_in_dynamic_smem((const void*)engine_kernel)
-               : opt_in_dynamic_smem((const void*)engine_kernel_one);
+  if (batch) return opt_in_dynamic_smem((const void*)engine_kernel);
+  return std::min(opt_in_dynamic_smem((const void*)engine_kernel_one),
+                  opt_in_dynamic_smem((const void*)engine_kernel_one_merged));
 }
 
 int engine_max_grid(size_t smem, bool batch) {
@@ -890,10 +900,16 @@ int engine_max_grid(size_t smem, bool batch) {
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
     return -1;
-  const cudaError_t e = batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel,
-                                                                              kItemThreads, smem)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel_one,
-                                                                              kItemThreads, smem);
+  cudaError_t e;
+  if (batch) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel, kItemThreads, smem);
+  } else {
+    int per_sm2 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel_one, kItemThreads, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, engine_kernel_one_merged, kItemThreads, smem);
+    per_sm = std::min(per_sm, per_sm2);
+  }
   if (e != cudaSuccess) return -1;
   if (!coop) return 0;
   return sms * per_sm;
