@@ -280,14 +280,16 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
   }
 
   // sizes of the arena
-  std::vector<float> rf[2], rzf[2];
+  std::vector<float> rf[2], rlof[2], rzf[2];
   std::vector<double> rz64[2];
   for (int p = 0; p < 2; ++p) {
     rf[p].resize(ld);
+    rlof[p].resize(ld);
     rzf[p].resize(ld);
     rz64[p].resize(ld);
     for (int s = 0; s < ld; ++s) {
       rf[p][s] = (float)r[p][s];
+      rlof[p][s] = (float)(r[p][s] - (double)rf[p][s]);
       rz64[p][s] = r[p][s] / Z;
       rzf[p][s] = (float)rz64[p][s];
     }
@@ -304,7 +306,7 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
   bytes += ld * (sizeof(uchar2) + sizeof(ushort2) + sizeof(uchar4) + sizeof(uint4)) + card_hands.size() * 2 +
            card_len.size() * 4;
   for (int p = 0; p < 2; ++p) {
-    bytes += ld * (2 * sizeof(float) + 2 * sizeof(double));
+    bytes += ld * (3 * sizeof(float) + 2 * sizeof(double));
     const Treeplex& T = C.tpx[p];
     bytes += (4 * T.J + T.L + 1 + 2 * T.S + 1 + T.child_idx.size()) * sizeof(int) + T.J * (sizeof(double) + sizeof(float));
     bytes += (tptr[p].size() + 2 * topp[p].size() + tcol[p].size()) * sizeof(int) +
@@ -344,6 +346,7 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
   g.card_len = (const int*)put(card_len.data(), card_len.size() * 4);
   for (int p = 0; p < 2; ++p) {
     g.r[p] = (const float*)put(rf[p].data(), ld * 4);
+    g.rlo[p] = (const float*)put(rlof[p].data(), ld * 4);
     g.rz[p] = (const float*)put(rzf[p].data(), ld * 4);
     g.r64[p] = (const double*)put(r[p].data(), ld * 8);
     g.rz64[p] = (const double*)put(rz64[p].data(), ld * 8);

@@ -61,7 +61,8 @@ struct DevGame {
   const uint4* hinfo;
   const uint16_t* card_hands;  // [n_slots][lmax] sorted hand indices holding the card
   const int* card_len;     // [n_slots]
-  const float* r[2];       // [ld] normalised ranges (0 on padding)
+  const float* r[2];       // [ld] normalised ranges rounded to FP32 (0 on padding): r_hi
+  const float* rlo[2];     // [ld] RN32(r64 - r_hi): r64 = r_hi + r_lo to within 2^-48 r64
   const float* rz[2];      // [ld] r / Z
   const double* r64[2];
   const double* rz64[2];

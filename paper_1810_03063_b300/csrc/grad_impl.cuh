@@ -16,18 +16,26 @@
 // coef_b x (sum) for every hand; the consumer of the product (the smoothed best
 // response, the FP64 best response, or the combine kernel of egt_grad) adds the
 // one or two contributions of a sequence in terminal order and multiplies by
-// r_me / Z while it loads them.  All sums are exact: each w is put in fixed point with two int64 limbs
-// (integer part at a per-terminal power-of-two scale leaving 2^59 headroom,
-// then 40 more fraction bits), so prefix sums, per-card corrections and the
-// tie-aware differences are integer operations, deterministic in any order and
-// on the full-rate integer pipes.  For FP32 inputs w = r (FP64 range) x y is
-// formed exactly as the 77-bit product of the two mantissas, with integer
-// operations only (B300's FP64 pipe is a small fraction of the integer rate).
-// From the same exact sums the CTA can emit an FP32 contribution (the path of
-// every EGT step) and an FP64 one (the stopping residual); asking for the FP64
-// one does not change the FP32 one.
+// r_me / Z while it loads them.
+//
+// Arithmetic: each w is put in 63-bit fixed point, an int64 at a per-column
+// power-of-two scale 2^ex that maps the column's largest |w| below 2^52 (so a
+// sum of up to 2048 terms stays below 2^63), and every prefix sum, per-card
+// correction and tie-aware difference is an exact integer operation:
+// deterministic in any order, on the full-rate integer pipes, and the same bits
+// whichever items or threads form it.  For FP32 inputs w 2^ex is formed from
+// the range split in two FP32 parts, r = r_hi + r_lo: p = r_hi a exactly as an
+// FMA product and its error, plus r_lo a, with a = y 2^ex (exact), each part
+// rounded to an integer; so the fixed-point w is within 2^-47 |w 2^ex| + 1.5 of
+// the exact one (ranges below 2^-60, where a could overflow, take the same
+// product in FP64).  FP64 inputs (the public FP64 product) use w = r y in
+// FP64.  From the same sums the CTA can emit an FP32 contribution (the path of
+// every EGT step) and an FP64 one (the stopping residual): the int64 sum
+// rounded once to each format; asking for the FP64 one does not change the
+// FP32 one.
 #pragma once
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <type_traits>
 
@@ -39,8 +47,8 @@ constexpr int kItemThreads = 512;     // threads of a CTA of the engine and of t
 
 namespace gradimpl {
 
-// Bit-level helpers that also compile for the host: the exact-arithmetic functions
-// below (w = r y, fixed point, rounding back to FP32 / FP64) are checked on the CPU
+// Bit-level helpers that also compile for the host: the arithmetic functions below
+// (w 2^ex in fixed point, rounding back to FP32 / FP64) are checked on the CPU
 // against rational arithmetic.
 __host__ __device__ __forceinline__ int clz64(unsigned long long x) {
 #ifdef __CUDA_ARCH__
@@ -54,13 +62,6 @@ __host__ __device__ __forceinline__ int clz32(unsigned x) {
   return __clz((int)x);
 #else
   return x ? __builtin_clz(x) : 32;
-#endif
-}
-__host__ __device__ __forceinline__ unsigned long long umul64hi(unsigned long long a, unsigned long long b) {
-#ifdef __CUDA_ARCH__
-  return __umul64hi(a, b);
-#else
-  return (unsigned long long)(((unsigned __int128)a * b) >> 64);
 #endif
 }
 __host__ __device__ __forceinline__ unsigned long long f64_bits(double x) {
@@ -100,20 +101,16 @@ __host__ __device__ __forceinline__ float bits_f32(unsigned b) {
 #endif
 }
 
-// fixed point: v0 = integer part, v1 = the next 40 fraction bits (both carry the sign)
+// fixed point: one signed int64 (w 2^ex rounded to an integer)
 struct Fx {
-  long long v0, v1;
+  long long v0;
 };
 
-__host__ __device__ __forceinline__ Fx fx_zero() { return {0, 0}; }
-__host__ __device__ __forceinline__ Fx fx_add(Fx a, Fx b) { return {a.v0 + b.v0, a.v1 + b.v1}; }
-__host__ __device__ __forceinline__ Fx fx_sub(Fx a, Fx b) { return {a.v0 - b.v0, a.v1 - b.v1}; }
-__device__ __forceinline__ Fx fx_shfl_up(Fx a, int d) {
-  return {__shfl_up_sync(0xffffffffu, a.v0, d), __shfl_up_sync(0xffffffffu, a.v1, d)};
-}
-__device__ __forceinline__ Fx fx_shfl(Fx a, int src) {
-  return {__shfl_sync(0xffffffffu, a.v0, src), __shfl_sync(0xffffffffu, a.v1, src)};
-}
+__host__ __device__ __forceinline__ Fx fx_zero() { return {0}; }
+__host__ __device__ __forceinline__ Fx fx_add(Fx a, Fx b) { return {a.v0 + b.v0}; }
+__host__ __device__ __forceinline__ Fx fx_sub(Fx a, Fx b) { return {a.v0 - b.v0}; }
+__device__ __forceinline__ Fx fx_shfl_up(Fx a, int d) { return {__shfl_up_sync(0xffffffffu, a.v0, d)}; }
+__device__ __forceinline__ Fx fx_shfl(Fx a, int src) { return {__shfl_sync(0xffffffffu, a.v0, src)}; }
 __device__ __forceinline__ Fx fx_scan(Fx v, int lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -126,80 +123,39 @@ __device__ __forceinline__ Fx fx_scan(Fx v, int lane) {
 __device__ __forceinline__ Fx fx_scan16(Fx v, int sl) {
 #pragma unroll
   for (int d = 1; d < 16; d <<= 1) {
-    const Fx o = {__shfl_up_sync(0xffffffffu, v.v0, d, 16), __shfl_up_sync(0xffffffffu, v.v1, d, 16)};
+    const Fx o = {__shfl_up_sync(0xffffffffu, v.v0, d, 16)};
     if (sl >= d) v = fx_add(v, o);
   }
   return v;
 }
 
-// 2^e as float / double for the exponent ranges used here (split in two factors)
-__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
-__device__ __forceinline__ double pow2d(int e) {
-  return __longlong_as_double((long long)(e + 1023) << 52);
+// 2^e as float (e in [-126, 127]) / double (e in [-1022, 1023]), from the exponent field
+__host__ __device__ __forceinline__ float pow2f(int e) { return bits_f32((unsigned)(e + 127) << 23); }
+__host__ __device__ __forceinline__ double pow2d(int e) {
+  return bits_f64((unsigned long long)(e + 1023) << 52);
 }
 
-// floor(P / 2^k) of the 128-bit P = hi:lo, low 64 bits
-__host__ __device__ __forceinline__ unsigned long long shr128(unsigned long long hi, unsigned long long lo, int k) {
-  if (k <= 0) return lo;
-  if (k >= 128) return 0;
-  if (k >= 64) return hi >> (k - 64);
-  return (lo >> k) | (hi << (64 - k));
+// round to the nearest integer, ties to even (the default rounding mode on the host)
+__host__ __device__ __forceinline__ long long rint_ll(float x) {
+#ifdef __CUDA_ARCH__
+  return __float2ll_rn(x);
+#else
+  return std::llrint(x);
+#endif
 }
-
-// |w| = P 2^E with P = hi:lo an exact integer, sign neg, lg = floor(log2 |w|)
-// (INT_MIN when w = 0).
-struct WBits {
-  unsigned long long hi, lo;
-  int E, lg, neg;
-};
-
-// w = r * y exactly: 53-bit x 24-bit mantissa product
-__host__ __device__ __forceinline__ WBits wprod(double r, float y) {
-  const unsigned long long rb = f64_bits(r);
-  const unsigned yb = f32_bits(y);
-  int er = (int)((rb >> 52) & 0x7ffull), ey = (int)((yb >> 23) & 0xffu);
-  unsigned long long mr = rb & ((1ull << 52) - 1), my = yb & 0x7fffffu;
-  WBits w;
-  w.neg = (int)((rb >> 63) ^ (yb >> 31));
-  if ((er == 0 && mr == 0) || (ey == 0 && my == 0)) {
-    w.hi = w.lo = 0;
-    w.E = 0;
-    w.lg = INT_MIN;
-    return w;
-  }
-  if (er == 0) er = 1;
-  else mr |= 1ull << 52;
-  if (ey == 0) ey = 1;
-  else my |= 1ull << 23;
-  w.lo = mr * my;
-  w.hi = umul64hi(mr, my);
-  w.E = (er - 1075) + (ey - 150);
-  const int nb = w.hi ? 128 - clz64(w.hi) : 64 - clz64(w.lo);
-  w.lg = w.E + nb - 1;
-  return w;
+__host__ __device__ __forceinline__ long long rint_ll(double x) {
+#ifdef __CUDA_ARCH__
+  return __double2ll_rn(x);
+#else
+  return std::llrint(x);
+#endif
 }
-
-// w = r * y for an FP64 y: rounded once in FP64, then exact from there
-__host__ __device__ __forceinline__ WBits wprod(double r, double y) {
-  const double w = r * y;
-  const unsigned long long b = f64_bits(w);
-  int e = (int)((b >> 52) & 0x7ffull);
-  unsigned long long m = b & ((1ull << 52) - 1);
-  WBits x;
-  x.neg = (int)(b >> 63);
-  if (e == 0 && m == 0) {
-    x.hi = x.lo = 0;
-    x.E = 0;
-    x.lg = INT_MIN;
-    return x;
-  }
-  if (e == 0) e = 1;
-  else m |= 1ull << 52;
-  x.hi = 0;
-  x.lo = m;
-  x.E = e - 1075;
-  x.lg = x.E + (64 - clz64(m)) - 1;
-  return x;
+__host__ __device__ __forceinline__ float fma32(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fmaf(a, b, c);
+#endif
 }
 
 // An upper bound on floor(log2 |r y|) for FP32 y from the two exponents alone (the
@@ -218,152 +174,73 @@ __host__ __device__ __forceinline__ int lg_bound(double r, float y) {
   return lr + ly + 1;
 }
 
-// |w| 2^ex as integer part + 40 truncated fraction bits, signed
-__host__ __device__ __forceinline__ Fx to_fx(const WBits& w, int ex) {
-  if (w.lg == INT_MIN) return fx_zero();
-  const int s = w.E + ex;
-  unsigned long long a, b;
-  if (s >= 0) {
-    a = w.lo << s;          // |w| 2^ex < 2^48 keeps this in range
-    b = 0;
-  } else {
-    // Q = P 2^(s + 40) truncated, holding a (integer part) and b (40 fraction bits),
-    // from one right shift of P 2^39 (P < 2^77) by u = -s - 1: no branch on the
-    // magnitude while u < 64 (hands within 35 binades of the column's largest |w|)
-    const unsigned long long Lhi = (w.hi << 39) | (w.lo >> 25), Llo = w.lo << 39;
-    const int u = -s - 1;
-    unsigned long long qhi = 0, qlo = 0;
-    if (u < 64) {
-      qlo = u ? (Llo >> u) | (Lhi << (64 - u)) : Llo;
-      qhi = Lhi >> u;
-    } else if (u < 128) {
-      qlo = Lhi >> (u - 64);
-    }
-    a = (qhi << 24) | (qlo >> 40);
-    b = qlo & ((1ull << 40) - 1);
-  }
-  const long long sa = (long long)a, sb = (long long)b;
-  return w.neg ? Fx{-sa, -sb} : Fx{sa, sb};
+// floor(log2 |w|) of an FP64 value (INT_MIN when 0), subnormals included
+__host__ __device__ __forceinline__ int lg64(double w) {
+  const unsigned long long b = f64_bits(w);
+  const int e = (int)((b >> 52) & 0x7ffull);
+  const unsigned long long m = b & ((1ull << 52) - 1);
+  if (e == 0 && m == 0) return INT_MIN;
+  return e ? e - 1023 : (63 - clz64(m)) - 1074;
 }
 
-// scale so that |w| 2^ex < 2^48 for the largest |w| (sums of 2048 terms < 2^59)
-__host__ __device__ __forceinline__ int scale_of(int maxlg) { return maxlg == INT_MIN ? 0 : 47 - maxlg; }
+// The scale exponent of a column whose largest |w| has floor(log2) <= maxlg: |w| 2^ex <
+// 2^52.  Clamped to [-252, 252] (a column below 2^-201 or above 2^303 keeps a coarser
+// scale; its sums stay exact at that scale), where 2^ex and 2^-ex are each a product of
+// two normal FP32 powers of two.
+__host__ __device__ __forceinline__ int scale_of(int maxlg) {
+  if (maxlg == INT_MIN) return 0;
+  const int ex = 51 - maxlg;
+  return ex < -252 ? -252 : (ex > 252 ? 252 : ex);
+}
 
-// |N| of a fixed-point sum, N = v0 2^40 + v1 as a signed 128-bit integer
-// (uh:ul), its sign and bit length (0 when N = 0).
-struct Wide {
-  unsigned long long uh, ul;
-  int nb, neg;
+// 2^ex as two float factors, each a normal power of two (|ex| <= 252)
+struct Pow2f {
+  float a, b;
 };
-
-__host__ __device__ __forceinline__ Wide fx_wide(Fx a) {
-  unsigned long long lo = (unsigned long long)a.v0 << 40;
-  long long hi = a.v0 >> 24;
-  const unsigned long long lo2 = lo + (unsigned long long)a.v1;
-  hi += (a.v1 < 0 ? -1 : 0) + (lo2 < lo ? 1 : 0);
-  lo = lo2;
-  Wide w;
-  w.neg = hi < 0;
-  w.uh = (unsigned long long)hi;
-  w.ul = lo;
-  if (w.neg) {
-    w.ul = ~w.ul + 1ull;
-    w.uh = ~w.uh + (w.ul == 0 ? 1ull : 0ull);
-  }
-  w.nb = w.uh ? 128 - clz64(w.uh) : (w.ul ? 64 - clz64(w.ul) : 0);
-  return w;
+__host__ __device__ __forceinline__ Pow2f pow2f_split(int ex) {
+  const int e1 = ex < -126 ? -126 : (ex > 127 ? 127 : ex);
+  return {pow2f(e1), pow2f(ex - e1)};
 }
 
-// The leading P bits of |N| (nb >= 1, 1 <= P <= 53) rounded to nearest even:
-// the mantissa in [2^(P-1), 2^P]; a carry to 2^P is left to the caller.
-__host__ __device__ __forceinline__ unsigned long long round_top(const Wide& w, int P) {
-  if (w.nb <= P) return w.ul << (P - w.nb);
-  const int sh = w.nb - P;
-  const unsigned long long mant = shr128(w.uh, w.ul, sh);
-  const int rb = sh - 1;                                     // position of the rounding bit
-  const unsigned long long round = rb < 64 ? (w.ul >> rb) & 1ull : (w.uh >> (rb - 64)) & 1ull;
-  bool sticky;
-  if (rb == 0) sticky = false;
-  else if (rb < 64) sticky = (w.ul & ((1ull << rb) - 1ull)) != 0;
-  else if (rb == 64) sticky = w.ul != 0;
-  else sticky = w.ul != 0 || (w.uh & ((1ull << (rb - 64)) - 1ull)) != 0;
-  return mant + ((round && (sticky || (mant & 1ull))) ? 1ull : 0ull);
+// r y 2^ex as an integer, FP32 y, r = r64 = r_hi + r_lo with r_hi = RN32(r64) and r_lo =
+// RN32(r64 - r_hi); s = pow2f_split(ex).  With a = y 2^ex (exact unless it underflows,
+// where the term is below 2^-126 and rounds to 0 anyway): r_hi a = p + e exactly (FMA),
+// r_lo a is rounded once (relative 2^-24 of a term at most 2^-24 |r a|), and each part
+// is rounded to an integer; with |r - r_hi - r_lo| <= 2^-48 |r|, |result - r y 2^ex| <=
+// 2^-47 |r y 2^ex| + 1.5.  A range below
+// 2^-60 (a could overflow there) takes w = r64 y in FP64 instead.
+__host__ __device__ __forceinline__ long long fx_of(double r64, float r_hi, float r_lo, float y, Pow2f s,
+                                                   int ex) {
+  if (!(r_hi >= 1.0f / 1152921504606846976.0f)) {            // r_hi < 2^-60 (0 included)
+    if (r64 == 0.0) return 0;
+    return rint_ll(r64 * (double)y * pow2d(ex));
+  }
+  const float a = (y * s.a) * s.b;
+  const float p = r_hi * a;
+  const float e = fma32(r_hi, a, -p);
+  const float q = r_lo * a;
+  return rint_ll(p) + rint_ll(e) + rint_ll(q);
 }
 
-// |N| 2^s (N from fx_wide) correctly rounded to a binary format with P-bit
-// significands, minimum normal exponent emin and bias `bias`: the magnitude's
-// bit pattern (exponent field << (P - 1) | fraction), or the all-ones exponent
-// field (infinity) on overflow.
-__host__ __device__ __forceinline__ unsigned long long fx_round(const Wide& w, int s, int P, int emin, int emax) {
-  const int e0 = w.nb - 1 + s;                                // exponent of the leading bit
-  if (e0 > emax) return (unsigned long long)(emax - emin + 2) << (P - 1);
-  if (e0 >= emin) {
-    unsigned long long mant = round_top(w, P);
-    int e = e0;
-    if (mant >> P) {
-      mant >>= 1;
-      ++e;
-    }
-    if (e > emax) return (unsigned long long)(emax - emin + 2) << (P - 1);
-    return ((unsigned long long)(e - emin + 1) << (P - 1)) | (mant & ((1ull << (P - 1)) - 1ull));
-  }
-  // subnormal: P - (emin - e0) significant bits remain
-  const int q = P - (emin - e0);
-  if (q < 0) return 0;
-  if (q == 0) {   // |value| in [min subnormal / 2, min subnormal): rounds up unless exactly half
-    const bool above = w.nb >= 2 && (w.nb - 1 >= 64 ? (w.ul != 0 || (w.uh & ((1ull << (w.nb - 65)) - 1ull)) != 0)
-                                                    : (w.ul & ((1ull << (w.nb - 1)) - 1ull)) != 0);
-    return above ? 1ull : 0ull;
-  }
-  return round_top(w, q);   // a carry to 2^q lands on the smallest normal, as it should
+// r y 2^ex as an integer, FP64 y: w = r y rounded once in FP64 (relative 2^-53)
+__host__ __device__ __forceinline__ long long fx_of64(double r64, double y, int ex) {
+  return rint_ll(r64 * y * pow2d(ex));
 }
 
-// FP32 and FP64 values of a fixed-point sum, a x 2^-ex, both correctly rounded
-// (every bit of the sum counts), with integer operations and one normalisation:
-// the magnitude, a 104-bit integer hi:lo, is shifted so that its leading bit is
-// bit 63 of T, and each significand is rounded to nearest even from the top of T,
-// the bits below it (in T, and past T: `rest`) acting as the sticky bit.  Only
-// subnormal and overflowing results branch off, to the general path.
+// FP32 and FP64 values of a fixed-point sum S 2^-ex: S rounded once to each format (to
+// nearest, ties to even), then scaled by the power of two (exact for normal results; a
+// subnormal result is rounded a second time).
 __host__ __device__ __forceinline__ void fx_to_f32_f64(Fx a, int ex, float& r32, double& r64) {
-  const long long v0 = a.v0 + (a.v1 >> 40);
-  const unsigned long long f = (unsigned long long)a.v1 & ((1ull << 40) - 1ull);
-  const bool neg = v0 < 0;
-  const unsigned long long m0 = neg ? (unsigned long long)(-(v0 + (f ? 1 : 0))) : (unsigned long long)v0;
-  const unsigned long long m1 = neg ? (f ? (1ull << 40) - f : 0ull) : f;
-  const unsigned long long hi = m0 >> 24, lo = (m0 << 40) | m1;   // |sum| = hi 2^64 + lo
-  if ((hi | lo) == 0) {
-    r32 = 0.f;
-    r64 = 0.0;
-    return;
-  }
-  // hi < 2^40, so lz is in [24, 127] and every shift below is in [1, 63]
-  const int lz = hi ? clz64(hi) : 64 + clz64(lo);
-  const unsigned long long T = lz < 64 ? (hi << lz) | (lo >> (64 - lz)) : lo << (lz - 64);
-  const bool rest = lz < 64 && (lo << lz) != 0;
-  const int e = 127 - lz - 40 - ex;                               // exponent of the leading bit
-  unsigned long long q = T >> 11;
-  q += ((T >> 10) & 1ull) & (unsigned long long)(((T & 0x3ffull) != 0) | rest | (q & 1ull));
-  int e64 = e;
-  if (q >> 53) {
-    q >>= 1;
-    ++e64;
-  }
-  unsigned long long p = T >> 40;
-  p += ((T >> 39) & 1ull) & (unsigned long long)(((T & ((1ull << 39) - 1ull)) != 0) | rest | (p & 1ull));
-  int e32 = e;
-  if (p >> 24) {
-    p >>= 1;
-    ++e32;
-  }
-  if (e64 + 1023 < 1 || e64 + 1023 > 2046 || e32 + 127 < 1 || e32 + 127 > 254) {
-    const Wide w = fx_wide(a);
-    r64 = bits_f64(((unsigned long long)w.neg << 63) | fx_round(w, -40 - ex, 53, -1022, 1023));
-    r32 = bits_f32(((unsigned)w.neg << 31) | (unsigned)fx_round(w, -40 - ex, 24, -126, 127));
-    return;
-  }
-  r64 = bits_f64(((unsigned long long)neg << 63) | ((unsigned long long)(e64 + 1023) << 52) |
-                 (q & ((1ull << 52) - 1ull)));
-  r32 = bits_f32(((unsigned)neg << 31) | ((unsigned)(e32 + 127) << 23) | (unsigned)(p & 0x7fffffull));
+#ifdef __CUDA_ARCH__
+  const float f = __ll2float_rn(a.v0);
+  const double d = __ll2double_rn(a.v0);
+#else
+  const float f = (float)a.v0;
+  const double d = (double)a.v0;
+#endif
+  const Pow2f s = pow2f_split(-ex);
+  r32 = (f * s.a) * s.b;
+  r64 = d * pow2d(-ex);
 }
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -398,12 +275,15 @@ struct GradTab {
   const int* card_len;         // [n_slots]
   const uint16_t* card_hands;  // [n_slots][lmax]
   const double* r64[2];        // [ld] normalised ranges of both players
+  const float* rhi[2];         // [ld] their FP32 split r = r_hi + r_lo (DevGame::r, DevGame::rlo)
+  const float* rlo[2];
 };
 
 __host__ __device__ inline size_t grad_tab_bytes(const DevGame& g) {
   using gradimpl::align16;
   return align16((size_t)g.ld * sizeof(uint4)) + align16((size_t)g.n_slots * sizeof(int)) +
-         align16((size_t)g.n_slots * g.lmax * sizeof(uint16_t)) + 2 * align16((size_t)g.ld * sizeof(double));
+         align16((size_t)g.n_slots * g.lmax * sizeof(uint16_t)) + 2 * align16((size_t)g.ld * sizeof(double)) +
+         4 * align16((size_t)g.ld * sizeof(float));
 }
 
 // Copy the tables into dst (all threads of the CTA; the caller synchronises before use).
@@ -417,10 +297,20 @@ __device__ inline GradTab stage_grad_tab(const DevGame& g, unsigned char* dst) {
   p += align16((size_t)g.n_slots * g.lmax * sizeof(uint16_t));
   double* r0 = reinterpret_cast<double*>(p);
   double* r1 = r0 + align16((size_t)g.ld * sizeof(double)) / sizeof(double);
+  p += 2 * align16((size_t)g.ld * sizeof(double));
+  const size_t fs = align16((size_t)g.ld * sizeof(float)) / sizeof(float);
+  float* h0 = reinterpret_cast<float*>(p);
+  float* h1 = h0 + fs;
+  float* l0 = h1 + fs;
+  float* l1 = l0 + fs;
   for (int i = threadIdx.x; i < g.ld; i += blockDim.x) {
     hi[i] = g.hinfo[i];
     r0[i] = g.r64[0][i];
     r1[i] = g.r64[1][i];
+    h0[i] = g.r[0][i];
+    h1[i] = g.r[1][i];
+    l0[i] = g.rlo[0][i];
+    l1[i] = g.rlo[1][i];
   }
   for (int i = threadIdx.x; i < g.n_slots; i += blockDim.x) cl[i] = g.card_len[i];
   for (int i = threadIdx.x; i < g.n_slots * g.lmax; i += blockDim.x) ch[i] = g.card_hands[i];
@@ -430,6 +320,10 @@ __device__ inline GradTab stage_grad_tab(const DevGame& g, unsigned char* dst) {
   t.card_hands = ch;
   t.r64[0] = r0;
   t.r64[1] = r1;
+  t.rhi[0] = h0;
+  t.rhi[1] = h1;
+  t.rlo[0] = l0;
+  t.rlo[1] = l1;
   return t;
 }
 
@@ -467,6 +361,8 @@ __device__ inline void prod_item(const DevGame& g, const GradTab& tb, int player
   // (selects instead of runtime indices into struct arrays, which would go to local memory)
   const DevTerms tm = player ? g.terms[1] : g.terms[0];
   const double* __restrict__ r_opp = opp ? tb.r64[1] : tb.r64[0];
+  const float* __restrict__ rhi_opp = opp ? tb.rhi[1] : tb.rhi[0];
+  const float* __restrict__ rlo_opp = opp ? tb.rlo[1] : tb.rlo[0];
   // the item's terminals and opponent column (loads independent of each other: the column
   // is not kept waiting for the terminals' kinds)
   int os, e_sd, e_fold;
@@ -509,7 +405,7 @@ __device__ inline void prod_item(const DevGame& g, const GradTab& tb, int player
     const int h = tid + k * kThreads;
     if (h < ld) {
       if constexpr (std::is_same<TIn, float>::value) mlg = max(mlg, lg_bound(r_opp[h], y[k]));
-      else mlg = max(mlg, wprod(r_opp[h], y[k]).lg);   // (FP64 y: rounded product, exact lg)
+      else mlg = max(mlg, lg64(r_opp[h] * y[k]));   // (FP64 y: the rounded product's exact lg)
     }
   }
 #pragma unroll
@@ -520,11 +416,15 @@ __device__ inline void prod_item(const DevGame& g, const GradTab& tb, int player
 #pragma unroll
   for (int q = 0; q < kWarps; ++q) M = max(M, wmax[q]);
   const int ex = scale_of(M);
-  // pass 2: exact fixed point
+  const Pow2f s2 = pow2f_split(ex);
+  // pass 2: fixed point
 #pragma unroll
   for (int k = 0; k < kMaxHandsPerThread; ++k) {
     const int h = tid + k * kThreads;
-    if (h < ld) F[h] = to_fx(wprod(r_opp[h], y[k]), ex);
+    if (h < ld) {
+      if constexpr (std::is_same<TIn, float>::value) F[h] = {fx_of(r_opp[h], rhi_opp[h], rlo_opp[h], y[k], s2, ex)};
+      else F[h] = {fx_of64(r_opp[h], y[k], ex)};
+    }
   }
   item_sync<kThreads>(bar);
 
@@ -659,6 +559,8 @@ __device__ inline void term_item_whole(const DevGame& g, const GradTab& tb, int 
   // (selects instead of runtime indices into struct arrays, which would go to local memory)
   const DevTerms tm = player ? g.terms[1] : g.terms[0];
   const double* __restrict__ r_opp = opp ? tb.r64[1] : tb.r64[0];
+  const float* __restrict__ rhi_opp = opp ? tb.rhi[1] : tb.rhi[0];
+  const float* __restrict__ rlo_opp = opp ? tb.rlo[1] : tb.rlo[0];
   const int os = tm.opp_seq[e];
   const int kind = tm.kind[e];
   const float coef32 = tm.coef[e];
@@ -679,7 +581,7 @@ __device__ inline void term_item_whole(const DevGame& g, const GradTab& tb, int 
     const int h = tid + k * kThreads;
     if (h < ld) {
       if constexpr (std::is_same<TIn, float>::value) mlg = max(mlg, lg_bound(r_opp[h], y[k]));
-      else mlg = max(mlg, wprod(r_opp[h], y[k]).lg);   // (FP64 y: rounded product, exact lg)
+      else mlg = max(mlg, lg64(r_opp[h] * y[k]));   // (FP64 y: the rounded product's exact lg)
     }
   }
 #pragma unroll
@@ -690,11 +592,15 @@ __device__ inline void term_item_whole(const DevGame& g, const GradTab& tb, int 
 #pragma unroll
   for (int q = 0; q < kWarps; ++q) M = max(M, wmax[q]);
   const int ex = scale_of(M);
-  // pass 2: exact fixed point
+  const Pow2f s2 = pow2f_split(ex);
+  // pass 2: fixed point
 #pragma unroll
   for (int k = 0; k < kMaxHandsPerThread; ++k) {
     const int h = tid + k * kThreads;
-    if (h < ld) F[h] = to_fx(wprod(r_opp[h], y[k]), ex);
+    if (h < ld) {
+      if constexpr (std::is_same<TIn, float>::value) F[h] = {fx_of(r_opp[h], rhi_opp[h], rlo_opp[h], y[k], s2, ex)};
+      else F[h] = {fx_of64(r_opp[h], y[k], ex)};
+    }
   }
   item_sync<kThreads>(bar);
 

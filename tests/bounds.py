@@ -2,7 +2,7 @@
 
 All bounds are element-wise and follow the arithmetic (eps32 = 2^-24):
 
-* product (exact fixed-point sums rounded once, then scaled):
+* product (63-bit fixed-point sums, exact, rounded once, then scaled):
   |err(A v)_i| <= 8 eps32 (|A| |v|)_i + floor_i, and an input error dv adds (|A| dv)_i;
 * smoothed best response, FP32 rounding inside (exponent arguments carry an
   absolute error of a few eps32 times kappa = max |g_hat| / t, so each factor
@@ -51,15 +51,17 @@ def abs_apply(og, v, player):
 
 
 def fixed_point_floor(og, vec, player):
-    """Absolute error floor of the products.  Each terminal's card-removal / strength
-    sums are exact in fixed point down to 2^-87 of the largest |w| = |r_opp v_opp| of
-    its column (at most H truncated terms); coef_b and r_me / Z multiply afterwards.
-    Bounded here by |coef_b| max(r_me) max(r_opp) / Z max|v_opp| H 2^-85 per output row."""
+    """Absolute error floor of the products.  Each term r_opp v_opp enters its column's
+    sums as an integer at the column scale 2^ex (|w| 2^ex < 2^52), off by at most 1.5
+    units of 2^-ex <= 2^-50 of the column's largest |w| besides a relative 2^-47 (the
+    integer sums are exact; the terms the card-removal algebra cancels cancel exactly), so
+    an output built from at most H terms is off by at most H 1.5 2^-50 max|w|.  Bounded
+    here by |coef_b| max(r_me) max(r_opp) / Z max|v_opp| H 2^-49 per output row."""
     r = og.spec.ranges
     out = np.zeros((og.S[player], og.H))
     for b, t in enumerate(og.sf.terminals):
         scale = abs(og.coef[b]) * r[player].max() * r[1 - player].max() / og.Z
-        out[t.seq[player]] += scale * np.abs(vec[t.seq[1 - player]]).max() * og.H * 2.0 ** -85
+        out[t.seq[player]] += scale * np.abs(vec[t.seq[1 - player]]).max() * og.H * 2.0 ** -49
     return out
 
 
