@@ -162,9 +162,10 @@ EGT_API egt_status egt_terminal_query(const egt_game* game, int32_t* seq1, int32
  * player 0: out[S0][ld] = A in, in = y [S1][ld];
  * player 1: out[S1][ld] = A^T in, in = x [S0][ld].  Device pointers, in != out.
  * Computed per terminal with card-removal inclusion-exclusion (folds) and
- * strength-sorted prefix sums with per-card corrections (showdowns).  The sums
- * are exact (w = r x in formed exactly, two-limb fixed point 2^-87 below the
- * terminal's largest |w|); the output is the correctly rounded FP32 value of
+ * strength-sorted prefix sums with per-card corrections (showdowns).  Each
+ * term w = r x in enters its column's sums as one int64 at a power-of-two
+ * scale (within 2^-47 |w| + 2^-50 of the column's largest |w|), and the
+ * integer sums are exact and rounded once: the output is the FP32 value of
  * r_me / Z x the sum of the sequence's terminal contributions. */
 EGT_API egt_status egt_grad(egt_game* game, int32_t player, const float* in, float* out, void* stream);
 
