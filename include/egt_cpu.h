@@ -38,7 +38,7 @@ typedef struct {
   double eps_mbb;     /* stop when the residual is <= eps_mbb (0: run max_iters iterations) */
   int32_t max_iters;  /* iterations (accepted Decr calls) at most, >= 0 */
   int32_t gap_every;  /* residual after every gap_every-th iteration and at the last one (>= 1) */
-  int32_t threads;    /* OpenMP threads (0: the runtime's default) */
+  int32_t threads;    /* OpenMP threads (0: one per processor) */
 } egt_cpu_opts;
 
 typedef struct {

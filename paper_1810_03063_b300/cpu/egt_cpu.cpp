@@ -105,9 +105,6 @@ void product(const egt_cpu_game& G, int p, const Vec& in, Vec& out, std::vector<
       Vec& c = contrib[e];
       c.resize(H);
       const double W = s.P[H];
-      const int a0 = 0, a1 = 1;
-      (void)a0;
-      (void)a1;
       for (int h = 0; h < H; ++h) {
         const int ca = G.card[0][h], cb = G.card[1][h];
         const Vec& Pa = s.Pc[ca];
@@ -143,9 +140,9 @@ void product(const egt_cpu_game& G, int p, const Vec& in, Vec& out, std::vector<
 double sbr(const egt_cpu_game& G, int p, const Vec& loss, double mu, Vec* q_out) {
   const egt::Treeplex& T = G.C.tpx[p];
   const int H = G.H, J = T.J, S = T.S;
-  double total = 0;
+  std::vector<double> per_hand(H);
   if (q_out) q_out->assign((size_t)S * H, 0.0);
-#pragma omp parallel reduction(+ : total)
+#pragma omp parallel
   {
     std::vector<double> V(J), qbar(S), gh(64), q(S);
 #pragma omp for schedule(static)
@@ -183,7 +180,7 @@ double sbr(const egt_cpu_game& G, int p, const Vec& loss, double mu, Vec* q_out)
       double vh = 0;
       for (int j = 0; j < J; ++j)
         if (T.inf_parent[j] < 0) vh += V[j];
-      total += vh;
+      per_hand[h] = vh;
       if (q_out) {
         // top-down: simplexes in reverse bottom-up order
         for (auto it = G.up[p].rbegin(); it != G.up[p].rend(); ++it) {
@@ -195,6 +192,8 @@ double sbr(const egt_cpu_game& G, int p, const Vec& loss, double mu, Vec* q_out)
       }
     }
   }
+  double total = 0;   // summed in hand order: the same bits for any thread count
+  for (int h = 0; h < H; ++h) total += per_hand[h];
   return total;
 }
 
@@ -375,7 +374,9 @@ egt_status egt_cpu_solve(egt_cpu_game* G, const egt_cpu_opts* o, double* x_out, 
   if (!G || !o) return fail(EGT_ERR_INVALID_ARG, "game or opts is NULL");
   if (!(o->alpha > 0) || o->max_iters < 0 || o->gap_every < 1 || o->threads < 0)
     return fail(EGT_ERR_INVALID_ARG, "alpha > 0, max_iters >= 0, gap_every >= 1, threads >= 0");
-  if (o->threads > 0) omp_set_num_threads(o->threads);
+  // threads = 0: every processor (the runtime's setting may have been lowered by an
+  // earlier call, or by OMP_NUM_THREADS in the environment)
+  omp_set_num_threads(o->threads > 0 ? o->threads : omp_get_num_procs());
   const auto t0 = std::chrono::steady_clock::now();
   const int H = G->H;
   const int S0 = G->C.tpx[0].S, S1 = G->C.tpx[1].S;

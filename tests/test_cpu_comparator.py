@@ -54,6 +54,7 @@ def test_full_deck_trajectory_and_thread_count_independence():
     a = g.solve(alpha=0.01, eps_mbb=0.0, max_iters=12, gap_every=1, threads=1, iterates=True)
     b = g.solve(alpha=0.01, eps_mbb=0.0, max_iters=12, gap_every=1, threads=3, iterates=True)
     assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["y"], b["y"])   # fixed-order sums
+    assert a["gap_mbb"] == b["gap_mbb"] and a["mu"] == b["mu"] and b["threads"] == 3
     assert a["backoffs"] == r.backoffs
     assert np.abs(a["x"] - r.x).max() <= 1e-10 and np.abs(a["y"] - r.y).max() <= 1e-10
     assert abs(a["gap_mbb"] - r.gap_mbb) <= 1e-9 * r.gap_mbb
