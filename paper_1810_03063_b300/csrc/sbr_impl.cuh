@@ -268,6 +268,18 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
   group_sync(wg);   // shared memory is reused by the caller's next item
 }
 
+// Order-preserving integer key of an FP64 value (not NaN): the bits of x >= 0 as they
+// are, the magnitude bits of x < 0 inverted, compared as signed int64 (-0 below +0).
+// Applying it twice gives x back.  The FP64 compare-and-select is a long dependent
+// step on this part's narrow FP64 pipe; the integer minimum is not.
+__device__ __forceinline__ long long ord_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double ord_key(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll));
+}
+
 // One item of the FP64 best-response value: sign * min over the treeplex of
 // <q, sign * g> summed over the item's live hands, written to *value_partial.
 // gv as in SbrItemArgs: dense [S][ld] or (contrib) terminal contributions.  Same
@@ -284,11 +296,11 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
   const int hl = lane % kH, bl = lane / kH;
   const int h0 = blk * kH, h = h0 + hl;
   const bool live = h < g.H;
+  const double rz = (contrib && live) ? grz[h] : 0.0;
   {
     constexpr int kU = 4;
     const int kRowStep = kWarps * kSubLanes;
     const bool neg = sign < 0;
-    const double rz = (contrib && live) ? grz[h] : 0.0;
     for (int s0 = kSubLanes * warp + bl; s0 < S; s0 += kRowStep * kU) {
       double c0[kU], c1[kU];
       int e0[kU], e1[kU];
@@ -318,7 +330,7 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
             if (e0[u] < e1[u]) acc += c0[u];
             if (e0[u] + 1 < e1[u]) acc += c1[u];
             for (int e = e0[u] + 2; e < e1[u]; ++e) acc += __ldcg(gv + (size_t)e * ld + h);
-            v = neg ? (-rz) * acc : rz * acc;
+            v = neg ? -acc : acc;              // (r / Z of the hand scales the value at the end)
           } else if (neg) {
             v = -v;
           }
@@ -331,22 +343,27 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
   for (int l = tp.L - 1; l >= 0; --l) {
     for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
       const int s0 = tp.inf_first[j], n = tp.inf_n[j];
-      double m = INFINITY;
+      long long m = ord_key(INFINITY);      // the minimum on integer keys (integer pipes)
       for (int i = bl; i < n; i += kSubLanes) {
         const int s = s0 + i;
         double gh = G[s * kH + hl];
         for (int c = tp.child_ptr[s]; c < tp.child_ptr[s + 1]; ++c) gh += V[tp.child_idx[c] * kH + hl];
-        m = fmin(m, gh);
+        m = min(m, ord_key(gh));
       }
-      m = fmin(m, __shfl_xor_sync(0xffffffffu, m, kH));
-      if (bl == 0) V[j * kH + hl] = m;
+      m = min(m, __shfl_xor_sync(0xffffffffu, m, kH));
+      if (bl == 0) V[j * kH + hl] = ord_key(m);   // (the key map is its own inverse)
     }
     group_sync(wg);
   }
   if (warp == 0) {
     double v = 0.0;
-    if (live && bl == 0)
+    if (live && bl == 0) {
       for (int j = tp.level_ptr[0]; j < tp.level_ptr[1]; ++j) v += V[j * kH + hl];
+      // a hand's gradient rows all carry its factor r / Z > 0, so its min over the
+      // treeplex is r / Z times the min of the unscaled rows: one FP64 product per hand
+      // instead of one per (sequence, hand)
+      if (contrib) v *= rz;
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
     if (lane == 0) *value_partial = sign * v;
