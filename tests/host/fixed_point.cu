@@ -8,6 +8,7 @@
 //                                            r_hi, r_lo split from r as the library does)
 //   X <double bits> <double bits> <ex>    -> fixed point of r y 2^ex, FP64 y (fx_of64)
 //   c <v0> <ex>                           -> <FP64 bits> <FP32 bits> of v0 2^-ex (fx_to_f32_f64)
+//   C <v0> <ex>                           -> the same by fx_to_f32_f64_conv
 #include <cstdio>
 
 #include "grad_impl.cuh"
@@ -42,13 +43,14 @@ int main() {
         v = fx_of64(r, bits_f64(yb), ex);
       }
       std::printf("%lld\n", v);
-    } else if (op == 'c') {
+    } else if (op == 'c' || op == 'C') {
       long long v0;
       int ex;
       if (std::scanf("%lld %d", &v0, &ex) != 2) return 2;
       float f;
       double d;
-      fx_to_f32_f64(Fx{v0}, ex, f, d);
+      if (op == 'c') fx_to_f32_f64(Fx{v0}, ex, f, d);
+      else fx_to_f32_f64_conv(Fx{v0}, ex, f, d);
       std::printf("%llu %u\n", f64_bits(d), f32_bits(f));
     } else {
       return 2;

@@ -260,3 +260,13 @@ def test_both_roundings_are_correct(host):
                 assert abs(Fraction(conv(bits)) - exact) <= tiny, (v0, ex, P)
                 n_sub += P == 24
     assert n_sub > 50           # the subnormal FP32 results were exercised
+
+
+def test_the_two_conversion_forms_agree(host):
+    """The integer form (batches, merged items) and the conversion-instruction form (the
+    one-game driver's one-terminal items) give the same bits, so results do not depend on
+    which kernel formed a product."""
+    cases = conversion_cases(random.Random(5))
+    a = host([f"c {v0} {ex}" for v0, ex in cases])
+    b = host([f"C {v0} {ex}" for v0, ex in cases])
+    assert a == b
