@@ -36,11 +36,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "EGT iter/s"
-# dram__bytes_read.sum + dram__bytes_write.sum of one timed engine launch (100 iterations after an
-# L2 flush), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
-# -k regex:engine_kernel_one -s 3 -c 1 python bench.py --steps 3 --warmup 3 --no-ttg --cpu-seconds 0
-# --batch-games 0`; to be re-taken (or set to None) whenever the engine kernel changes.
-ENGINE_TRAFFIC_BYTES = 1642752   # dram read 1 253 632 + write 389 120 B, one ncu pass over one timed launch
+# dram__bytes_read.sum + dram__bytes_write.sum of one timed launch, from one ncu pass each
+# (to be re-taken, or set to None, whenever the engine kernels change):
+#   B="python bench.py --steps 3 --warmup 3 --no-ttg --cpu-seconds 0 --served-requests 0 --no-cpu-fast"
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
+#       -k regex:engine_kernel_one -s 3 -c 1 --csv --log-file engine_dram.csv $B --batch-games 0 --no-large
+#   (large game: -k regex:engine_kernel_one_merged -s 3 -c 1 ... $B --batch-games 0;
+#    64-game batch, both waves of the timed pass: -k regex:^engine_kernel$ -s 2 -c 2 ... $B --no-large)
+ENGINE_TRAFFIC_BYTES = 1620480       # full deck, 100 iterations: read 1 241 088 + write 379 392 B
+LARGE_TRAFFIC_BYTES = 10012160       # large game, 100 iterations: read 8 146 176 + write 1 865 984 B
+BATCH_TRAFFIC_BYTES = 20117706240    # 64 games x 200 iterations, two waves: read 0.68 GB + write 19.44 GB
 UNIT = "iter/s"
 WORKLOAD = "full-deck river endgame: 52 cards, 1081 hands/player, bets {0.5,1}xpot + all-in, raise cap 3, stack 10, pot 1, EGT/as"
 
@@ -364,31 +369,39 @@ def run_batched(args, local):
     games = [egt.Game(sp, device=local) for sp in specs]
     n = args.batch_iters
 
-    def timed(fn):
+    def timed(fn, setup=None):
+        # the solvers are re-initialised and the batch (if any) assembled before the timed
+        # region: a batch is built once and stepped many times, as a server does
         for g in games:
             g.solver_init(variant=egt.EGT_AS, alpha=0.01)
+        state = setup() if setup is not None else None
+        torch.cuda.synchronize()
         flush.fill_(1.0)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        out = fn()
+        out = fn(state)
         b.record(stream)
         torch.cuda.synchronize()
         return a.elapsed_time(b) * 1e-3, out
 
-    def one_per_launch():
+    def one_per_launch(_):
         for g in games:
             g.iterate(n, variant=egt.EGT_AS, gap_every=1)
 
-    def batched(launch_shape=None):
-        bt = egt.Batch(local)
-        if launch_shape is not None:
-            bt.shape = launch_shape
-        for g in games:
-            bt.add(g, variant=egt.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1)
+    def assemble(launch_shape=None):
+        def setup():
+            bt = egt.Batch(local)
+            if launch_shape is not None:
+                bt.shape = launch_shape
+            for g in games:
+                bt.add(g, variant=egt.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1)
+            return bt
+        return setup
+
+    def batched(bt):
         steps = bt.run(n_iters=n)
         shape = bt.launch_shape()
-        bt.close()
-        return steps, shape
+        return steps, shape, bt
 
     def tune():
         # egt_batch_tune on the batch's own first iterations (real steps; untimed here)
@@ -400,11 +413,14 @@ def run_batched(args, local):
         bt.close()
         return shape, rep
 
-    timed(batched)                                    # warm-up (module load, opt-in)
+    _, (_, _, bt0) = timed(batched, assemble())        # warm-up (module load, opt-in)
+    bt0.close()
     seq_s, _ = timed(one_per_launch)
-    bat_s, (steps, shape) = timed(batched)
-    _, (tuned_shape, tune_rep) = timed(tune)
-    tun_s, (tun_steps, tun_launch) = timed(lambda: batched(tuned_shape))
+    bat_s, (steps, shape, bt1) = timed(batched, assemble())
+    bt1.close()
+    _, (tuned_shape, tune_rep) = timed(lambda _: tune())
+    tun_s, (tun_steps, tun_launch, bt2) = timed(batched, assemble(tuned_shape))
+    bt2.close()
     total = len(games) * n
     state_bytes = sum(4 * g.ld * (2 * g.S[0] + 2 * g.S[1] + 4 * g.T) for g in games)
     alg = sum(algorithmic_bytes(g)["engine"] for g in games) * n
@@ -416,6 +432,7 @@ def run_batched(args, local):
         gbs = alg / sec / 1e9
         return {"bound": "hbm", "achieved": round(gbs, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(gbs / peak, 5), "peak_source": peak_kind, "alg_bytes": int(alg),
+                "traffic": BATCH_TRAFFIC_BYTES if (len(games) == 64 and n == 200) else None,
                 "how": "sum over members of the engine's algorithmic bytes per iteration x iterations, "
                        "over the pass's CUDA-event time"}
     return {"workload": f"{len(games)} mixed river endgames (20/52-card decks, raise caps 2-4, "
@@ -472,7 +489,7 @@ def run_large(args, local):
            "us_per_iter": round(launch_ms * 10.0, 2),
            "roofline": {"bound": "hbm", "kernel": "engine", "achieved": round(alg / (launch_ms * 1e-3) / 1e9, 2),
                         "peak": peak, "unit": "GB/s", "frac": round(alg / (launch_ms * 1e-3) / 1e9 / peak, 5),
-                        "peak_source": peak_kind, "alg_bytes_per_launch": int(alg),
+                        "peak_source": peak_kind, "traffic": LARGE_TRAFFIC_BYTES, "alg_bytes_per_launch": int(alg),
                         "avg_launch_us": round(launch_ms * 1e3, 2)},
            "time_to_gap": {"reached": rep["status"] == "EGT_OK", "iters": rep["iters"],
                            "gap_mbb": round(rep["gap_mbb"], 4), "backoffs": rep["backoffs"],

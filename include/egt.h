@@ -365,7 +365,9 @@ EGT_API egt_status egt_batch_destroy(egt_batch* batch);
 
 /* Add an initialised game with opts->variant, eps_mbb, gap_every, max_iters
  * (max_iters counted from now; replay and log are not accepted).  *slot (host):
- * its index, stable until egt_batch_remove; freed slots are reused. */
+ * its index, stable until egt_batch_remove; freed slots are reused.  The
+ * batch's launch arrays grow here (device and pinned host memory for the
+ * members), so the steps allocate nothing.  OOM if that allocation fails. */
 EGT_API egt_status egt_batch_add(egt_batch* batch, egt_game* game, const egt_solve_opts* opts,
                                  int32_t* slot);
 EGT_API egt_status egt_batch_remove(egt_batch* batch, int32_t slot);

@@ -428,6 +428,11 @@ egt_status egt_batch_add(egt_batch* B, egt_game* G, const egt_solve_opts* o, int
   m.active = 1;
   int k = 0;
   while (k < (int)B->members.size() && B->members[k].G) ++k;
+  // the launch arrays for every member, allocated here rather than in a step
+  {
+    DeviceGuard guard(B->device);
+    EGT_TRY(batch_reserve(B, std::max(k + 1, (int)B->members.size())));
+  }
   if (k == (int)B->members.size()) B->members.push_back(m);
   else B->members[k] = m;
   *slot = k;

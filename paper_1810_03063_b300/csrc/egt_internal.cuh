@@ -47,6 +47,13 @@ struct DevTerms {
   const int4* col;         // [n_col]
 };
 
+// Whether a group of `ctas` CTAs takes a product phase of T terminals over n_col opponent
+// columns in merged items (one per column): when that needs fewer rounds of items per
+// CTA than one item per terminal (each round lasts about one item).
+__host__ __device__ inline bool merge_items(int T, int n_col, int ctas) {
+  return ctas > 0 && (n_col + ctas - 1) / ctas < (T + ctas - 1) / ctas;
+}
+
 struct DevGame {
   int H, ld;               // hands, leading dimension (multiple of 32)
   int hand_size;           // 1 or 2

@@ -282,9 +282,11 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, Grp gr
 }
 
 // Product items of a phase of `player`: one per terminal when the group has a CTA for
-// every terminal (the phase then lasts one item), else one per opponent column, whose
-// showdown and fold terminals share the column's sums (less work per phase).  The
-// results are the same bits either way (the sums are exact).
+// every terminal, else one per opponent column, whose showdown and fold terminals share
+// the column's sums (less work per phase; in batches, where a group runs many items per
+// phase, this measured faster even where it saves no round of items).  The one-game
+// driver picks its kernel by merge_items instead.  The results are the same bits either
+// way (the sums are exact).
 __device__ __forceinline__ int prod_items(const DevTerms& tm, Grp gr, bool& merged) {
   merged = gr.size < tm.n;
   return merged ? tm.n_col : tm.n;
@@ -870,7 +872,8 @@ cudaError_t engine_launch_one(const EngineJob& job, int grid, size_t smem, unsig
   unsigned int ex = extra;
   unsigned long long lim = limit_ns;
   void* args[] = {&j, &ex, &lim};
-  const bool merged = grid < std::max(job.g.terms[0].n, job.g.terms[1].n);
+  const bool merged = merge_items(job.g.terms[0].n, job.g.terms[0].n_col, grid) ||
+                      merge_items(job.g.terms[1].n, job.g.terms[1].n_col, grid);
   return cudaLaunchCooperativeKernel(merged ? (const void*)engine_kernel_one_merged : (const void*)engine_kernel_one,
                                      dim3(grid), dim3(kItemThreads), args, smem, st);
 }
