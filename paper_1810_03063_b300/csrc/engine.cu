@@ -103,7 +103,8 @@ __device__ bool grid_sync(const GridBar& b, unsigned long long& k, PhaseClock* c
         }
       }
     }
-    if (ld_volatile(b.status) != 0) ok = 0;
+    // no status read on the way out: a CTA that timed out never arrives again, and
+    // the others see its status in the loop above at their next barrier
     ok_s = ok;
   }
   __syncthreads();
@@ -132,10 +133,15 @@ __device__ __forceinline__ bool grid_sync_verdict(const GridBar& b, unsigned lon
     unsigned long long w = 0;
     unsigned int polls = 0;
     unsigned long long t0 = 0;
+    // the deciding CTA publishes the word before it arrives, so once every arrival
+    // is in (acquire) the word is read once; it is polled only while still stale
+    bool all = !group;
     for (;;) {
-      const bool all = !group || ld_acquire(b.arrive) >= target;
-      w = ld_acquire(word);
-      if (all && (w >> 8) == tag) break;
+      if (!all) all = ld_acquire(b.arrive) >= target;
+      if (all) {
+        w = ld_acquire(word);
+        if ((w >> 8) == tag) break;
+      }
       if ((++polls & 1023u) == 0) {
         const unsigned long long now = global_ns();
         if (t0 == 0) {
@@ -151,7 +157,6 @@ __device__ __forceinline__ bool grid_sync_verdict(const GridBar& b, unsigned lon
         }
       }
     }
-    if (group && ld_volatile(b.status) != 0) ok = 0;
     ok_s = ok;
     code_s = (int)(w & 0xffu);
   }
