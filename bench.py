@@ -42,10 +42,11 @@ METRIC = "EGT iter/s"
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
 #       -k regex:engine_kernel_one -s 3 -c 1 --csv --log-file engine_dram.csv $B --batch-games 0 --no-large
 #   (large game: -k regex:engine_kernel_one_merged -s 3 -c 1 ... $B --batch-games 0;
-#    64-game batch, both waves of the timed pass: -k regex:^engine_kernel$ -s 2 -c 2 ... $B --no-large)
-ENGINE_TRAFFIC_BYTES = 1620480       # full deck, 100 iterations: read 1 241 088 + write 379 392 B
-LARGE_TRAFFIC_BYTES = 10012160       # large game, 100 iterations: read 8 146 176 + write 1 865 984 B
-BATCH_TRAFFIC_BYTES = 20117706240    # 64 games x 200 iterations, two waves: read 0.68 GB + write 19.44 GB
+#    64-game batch, the three 128 MB waves of the timed pass (the three warm-up waves
+#    skipped): -k regex:^engine_kernel$ -s 3 -c 3 ... $B --no-large)
+ENGINE_TRAFFIC_BYTES = 1766400       # full deck, 100 iterations: read 1 350 912 + write 415 488 B
+LARGE_TRAFFIC_BYTES = 10021120       # large game, 100 iterations: read 8 081 152 + write 1 939 968 B
+BATCH_TRAFFIC_BYTES = 30917168896    # 64 games x 200 iterations, three waves: read 0.78 GB + write 30.13 GB
 UNIT = "iter/s"
 WORKLOAD = "full-deck river endgame: 52 cards, 1081 hands/player, bets {0.5,1}xpot + all-in, raise cap 3, stack 10, pot 1, EGT/as"
 
