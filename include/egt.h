@@ -414,6 +414,11 @@ EGT_API egt_status egt_batch_launch_shape(const egt_batch* batch, int32_t* group
  *             (egt_dims.device_bytes) / wave_mb MB) consecutive waves of about
  *             equal bytes, one launch each, so that a wave's state can stay in
  *             L2 (default 128, about the B300's 126 MB L2); 0: all in one launch.
+ *   wave_min: >= 1: at most (active members / wave_min) waves, at least one,
+ *             so that every wave keeps about wave_min members: a wave of few
+ *             members gives each of them many CTAs with few items apiece, the
+ *             way one game alone runs, and loses more to that than L2 residency
+ *             gains (default 16; 1: waves by bytes alone).
  * No choice changes any member's results (they come from exact products and
  * fixed-order sums); only the speed differs. */
 typedef struct {
@@ -422,6 +427,7 @@ typedef struct {
   int32_t grid_pct;
   int32_t pack;
   int32_t wave_mb;
+  int32_t wave_min;
 } egt_launch_shape;
 
 /* Set / read the batch's launch shape (host structs).  Set returns

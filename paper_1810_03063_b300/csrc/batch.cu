@@ -32,7 +32,7 @@ struct egt_batch {
   EngineGroup* plan_host = nullptr;
   int cap = 0;
   int last_group = 0, last_grid = 0;
-  egt_launch_shape shape{3, 1, 100, 0, 128};
+  egt_launch_shape shape{3, 1, 100, 0, 128, 16};
   cudaEvent_t ev[2] = {nullptr, nullptr};   // timing of tuning trials (created on first use)
 };
 
@@ -40,7 +40,7 @@ namespace {
 
 bool shape_ok(const egt_launch_shape& x) {
   return x.share >= 0 && x.share <= 4 && (x.pairs == 0 || x.pairs == 1) && x.grid_pct >= 1 && x.grid_pct <= 100 &&
-         (x.pack == 0 || x.pack == 1) && x.wave_mb >= 0;
+         (x.pack == 0 || x.pack == 1) && x.wave_mb >= 0 && x.wave_min >= 1;
 }
 
 void batch_free_arrays(egt_batch* B) {
@@ -342,8 +342,8 @@ egt_status launch_members(egt_batch* B, const std::vector<int>& act, int32_t n_i
 
 // One batch step under launch shape `sh`: the active members in one launch, or
 // (sh.wave_mb > 0) in k = ceil(total device bytes / wave_mb MB) consecutive waves of
-// about equal bytes, one launch each, so that a wave's state can stay in L2.  ms /
-// done add up over the waves.
+// about equal bytes, one launch each, so that a wave's state can stay in L2, but no
+// more waves than (active members / sh.wave_min).  ms / done add up over the waves.
 egt_status batch_launch(egt_batch* B, int32_t n_iters, int32_t group, const egt_launch_shape& sh,
                         int32_t* n_active, cudaStream_t st, float* ms, long long* done) {
   if (n_iters <= 0) return fail(EGT_ERR_INVALID_ARG, "n_iters must be > 0");
@@ -356,7 +356,7 @@ egt_status batch_launch(egt_batch* B, int32_t n_iters, int32_t group, const egt_
   const double budget = (double)((size_t)sh.wave_mb << 20);
   double total = 0.0;
   for (int k : act) total += (double)B->members[k].G->device_bytes;
-  const int waves = std::max(1, (int)std::ceil(total / budget));
+  const int waves = std::max(1, std::min((int)std::ceil(total / budget), (int)act.size() / sh.wave_min));
   const double target = total / waves;
   if (done) *done = 0;
   if (ms) *ms = 0.f;
@@ -472,11 +472,11 @@ egt_status egt_batch_tune(egt_batch* B, int32_t n_iters, int32_t reps, egt_tune_
   egt_tune_report r;
   std::memset(&r, 0, sizeof(r));
   r.best = -1;
-  for (int share : {4, 3, 2, 1, 0}) r.shape[r.n++] = egt_launch_shape{share, 1, 100, 0, 0};
-  for (int share : {4, 3, 2}) r.shape[r.n++] = egt_launch_shape{share, 0, 100, 0, 0};
-  r.shape[r.n++] = egt_launch_shape{3, 1, 75, 0, 0};
-  r.shape[r.n++] = egt_launch_shape{4, 1, 100, 1, 0};
-  for (int mb : {64, 96, 128}) r.shape[r.n++] = egt_launch_shape{3, 1, 100, 0, mb};   // L2: 126 MB
+  for (int share : {4, 3, 2, 1, 0}) r.shape[r.n++] = egt_launch_shape{share, 1, 100, 0, 0, 16};
+  for (int share : {4, 3, 2}) r.shape[r.n++] = egt_launch_shape{share, 0, 100, 0, 0, 16};
+  r.shape[r.n++] = egt_launch_shape{3, 1, 75, 0, 0, 16};
+  r.shape[r.n++] = egt_launch_shape{4, 1, 100, 1, 0, 16};
+  for (int mb : {64, 96, 128}) r.shape[r.n++] = egt_launch_shape{3, 1, 100, 0, mb, 16};   // L2: 126 MB
   static_assert(5 + 3 + 1 + 1 + 3 <= EGT_TUNE_MAX, "tuning candidates");
   double best = 0.0;
   for (int k = 0; k < r.n; ++k) {

@@ -104,7 +104,7 @@ class Checkpoint(C.Structure):
 
 class LaunchShape(C.Structure):
     _fields_ = [("share", C.c_int32), ("pairs", C.c_int32), ("grid_pct", C.c_int32), ("pack", C.c_int32),
-                ("wave_mb", C.c_int32)]
+                ("wave_mb", C.c_int32), ("wave_min", C.c_int32)]
 
 
 TUNE_MAX = 16
@@ -557,17 +557,18 @@ class Batch:
 
     @property
     def shape(self):
-        """The launch shape of group-0 steps: dict(share, pairs, grid_pct, pack, wave_mb)."""
+        """The launch shape of group-0 steps: dict(share, pairs, grid_pct, pack, wave_mb, wave_min)."""
         x = LaunchShape()
         _check(lib.egt_batch_get_shape(self._h, C.byref(x)))
-        return dict(share=x.share, pairs=x.pairs, grid_pct=x.grid_pct, pack=x.pack, wave_mb=x.wave_mb)
+        return dict(share=x.share, pairs=x.pairs, grid_pct=x.grid_pct, pack=x.pack, wave_mb=x.wave_mb,
+                    wave_min=x.wave_min)
 
     @shape.setter
     def shape(self, value):
         """Set some or all of the fields; the others keep their current values."""
         cur = self.shape
         cur.update(value)
-        x = LaunchShape(cur["share"], cur["pairs"], cur["grid_pct"], cur["pack"], cur["wave_mb"])
+        x = LaunchShape(cur["share"], cur["pairs"], cur["grid_pct"], cur["pack"], cur["wave_mb"], cur["wave_min"])
         _check(lib.egt_batch_set_shape(self._h, C.byref(x)))
 
     def tune(self, n_iters=20, reps=1, stream=None):
@@ -576,7 +577,8 @@ class Batch:
         r = TuneReport()
         _check(lib.egt_batch_tune(self._h, n_iters, reps, C.byref(r), _stream(stream)))
         cands = [dict(share=r.shape[k].share, pairs=r.shape[k].pairs, grid_pct=r.shape[k].grid_pct,
-                      pack=r.shape[k].pack, wave_mb=r.shape[k].wave_mb, us_per_iter=r.us_per_iter[k],
+                      pack=r.shape[k].pack, wave_mb=r.shape[k].wave_mb, wave_min=r.shape[k].wave_min,
+                      us_per_iter=r.us_per_iter[k],
                       iters=r.iters[k]) for k in range(r.n)]
         return dict(best=r.best, candidates=cands)
 

@@ -178,7 +178,7 @@ def test_autotuned_shapes_leave_results_bitwise_unchanged(egtlib):
         g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
         slots.append(b.add(g, variant=egtlib.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1))
         games.append(g)
-    assert b.shape == dict(share=3, pairs=1, grid_pct=100, pack=0, wave_mb=128)
+    assert b.shape == dict(share=3, pairs=1, grid_pct=100, pack=0, wave_mb=128, wave_min=16)
     rep = b.tune(n_iters=3, reps=1)                # 13 candidates x 3 iterations = 39 of the 60
     cands = rep["candidates"]
     assert len(cands) == 13 and 0 <= rep["best"] < 13
@@ -186,7 +186,7 @@ def test_autotuned_shapes_leave_results_bitwise_unchanged(egtlib):
     assert all(c["iters"] == 3 * len(specs) for c in timed)    # every member ran every trial
     best = cands[rep["best"]]
     assert best["us_per_iter"] == min(c["us_per_iter"] for c in timed) > 0
-    assert b.shape == {k: best[k] for k in ("share", "pairs", "grid_pct", "pack", "wave_mb")}
+    assert b.shape == {k: best[k] for k in ("share", "pairs", "grid_pct", "pack", "wave_mb", "wave_min")}
     b.run(n_iters=7)
     for sp, g, s in zip(specs, games, slots):
         xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, n, 1)
@@ -202,8 +202,10 @@ def test_autotuned_shapes_leave_results_bitwise_unchanged(egtlib):
         b.shape = dict(share=5, pairs=1, grid_pct=100)
     with pytest.raises(egtlib.EGTError):
         b.shape = dict(share=2, pairs=1, grid_pct=0)
-    b.shape = dict(share=0, pairs=0, grid_pct=50, pack=1, wave_mb=3)
-    assert b.shape == dict(share=0, pairs=0, grid_pct=50, pack=1, wave_mb=3)
+    with pytest.raises(egtlib.EGTError):
+        b.shape = dict(wave_min=0)
+    b.shape = dict(share=0, pairs=0, grid_pct=50, pack=1, wave_mb=3, wave_min=2)
+    assert b.shape == dict(share=0, pairs=0, grid_pct=50, pack=1, wave_mb=3, wave_min=2)
     b.close()
 
 
@@ -295,7 +297,7 @@ def test_waves_keep_results(egtlib):
         g.solver_init(variant=egtlib.EGT_AS, alpha=0.01)
         b.add(g, variant=egtlib.EGT_AS, eps_mbb=0.0, max_iters=n, gap_every=1)
         games.append(g)
-    b.shape = dict(share=3, pairs=1, grid_pct=100, pack=0, wave_mb=1)   # about one member per wave
+    b.shape = dict(share=3, pairs=1, grid_pct=100, pack=0, wave_mb=1, wave_min=1)   # about one member per wave
     b.run(n_iters=6)
     for sp, g in zip(specs, games):
         xs, ys, rs = solo(egtlib, sp, egtlib.EGT_AS, 0.0, n, 1)
