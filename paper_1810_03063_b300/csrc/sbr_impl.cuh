@@ -125,6 +125,51 @@ __device__ __forceinline__ double reduce_partials(const double* p, int n, int la
 constexpr int kSubLanes = 32 / kSbrHands;
 static_assert(kSbrHands * kSubLanes == 32, "an item's hands times sub-lanes fill a warp");
 
+// A level with more simplexes than this runs one simplex per half warp (each lane one
+// hand, all branches in turn) instead of one per warp with the branches split over the
+// two sub-lanes: the warps then hold twice as many independent simplexes, where one warp
+// would otherwise take several in a row.  A fixed count, so that an item run by the
+// whole CTA and one run by a warp half take the same form on every level.
+constexpr int kSplitLevel = 16;
+
+// The simplex problem of simplex j (Sec. 5) for hand lane hl, all branches by one lane:
+// g_hat_i = g_i + child values into G, then q_bar into G and the value into V.  The sums
+// over branches are kept per branch parity and added at the end: the order in which the
+// two sub-lanes of the one-simplex-per-warp form add them, so both forms give the same
+// bits.
+__device__ __forceinline__ void sbr_simplex_serial(const TpxTab& tp, int j, float* G, float* V, const float* tj,
+                                                   const float* itj, int hl) {
+  constexpr int kH = kSbrHands;
+  const int s0 = tp.inf_first[j], n = tp.inf_n[j];
+  float m = INFINITY;
+  for (int i = 0; i < n; ++i) {
+    const int s = s0 + i;
+    float gh = G[s * kH + hl];
+    for (int c = tp.child_ptr[s]; c < tp.child_ptr[s + 1]; ++c) gh += V[tp.child_idx[c] * kH + hl];
+    G[s * kH + hl] = gh;
+    m = fminf(m, gh);
+  }
+  const float it = itj[j];
+  float sum0 = 0.f, sum1 = 0.f, X0 = 0.f, X1 = 0.f;
+  for (int i = 0; i < n; ++i) {
+    float* u = G + (s0 + i) * kH + hl;
+    const float d = -(*u - m) * it;
+    const float e = expf(d);
+    if (i & 1) {
+      X1 += expm1f(d);
+      sum1 += e;
+    } else {
+      X0 += expm1f(d);
+      sum0 += e;
+    }
+    *u = e;
+  }
+  const float sum = sum0 + sum1, X = X0 + X1;
+  const float inv = 1.f / sum;
+  for (int i = 0; i < n; ++i) G[(s0 + i) * kH + hl] *= inv;
+  V[j * kH + hl] = m - tj[j] * log1pf(X / (float)n);
+}
+
 // The warps that run an item: all of the CTA (bar = 0: __syncthreads), or half of it
 // with its own named barrier (bar = 1 or 2) so that two items run side by side.
 struct WarpGroup {
@@ -209,6 +254,12 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
   group_sync(wg);
 
   for (int l = tp.L - 1; l >= 0; --l) {
+    if (tp.level_ptr[l + 1] - tp.level_ptr[l] > kSplitLevel) {
+      for (int j = tp.level_ptr[l] + kSubLanes * warp + bl; j < tp.level_ptr[l + 1]; j += kSubLanes * kWarps)
+        sbr_simplex_serial(tp, j, G, V, tj, itj, hl);
+      group_sync(wg);
+      continue;
+    }
     for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
       const int s0 = tp.inf_first[j], n = tp.inf_n[j];
       float m = INFINITY;
@@ -341,6 +392,22 @@ __device__ inline void br64_item(const DevGame& g, const TpxTab& tp, int blk, co
   }
   group_sync(wg);
   for (int l = tp.L - 1; l >= 0; --l) {
+    if (tp.level_ptr[l + 1] - tp.level_ptr[l] > kSplitLevel) {
+      // one simplex per half warp (the minimum is exact: the same value in either form)
+      for (int j = tp.level_ptr[l] + kSubLanes * warp + bl; j < tp.level_ptr[l + 1]; j += kSubLanes * kWarps) {
+        const int s0 = tp.inf_first[j], n = tp.inf_n[j];
+        long long m = ord_key(INFINITY);
+        for (int i = 0; i < n; ++i) {
+          const int s = s0 + i;
+          double gh = G[s * kH + hl];
+          for (int c = tp.child_ptr[s]; c < tp.child_ptr[s + 1]; ++c) gh += V[tp.child_idx[c] * kH + hl];
+          m = min(m, ord_key(gh));
+        }
+        V[j * kH + hl] = ord_key(m);
+      }
+      group_sync(wg);
+      continue;
+    }
     for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
       const int s0 = tp.inf_first[j], n = tp.inf_n[j];
       long long m = ord_key(INFINITY);      // the minimum on integer keys (integer pipes)
