@@ -45,6 +45,8 @@ struct DevTerms {
   // terminal of a kind (every column has at most one of each)
   int n_col;
   const int4* col;         // [n_col]
+  const int* col_order;    // [n_col] the items in descending order of work (showdown and
+                           // fold, showdown, fold; column order within each)
 };
 
 // Whether a group of `ctas` CTAs takes a product phase of T terminals over n_col opponent

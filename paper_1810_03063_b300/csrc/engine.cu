@@ -303,13 +303,26 @@ __device__ __forceinline__ int prod_items(const DevTerms& tm, Grp gr, bool& merg
 // kProd selects the product items: 0, one terminal per item (term_item_whole), the
 // one-game kernel's items when every terminal of a phase has its own CTA; 2,
 // prod_item, merged per opponent column when the group has fewer CTAs than
-// terminals.  The results are the same bits either way.
+// terminals, the CTAs taking the items round-robin (batches); 3, the same items in
+// rounds of alternating direction (round_unit: the one-game kernel when its CTAs are
+// fewer than its terminals).  The results are the same bits in every form.
 template <int kProd>
 __device__ __forceinline__ void one_prod_item(const DevGame& g, const GradTab& tb, int player, int item,
                                               bool merged, const float* in, float* c32, double* c64,
                                               unsigned char* sm) {
   if constexpr (kProd == 0) term_item_whole<float>(g, tb, player, item, in, c32, c64, sm);
   else prod_item<float>(g, tb, player, item, merged, in, c32, c64, sm);
+}
+
+// The unit (item, or pair of items) this CTA takes in round r of `rounds` rounds of
+// gr.size units: the rounds alternate direction and the last one, which may be partial,
+// runs from rank 0 up, so the group's last rank (the deciding CTA) holds the fewest
+// units, and units in descending order of work (merged product items are: a showdown
+// and a fold, a showdown alone, a fold alone: DevTerms::col_order) give every CTA
+// about the same total, where taking them round-robin gives rank 0 the largest of
+// every round.
+__device__ __forceinline__ int round_unit(int r, int rounds, Grp gr) {
+  return r * gr.size + (((rounds - 1 - r) & 1) ? gr.size - 1 - gr.rank : gr.rank);
 }
 
 template <int kProd>
@@ -323,22 +336,40 @@ __device__ __forceinline__ void run_grad(const DevGame& g, const Tabs& tb, Grp g
     n = tm.n;
   }
   if (!(pair_ok && 2 * gr.size <= n)) {
-    for (int item = gr.rank; item < n; item += gr.size)
-      one_prod_item<kProd>(g, tb.grad, player, item, merged, in, c32, c64, sm);
+    if constexpr (kProd == 3) {
+      const int rounds = (n + gr.size - 1) / gr.size;
+      for (int r = 0; r < rounds; ++r) {
+        const int u = round_unit(r, rounds, gr);
+        if (u < n) one_prod_item<kProd>(g, tb.grad, player, merged ? tm.col_order[u] : u, merged, in, c32, c64, sm);
+      }
+    } else {
+      for (int item = gr.rank; item < n; item += gr.size)
+        one_prod_item<kProd>(g, tb.grad, player, item, merged, in, c32, c64, sm);
+    }
     return;
   }
   constexpr int kHalf = kItemThreads / 64;
   const int half = (int)(threadIdx.x >> 5) >= kHalf ? 1 : 0;
   unsigned char* hs = sm + half * gradimpl::align16(grad_item_smem(g));
-  for (int base = 2 * gr.rank; base < n; base += 2 * gr.size)
+  auto pair_item = [&](int base) {
     if (base + half < n) {
-      if constexpr (kProd == 0)
+      if constexpr (kProd == 0) {
         term_item_whole<float, kItemThreads / 2>(g, tb.grad, player, base + half, in, c32, c64, hs,
                                                  half * kHalf, 1 + half);
-      else
-        prod_item<float, kItemThreads / 2>(g, tb.grad, player, base + half, merged, in, c32, c64, hs,
+      } else {
+        const int item = kProd == 3 && merged ? tm.col_order[base + half] : base + half;
+        prod_item<float, kItemThreads / 2>(g, tb.grad, player, item, merged, in, c32, c64, hs,
                                            half * kHalf, 1 + half);
+      }
     }
+  };
+  if constexpr (kProd == 3) {
+    const int n_pairs = (n + 1) / 2;
+    const int rounds = (n_pairs + gr.size - 1) / gr.size;
+    for (int r = 0; r < rounds; ++r) pair_item(2 * round_unit(r, rounds, gr));
+  } else {
+    for (int base = 2 * gr.rank; base < n; base += 2 * gr.size) pair_item(base);
+  }
 }
 
 // Item `item` of player p's FP64 best response of the residual (player 0: min over x of
@@ -826,7 +857,7 @@ __global__ void __launch_bounds__(kItemThreads, 1)
 __global__ void __launch_bounds__(kItemThreads, 1)
     engine_kernel_one_merged(EngineJob job, unsigned int extra, unsigned long long limit_ns) {
   extern __shared__ __align__(16) unsigned char smem_all[];
-  engine_job<2>(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x}, job.pair,
+  engine_job<3>(job.g, job.b, job.ctl, Grp{(int)blockIdx.x, (int)gridDim.x}, job.pair,
                 (unsigned long long)gridDim.x + extra, limit_ns, smem_all);
 }
 
