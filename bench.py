@@ -44,9 +44,9 @@ METRIC = "EGT iter/s"
 #   (large game: -k regex:engine_kernel_one_merged -s 3 -c 1 ... $B --batch-games 0;
 #    64-game batch, the three 128 MB waves of the timed pass (the three warm-up waves
 #    skipped): -k regex:^engine_kernel$ -s 3 -c 3 ... $B --no-large)
-ENGINE_TRAFFIC_BYTES = 1766400       # full deck, 100 iterations: read 1 350 912 + write 415 488 B
-LARGE_TRAFFIC_BYTES = 10021120       # large game, 100 iterations: read 8 081 152 + write 1 939 968 B
-BATCH_TRAFFIC_BYTES = 30917168896    # 64 games x 200 iterations, three waves: read 0.78 GB + write 30.13 GB
+ENGINE_TRAFFIC_BYTES = None          # full deck, 100 iterations (re-capture after the kernel change)
+LARGE_TRAFFIC_BYTES = None           # large game, 100 iterations (re-capture after the kernel change)
+BATCH_TRAFFIC_BYTES = None           # 64 games x 200 iterations, three waves (re-capture after the kernel change)
 UNIT = "iter/s"
 WORKLOAD = "full-deck river endgame: 52 cards, 1081 hands/player, bets {0.5,1}xpot + all-in, raise cap 3, stack 10, pot 1, EGT/as"
 
@@ -90,6 +90,8 @@ def parse():
     ap.add_argument("--served-requests", type=int, default=32,
                     help="requests of the short served stream in the default line (0: skip)")
     ap.add_argument("--served-rate", type=float, default=100.0, help="its arrival rate (requests/s)")
+    ap.add_argument("--served-sweep", default="10,500",
+                    help="further arrival rates for the default line's served stream ('' for none)")
     ap.add_argument("--no-large", action="store_true", help="skip the large endgame in the default line")
     ap.add_argument("--no-cpu-fast", action="store_true", help="skip the C++/OpenMP CPU comparator")
     ap.add_argument("--serve-rates", default="10,100,500", help="arrival rates (requests/s)")
@@ -502,19 +504,25 @@ def run_large(args, local):
 def run_served_short(args, local):
     """A short served stream for the default line: --served-requests requests arriving as a
     Poisson stream at --served-rate through egt_server_* (continuous batching), against the same
-    requests solved one at a time with egt_solve."""
+    requests solved one at a time with egt_solve; beside it the same number of requests at each
+    rate of --served-sweep (the low and high ends of the 10-500 requests/s range)."""
     import argparse as _ap
     sub = _ap.Namespace(**vars(args))
-    sub.serve_rates = str(args.served_rate)
+    sweep = [float(v) for v in args.served_sweep.split(",") if v.strip()] if args.served_sweep else []
+    sweep = [v for v in sweep if v != args.served_rate]
+    # the main rate last: the one-at-a-time comparison runs on the last rate's requests
+    sub.serve_rates = ",".join(str(v) for v in sweep + [args.served_rate])
     sub.serve_requests = args.served_requests
     r = run_serve(sub, local)
-    rate = r["rates"][0]
+    rate = r["rates"][-1]
     seq = r["one_game_per_launch"]["solves_per_s"]
     return {"metric": "served solves/s, p50/p99 latency", "workload": r["workload"], "rate": rate["rate"],
             "requests": rate["requests"], "reached": rate["reached"], "solves_per_s": rate["solves_per_s"],
             "latency_p50_s": rate["latency_p50_s"], "latency_p99_s": rate["latency_p99_s"],
             "iters_per_launch": r["iters_per_launch"], "one_game_per_launch_solves_per_s": seq,
-            "speedup": round(rate["solves_per_s"] / seq, 3) if seq else None}
+            "speedup": round(rate["solves_per_s"] / seq, 3) if seq else None,
+            "sweep": [{k: x[k] for k in ("rate", "requests", "reached", "solves_per_s", "latency_p50_s",
+                                         "latency_p99_s")} for x in r["rates"]]}
 
 
 def serve_requests(n, rate, seed):

@@ -55,3 +55,5 @@ def test_gpu_arm_line_has_every_key():
     assert cf["value"] > 0 and cf["cores"] >= 1 and cf["time_to_gap"]["iters"] > 0
     sv = d["served"]
     assert sv["requests"] == 3 and sv["solves_per_s"] > 0 and sv["latency_p99_s"] >= sv["latency_p50_s"] > 0
+    assert sorted(x["rate"] for x in sv["sweep"]) == [10.0, 100.0, 500.0]
+    assert all(x["requests"] == 3 and x["solves_per_s"] > 0 for x in sv["sweep"])
