@@ -215,18 +215,36 @@ egt_status upload(egt_game* G, const egt_game_desc* d, bool to_device, cudaStrea
   if (!(Z > 0)) return fail(EGT_ERR_INVALID_ARG, "no compatible hand pair has positive probability (Z = 0)");
   G->Z = Z;
 
-  // ||A|| = max_ij |A_ij|: largest |coef| of each terminal kind times the largest chance weight
+  // ||A|| = max_ij |A_ij|: largest |coef| of each terminal kind times the largest chance
+  // weight r1(a) r2(b) over compatible pairs (any pair for folds, pairs of unequal
+  // strength for showdowns).  For each a the largest r2(b) over the b it may meet gives
+  // its largest product (a product with r1(a) >= 0 is monotone in r2(b)), so each a scans
+  // the hands in descending r2 only past those that share a card with it (at most two
+  // card lists) and, for showdowns, its tie group as well.
   double max_any = 0, max_diff = 0;
-  for (int a = 0; a < H; ++a)
-    for (int b = 0; b < H; ++b) {
-      const bool share = hcard[a].x == hcard[b].x || (k == 2 && (hcard[a].x == hcard[b].y ||
-                                                                 hcard[a].y == hcard[b].x ||
-                                                                 hcard[a].y == hcard[b].y));
-      if (share) continue;
-      const double w = r[0][a] * r[1][b];
-      max_any = std::max(max_any, w);
-      if (d->strength[G->order[a]] != d->strength[G->order[b]]) max_diff = std::max(max_diff, w);
+  {
+    std::vector<int> by_r1(H);
+    std::iota(by_r1.begin(), by_r1.end(), 0);
+    std::stable_sort(by_r1.begin(), by_r1.end(), [&](int u, int v) { return r[1][u] > r[1][v]; });
+    for (int a = 0; a < H; ++a) {
+      bool got_any = false;
+      for (int b : by_r1) {
+        const bool share = hcard[a].x == hcard[b].x || (k == 2 && (hcard[a].x == hcard[b].y ||
+                                                                   hcard[a].y == hcard[b].x ||
+                                                                   hcard[a].y == hcard[b].y));
+        if (share) continue;
+        const double w = r[0][a] * r[1][b];
+        if (!got_any) {
+          max_any = std::max(max_any, w);
+          got_any = true;
+        }
+        if (d->strength[G->order[a]] != d->strength[G->order[b]]) {
+          max_diff = std::max(max_diff, w);
+          break;
+        }
+      }
     }
+  }
   double na = 0;
   for (auto& t : C.term) na = std::max(na, std::fabs(t.coef) * (t.kind == 0 ? max_any : max_diff));
   G->normA = na / Z;
