@@ -266,10 +266,11 @@ __device__ __forceinline__ void for_items(const DevGame& g, Grp gr, int n_items,
     if (base + half < n_items) f(base + half, wg, hs);
 }
 
+template <int kH = kSbrHands>
 __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, Grp gr, bool pair_ok, int player,
                                         const float* gv, double mu, const float* old, float tau, float* out,
                                         double* partials, unsigned char* sm) {
-  const int NB = g.ld / kSbrHands;
+  const int NB = g.ld / kH;
   const TpxTab tp = pick(tb, player);
   for_items(g, gr, NB, pair_ok, sm, [&](int item, const WarpGroup& wg, unsigned char* ism) {
     SbrItemArgs a;
@@ -282,8 +283,24 @@ __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, Grp gr
     a.tau = tau;
     a.out = out;
     a.value_partial = partials ? partials + item : nullptr;
-    sbr_item(g, tp, item, a, reinterpret_cast<float*>(ism), wg);
+    sbr_item<kH>(g, tp, item, a, reinterpret_cast<float*>(ism), wg);
   });
+}
+
+// An SBR phase without value partials: in the one-game merged kernel, 8-hand items where
+// one round of them fits the group (twice the items, each half the work: the large
+// game's 136 items on 148 CTAs instead of 68), else 16-hand items.  The same bits.
+template <int kProd>
+__device__ __forceinline__ void run_sbr_plain(const DevGame& g, const Tabs& tb, Grp gr, bool pair_ok, int player,
+                                              const float* gv, double mu, const float* old, float tau, float* out,
+                                              unsigned char* sm) {
+  if constexpr (kProd == 3) {
+    if (!pair_ok && g.ld / 8 <= gr.size) {
+      run_sbr<8>(g, tb, gr, pair_ok, player, gv, mu, old, tau, out, nullptr, sm);
+      return;
+    }
+  }
+  run_sbr<kSbrHands>(g, tb, gr, pair_ok, player, gv, mu, old, tau, out, nullptr, sm);
 }
 
 // Product items of a phase of `player`: one per terminal when the group has a CTA for
@@ -697,7 +714,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
 
     // v_hat = (1 - tau) v + tau v_mu(other)
     if (!have_hat) {
-      run_sbr(g, tb, gr, pair_ok, m, g_me, sc.mu_me, v_me, sc.tau, t_me, nullptr, sm);
+      run_sbr_plain<kProd>(g, tb, gr, pair_ok, m, g_me, sc.mu_me, v_me, sc.tau, t_me, sm);
       if (!phase_end(bar, bk, clk, 0, clock_cta)) return;
     }
     phase_cut(clk, 8, clock_cta);
@@ -722,7 +739,7 @@ __device__ __forceinline__ void engine_job(const DevGame& g, const EngineBufs& b
       if (lead) load_sched(sc_next, &ctl->next);   // (first read at the end of the attempt)
     }
     // other_+ = (1 - tau) other + tau other_mu(v_hat)
-    run_sbr(g, tb, gr, pair_ok, ot, t_ot, sc.mu_ot, v_ot, sc.tau, v_ot_n, nullptr, sm);
+    run_sbr_plain<kProd>(g, tb, gr, pair_ok, ot, t_ot, sc.mu_ot, v_ot, sc.tau, v_ot_n, sm);
     if (!phase_end(bar, bk, clk, 2, clock_cta)) return;
     run_grad<kProd>(g, tb, gr, pair_terms, m, v_ot_n, g_me_n, g64_me, sm);   // my loss gradient at other_+
     if (!phase_end(bar, bk, clk, 3, clock_cta)) return;

@@ -43,9 +43,10 @@ struct SbrItemArgs {
 };
 
 // (the shared memory below excludes the staged tables)
+template <int kH = kSbrHands>
 __host__ __device__ inline size_t sbr_item_smem(const DevGame& g, int player) {
   const DevTpx& tp = g.tpx[player];
-  return ((size_t)2 * tp.S * kSbrHands + (size_t)tp.J * kSbrHands + 2 * (size_t)tp.J) * sizeof(float);
+  return ((size_t)2 * tp.S * kH + (size_t)tp.J * kH + 2 * (size_t)tp.J) * sizeof(float);
 }
 
 __host__ __device__ inline size_t br_item_smem(const DevGame& g, int player) {
@@ -137,9 +138,9 @@ constexpr int kSplitLevel = 16;
 // over branches are kept per branch parity and added at the end: the order in which the
 // two sub-lanes of the one-simplex-per-warp form add them, so both forms give the same
 // bits.
+template <int kH>
 __device__ __forceinline__ void sbr_simplex_serial(const TpxTab& tp, int j, float* G, float* V, const float* tj,
                                                    const float* itj, int hl) {
-  constexpr int kH = kSbrHands;
   const int s0 = tp.inf_first[j], n = tp.inf_n[j];
   float m = INFINITY;
   for (int i = 0; i < n; ++i) {
@@ -182,11 +183,18 @@ __device__ __forceinline__ void group_sync(const WarpGroup& wg) {
   else asm volatile("bar.sync %0, %1;" ::"r"(wg.bar), "r"(wg.n_warps * 32) : "memory");
 }
 
-// One item (kSbrHands hands starting at blk * kSbrHands) of player `player`'s smoothed
-// best response.
+// One item (kH hands starting at blk * kH) of player `player`'s smoothed best response.
+// kH = 16: a warp holds each hand twice (two branch sub-lanes).  kH = 8: four times, and
+// its two halves take a simplex each where kH = 16 takes one per warp (four where it
+// takes two); every (sequence, hand) result is formed by the same operations in the
+// same order either way, so both give the same bits.  The value partial sums the
+// item's hands, so it depends on kH.
+template <int kH = kSbrHands>
 __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, const SbrItemArgs& a,
                                 float* sm, WarpGroup wg = kWholeCta) {
-  constexpr int kH = kSbrHands;
+  static_assert(kH == 8 || kH == 16, "8 or 16 hands per item");
+  constexpr int kSL = 32 / kH;                     // lanes per hand
+  constexpr int kGroups = kSL / 2;                 // simplexes per warp, one per two sub-lanes
   const int S = tp.S, J = tp.J, ld = g.ld;
   const int kWarps = wg.n_warps;
   float* G = sm;                                   // [S][kH] sign*g -> g_hat -> q_bar -> q
@@ -195,17 +203,20 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
   float* tj = V + (size_t)J * kH;                  // [J] t_j = mu beta_j
   float* itj = tj + J;                             // [J] 1 / t_j
   const int tid = threadIdx.x - wg.first_warp * 32, lane = threadIdx.x & 31, warp = tid >> 5;
-  const int hl = lane % kH, bl = lane / kH;
+  const int hl = lane % kH, sq = lane / kH;        // hand, copy of the hand (0 .. kSL - 1)
+  const int bl = sq & 1, grp = sq >> 1;            // branch sub-lane, simplex group
+  const unsigned gmask = kGroups == 1 ? 0xffffffffu : 0xffffu << (16 * grp);
   const int h0 = blk * kH, h = h0 + hl;
   const bool live = h < g.H;
 
   // the [S][kH] tile of sign * g (and of the previous iterate): each warp takes rows
-  // 2 warp + bl, 2 warp + bl + 2 warps, ...; the loads of kU rows are issued before any is used
+  // kSL warp + sq, then kSL warps further on, ...; the loads of kU rows are issued before
+  // any is used
   {
     constexpr int kU = 4;
-    const int kRowStep = kWarps * kSubLanes;
+    const int kRowStep = kWarps * kSL;
     const float rz = (a.g != nullptr && a.contrib && live) ? a.grz[h] : 0.f;
-    for (int s0 = kSubLanes * warp + bl; s0 < S; s0 += kRowStep * kU) {
+    for (int s0 = kSL * warp + sq; s0 < S; s0 += kRowStep * kU) {
       float c0[kU], c1[kU], o[kU];
       int e0[kU], e1[kU];
 #pragma unroll
@@ -255,27 +266,27 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
 
   for (int l = tp.L - 1; l >= 0; --l) {
     if (tp.level_ptr[l + 1] - tp.level_ptr[l] > kSplitLevel) {
-      for (int j = tp.level_ptr[l] + kSubLanes * warp + bl; j < tp.level_ptr[l + 1]; j += kSubLanes * kWarps)
-        sbr_simplex_serial(tp, j, G, V, tj, itj, hl);
+      for (int j = tp.level_ptr[l] + kSL * warp + sq; j < tp.level_ptr[l + 1]; j += kSL * kWarps)
+        sbr_simplex_serial<kH>(tp, j, G, V, tj, itj, hl);
       group_sync(wg);
       continue;
     }
-    for (int j = tp.level_ptr[l] + warp; j < tp.level_ptr[l + 1]; j += kWarps) {
+    for (int j = tp.level_ptr[l] + kGroups * warp + grp; j < tp.level_ptr[l + 1]; j += kGroups * kWarps) {
       const int s0 = tp.inf_first[j], n = tp.inf_n[j];
       float m = INFINITY;
-      for (int i = bl; i < n; i += kSubLanes) {
+      for (int i = bl; i < n; i += 2) {
         const int s = s0 + i;
         float gh = G[s * kH + hl];
         for (int c = tp.child_ptr[s]; c < tp.child_ptr[s + 1]; ++c) gh += V[tp.child_idx[c] * kH + hl];
         G[s * kH + hl] = gh;
         m = fminf(m, gh);
       }
-      m = fminf(m, __shfl_xor_sync(0xffffffffu, m, kH));
+      m = fminf(m, __shfl_xor_sync(gmask, m, kH));
       // e_i = exp(-(g_hat_i - m)/t) keeps tiny q_bar accurate; X = sum_i (e_i - 1) via expm1
       // keeps the value accurate: t log q_bar_i* + t log n = -t log1p(X / n)
       const float it = itj[j];
       float sum = 0.f, X = 0.f;
-      for (int i = bl; i < n; i += kSubLanes) {
+      for (int i = bl; i < n; i += 2) {
         float* u = G + (s0 + i) * kH + hl;
         const float d = -(*u - m) * it;
         const float e = expf(d);
@@ -284,10 +295,10 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
         sum += e;
       }
       // both sub-lanes get partial(0) + partial(1) (addition commutes: the same bits)
-      sum += __shfl_xor_sync(0xffffffffu, sum, kH);
-      X += __shfl_xor_sync(0xffffffffu, X, kH);
+      sum += __shfl_xor_sync(gmask, sum, kH);
+      X += __shfl_xor_sync(gmask, X, kH);
       const float inv = 1.f / sum;
-      for (int i = bl; i < n; i += kSubLanes) G[(s0 + i) * kH + hl] *= inv;
+      for (int i = bl; i < n; i += 2) G[(s0 + i) * kH + hl] *= inv;
       if (bl == 0) V[j * kH + hl] = m - tj[j] * log1pf(X / (float)n);
     }
     group_sync(wg);
@@ -295,7 +306,7 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
 
   if (a.value_partial != nullptr && warp == 0) {
     double v = 0.0;
-    if (live && bl == 0)
+    if (live && sq == 0)
       for (int j = tp.level_ptr[0]; j < tp.level_ptr[1]; ++j) v += (double)V[j * kH + hl];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
@@ -308,7 +319,7 @@ __device__ inline void sbr_item(const DevGame& g, const TpxTab& tp, int blk, con
     // normalised q_bar every (sequence, hand) is independent: no level barriers, and
     // every warp takes rows
     const float tau = a.tau, omt = 1.f - a.tau;
-    for (int s = kSubLanes * warp + bl; s < S; s += kWarps * kSubLanes) {
+    for (int s = kSL * warp + sq; s < S; s += kWarps * kSL) {
       float q = G[s * kH + hl];
       for (int p = tp.seq_par[s]; p >= 0; p = tp.seq_par[p]) q *= G[p * kH + hl];
       float o = q;
