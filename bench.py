@@ -44,9 +44,9 @@ METRIC = "EGT iter/s"
 #   (large game: -k regex:engine_kernel_one_merged -s 3 -c 1 ... $B --batch-games 0;
 #    64-game batch, the three 128 MB waves of the timed pass (the three warm-up waves
 #    skipped): -k regex:^engine_kernel$ -s 3 -c 3 ... $B --no-large)
-ENGINE_TRAFFIC_BYTES = 1679616       # full deck, 100 iterations: read 1 257 216 + write 422 400 B
-LARGE_TRAFFIC_BYTES = 10067200       # large game, 100 iterations: read 8 203 008 + write 1 864 192 B
-BATCH_TRAFFIC_BYTES = 31726703872    # 64 games x 200 iterations, three waves: read 1.23 GB + write 30.49 GB
+ENGINE_TRAFFIC_BYTES = None          # full deck, 100 iterations (re-capture after the kernel change)
+LARGE_TRAFFIC_BYTES = None           # large game, 100 iterations (re-capture after the kernel change)
+BATCH_TRAFFIC_BYTES = None           # 64 games x 200 iterations, three waves (re-capture after the kernel change)
 UNIT = "iter/s"
 WORKLOAD = "full-deck river endgame: 52 cards, 1081 hands/player, bets {0.5,1}xpot + all-in, raise cap 3, stack 10, pot 1, EGT/as"
 
