@@ -44,9 +44,9 @@ METRIC = "EGT iter/s"
 #   (large game: -k regex:engine_kernel_one_merged -s 3 -c 1 ... $B --batch-games 0;
 #    64-game batch, the three 128 MB waves of the timed pass (the three warm-up waves
 #    skipped): -k regex:^engine_kernel$ -s 3 -c 3 ... $B --no-large)
-ENGINE_TRAFFIC_BYTES = None          # full deck, 100 iterations (re-capture after the kernel change)
-LARGE_TRAFFIC_BYTES = None           # large game, 100 iterations (re-capture after the kernel change)
-BATCH_TRAFFIC_BYTES = None           # 64 games x 200 iterations, three waves (re-capture after the kernel change)
+ENGINE_TRAFFIC_BYTES = 1696512       # full deck, 100 iterations: read 1 263 872 + write 432 640 B
+LARGE_TRAFFIC_BYTES = 9876480        # large game, 100 iterations: read 8 043 520 + write 1 832 960 B
+BATCH_TRAFFIC_BYTES = 31492615680    # 64 games x 200 iterations, three waves: read 0.93 GB + write 30.56 GB
 UNIT = "iter/s"
 WORKLOAD = "full-deck river endgame: 52 cards, 1081 hands/player, bets {0.5,1}xpot + all-in, raise cap 3, stack 10, pot 1, EGT/as"
 
