@@ -16,7 +16,9 @@
 // hands are independent.  One item = 16 hands; a warp holds each hand twice
 // (lane = hand + 16 x sub-lane) and the two sub-lanes take a simplex's branches
 // alternately, halving the dependent chain of every simplex; the minimum and
-// the sums over branches combine the sub-lanes with one shuffle.  The whole
+// the sums over branches combine the sub-lanes with one shuffle.  (The SBR item
+// also comes in an 8-hand form, each hand four times and two simplexes per
+// warp, with the same bits: see sbr_item.)  The whole
 // [S][16] tile of g (and of the previous iterate the output is mixed with) is
 // fetched into shared memory before the recursion (two 64-byte row pieces per
 // warp load), which then runs on shared memory: the warps split the simplexes
