@@ -97,6 +97,12 @@ def parse():
     ap.add_argument("--serve-rates", default="10,100,500", help="arrival rates (requests/s)")
     ap.add_argument("--serve-requests", type=int, default=24, help="requests per rate")
     ap.add_argument("--serve-iters", type=int, default=200, help="iterations per server launch")
+    ap.add_argument("--serve-mem-mb", type=int, default=0,
+                    help="the server's device-memory budget for running requests in MB (0: its default)")
+    ap.add_argument("--serve-max-running", type=int, default=0,
+                    help="the server's cap on running requests (0: its default)")
+    ap.add_argument("--serve-no-sequential", action="store_true",
+                    help="--serve: skip the one-request-at-a-time comparison")
     ap.add_argument("--engine", default="device", choices=["device", "host"],
                     help="device: each step is one egt_iterate launch; host: egt_step + egt_state_gap per iteration")
     return ap.parse_args()
@@ -561,7 +567,8 @@ def run_serve(args, local):
     out = []
     for rate in [float(r) for r in args.serve_rates.split(",")]:
         reqs = serve_requests(args.serve_requests, rate, synth_seed(rate))
-        srv = egt.Server(local, iters_per_step=args.serve_iters)
+        srv = egt.Server(local, mem_budget_bytes=getattr(args, "serve_mem_mb", 0) << 20,
+                         max_running=getattr(args, "serve_max_running", 0), iters_per_step=args.serve_iters)
         t0 = srv.clock()
         ids, nxt = [], 0
         while True:
@@ -586,6 +593,10 @@ def run_serve(args, local):
                     "latency_p99_s": round(float(np.percentile(lat, 99)), 3),
                     "launches": st["launches"], "iters_mean": round(float(np.mean([r["iters"] for r in res])), 1)})
     # the plain GPU EGT: the last rate's requests solved one at a time, back to back
+    if getattr(args, "serve_no_sequential", False):
+        return {"metric": "served solves/s", "unit": "solves/s", "higher_is_better": True,
+                "iters_per_launch": args.serve_iters, "mem_budget_mb": getattr(args, "serve_mem_mb", 0),
+                "max_running": getattr(args, "serve_max_running", 0), "rates": out, "data": "synthetic"}
     t = time.perf_counter()
     for a, spec, eps in reqs:
         g = egt.Game(spec, device=local)
