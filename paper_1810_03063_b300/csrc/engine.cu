@@ -5,10 +5,10 @@
 //
 // The CTAs of a launch are split into groups; each group runs the jobs (games)
 // assigned to it one after the other.  Phases are separated by a group barrier;
-// the work of a phase (32-hand SBR items, one terminal per product item) is
-// spread over the group's CTAs.  Products stay
-// in terminal-contribution form; the SBR items add a sequence's contributions
-// while they load their tile.
+// the work of a phase (SBR and best-response items of 16 hands, or 8; product items
+// of one terminal, or of one opponent column) is spread over the group's CTAs.
+// Products stay in terminal-contribution form; the SBR items add a sequence's
+// contributions while they load their tile.
 // One CTA of the group (the last rank, which holds the fewest items of a phase)
 // keeps the solver state (t, mu, tau, buffer index) and takes every decision
 // (EGV sign, tau back-off, gap target) from the per-item FP64 partials, summed in
@@ -237,8 +237,6 @@ __device__ __forceinline__ TpxTab pick(const Tabs& tb, int p) {
   return t;
 }
 
-// One SBR phase: all 32-hand items of `player`, spread over the CTAs; gv holds the
-// player's terminal contributions (or is NULL).
 // Shared memory of one SBR / best-response item of either player (a warp half's share
 // when items run in pairs).
 __device__ __forceinline__ size_t pair_half_bytes(const DevGame& g) {
@@ -266,6 +264,8 @@ __device__ __forceinline__ void for_items(const DevGame& g, Grp gr, int n_items,
     if (base + half < n_items) f(base + half, wg, hs);
 }
 
+// One SBR phase: all kH-hand items of `player`, spread over the CTAs; gv holds the
+// player's terminal contributions (or is NULL).
 template <int kH = kSbrHands>
 __device__ __forceinline__ void run_sbr(const DevGame& g, const Tabs& tb, Grp gr, bool pair_ok, int player,
                                         const float* gv, double mu, const float* old, float tau, float* out,
