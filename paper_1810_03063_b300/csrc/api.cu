@@ -523,7 +523,7 @@ egt_status prof_drain(egt_game* G) {
 
 // Run one kernel launch, bracketed by events when accounting is on.
 template <typename F>
-egt_status timed(egt_game* G, int kind, cudaStream_t st, const char* what, F&& launch) {
+egt_status timed(egt_game* G, int kind, cudaStream_t st, const char* what, F&& launch, int count = 1) {
   cudaEvent_t a = nullptr, b = nullptr;
   if (G->prof_on) {
     if (G->prof_pending.size() > 4096) EGT_TRY(prof_drain(G));
@@ -532,7 +532,7 @@ egt_status timed(egt_game* G, int kind, cudaStream_t st, const char* what, F&& l
     cudaEventRecord(a, st);
   }
   launch();
-  G->launches[kind]++;
+  G->launches[kind] += count;
   egt_status s = check_launch(what);
   if (G->prof_on) {
     cudaEventRecord(b, st);
@@ -579,17 +579,14 @@ egt_status read_vals(egt_game* G, int first, int n, cudaStream_t st) {
   return EGT_OK;
 }
 
+// The two products and the two best responses each run as one launch over both
+// players (the same bits as one launch per player); each counts as one launch per player.
 egt_status gap_internal(egt_game* G, const float* x, const float* y, double* gap_mbb, cudaStream_t st) {
-  EGT_TRY(timed(G, EGT_KERNEL_GRAD_F64, st, "grad f64 kernel",               // A y
-                [&] { launch_terms<float>(G->dg, 0, y, nullptr, G->g64[0], st); }));
-  EGT_TRY(timed(G, EGT_KERNEL_GRAD_F64, st, "grad f64 kernel",               // A^T x
-                [&] { launch_terms<float>(G->dg, 1, x, nullptr, G->g64[1], st); }));
-  EGT_TRY(timed(G, EGT_KERNEL_BR_F64, st, "br kernel", [&] {                // min_x <x, Ay>
-    launch_br64(G->dg, 0, G->g64[0], true, 1.0, G->vals + 8, G->partials, G->counter, st);
-  }));
-  EGT_TRY(timed(G, EGT_KERNEL_BR_F64, st, "br kernel", [&] {                // max_y <y, A^T x>
-    launch_br64(G->dg, 1, G->g64[1], true, -1.0, G->vals + 9, G->partials, G->counter, st);
-  }));
+  EGT_TRY(timed(G, EGT_KERNEL_GRAD_F64, st, "grad f64 kernel",               // A y, A^T x
+                [&] { launch_terms_pair64(G->dg, y, x, G->g64[0], G->g64[1], st); }, 2));
+  EGT_TRY(timed(G, EGT_KERNEL_BR_F64, st, "br kernel", [&] {                // min_x <x, Ay>, max_y <y, A^T x>
+    launch_br64_pair(G->dg, G->g64[0], G->g64[1], G->vals + 8, G->vals + 9, G->partials, G->counter, st);
+  }, 2));
   CUDA_TRY(cudaMemcpyAsync(G->pinned + 8, G->vals + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   const double eps = G->pinned[9] - G->pinned[8];

@@ -102,6 +102,12 @@ int opt_in_dynamic_smem(const void* kernel);
 template <typename TIn>
 void launch_terms(const DevGame& g, int player, const TIn* in, float* c32, double* c64, cudaStream_t st);
 
+// Both players' FP64 contributions in one launch (the saddle-point residual): player 0's
+// from y into c64_0, player 1's from x into c64_1; every CTA runs the body of
+// launch_terms, so the results are the same bits as two launches.
+void launch_terms_pair64(const DevGame& g, const float* y, const float* x, double* c64_0, double* c64_1,
+                         cudaStream_t st);
+
 // Product rows from contributions: out[s][h] = rz[h] x (sum of the contributions of the
 // terminals of sequence s, in terminal order); 0 on padding hands.
 template <typename T>
@@ -136,5 +142,13 @@ size_t sbr_smem_bytes(const DevGame& g, int player);
 void launch_br64(const DevGame& g, int player, const double* gv, bool contrib, double sign, double* value_dev,
                  double* partials, unsigned int* counter, cudaStream_t st);
 size_t br_smem_bytes(const DevGame& g, int player);
+
+// Both players' best-response values of the residual in one launch, from their
+// terminal contributions: *value0 = min over x of <x, A y> (gv0), *value1 = max over y
+// of <y, A^T x> (gv1).  Each player's CTAs reduce their own partials (partials[0 .. NB)
+// and [NB .. 2 NB), counter[0] and counter[1]) in the order launch_br64 uses: the same
+// bits as two launches.
+void launch_br64_pair(const DevGame& g, const double* gv0, const double* gv1, double* value0, double* value1,
+                      double* partials, unsigned int* counter, cudaStream_t st);
 
 }  // namespace egt

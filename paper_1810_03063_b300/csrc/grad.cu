@@ -21,6 +21,19 @@ __global__ void __launch_bounds__(kItemThreads)
   term_item<TIn>(g, tb, player, blockIdx.x, in, c32, c64, smem_raw + grad_tab_bytes(g));
 }
 
+// CTAs [0, T0): player 0's terminals (A y from y); [T0, T0 + T1): player 1's (A^T x from x).
+__global__ void __launch_bounds__(kItemThreads)
+    term_pair64_kernel(DevGame g, const float* __restrict__ y, const float* __restrict__ x,
+                       double* __restrict__ c64_0, double* __restrict__ c64_1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const GradTab tb = stage_grad_tab(g, smem_raw);
+  __syncthreads();
+  const int T0 = g.terms[0].n;
+  const int p = (int)blockIdx.x >= T0 ? 1 : 0;
+  term_item<float>(g, tb, p, (int)blockIdx.x - p * T0, p ? x : y, nullptr, p ? c64_1 : c64_0,
+                   smem_raw + grad_tab_bytes(g));
+}
+
 __device__ __forceinline__ float combine_one(const float* c, const int* ptr, int s, int ld, int h,
                                              const DevGame& g, int player) {
   return product32(c, ptr, s, ld, h, (player ? g.rz[1] : g.rz[0])[h]);
@@ -65,6 +78,14 @@ template <>
 void launch_terms<double>(const DevGame& g, int player, const double* in, float* c32, double* c64,
                           cudaStream_t st) {
   launch_t<double>(g, player, in, c32, c64, st);
+}
+
+void launch_terms_pair64(const DevGame& g, const float* y, const float* x, double* c64_0, double* c64_1,
+                         cudaStream_t st) {
+  opt_in_dynamic_smem((const void*)term_pair64_kernel);
+  const int T = g.terms[0].n + g.terms[1].n;
+  if (T == 0) return;
+  term_pair64_kernel<<<T, kItemThreads, grad_smem_bytes(g), st>>>(g, y, x, c64_0, c64_1);
 }
 
 template <typename T>

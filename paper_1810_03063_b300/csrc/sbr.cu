@@ -2,6 +2,7 @@
 // 16 hands running the shared bodies of sbr_impl.cuh (Sec. 5 recursion).  The
 // value summed over hands and root simplexes is reduced in FP64: per-CTA
 // partials, the last CTA to finish adds them in a fixed order (deterministic).
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -29,6 +30,27 @@ __device__ void finish_value(double* partials, unsigned int* counter, double* va
     if (threadIdx.x == 0) {
       *value_dev = v;
       if (!isfinite(v) && status) atomicExch(status, 1);
+      *counter = 0u;
+    }
+  }
+}
+
+// finish_value over the n CTAs [first, first + n) of the grid that share partials and
+// counter (the same fixed-order sum of n partials).
+__device__ void finish_value_n(double* partials, int n, unsigned int* counter, double* value_dev) {
+  __shared__ bool is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    is_last = (prev == (unsigned int)n - 1u);
+  }
+  __syncthreads();
+  if (is_last && threadIdx.x < 32) {
+    __threadfence();
+    const double v = reduce_partials(partials, n, threadIdx.x);
+    if (threadIdx.x == 0) {
+      *value_dev = v;
       *counter = 0u;
     }
   }
@@ -64,6 +86,24 @@ __global__ void __launch_bounds__(kItemThreads)
   br64_item(g, tt, blockIdx.x, gv, contrib, grz, sign, partials + blockIdx.x,
             reinterpret_cast<double*>(raw + tpx_tab_bytes(g, player)));
   finish_value(partials, counter, value_dev, nullptr);
+}
+
+// CTAs [0, NB): player 0 (sign +1, gv0); [NB, 2 NB): player 1 (sign -1, gv1).
+__global__ void __launch_bounds__(kItemThreads)
+    br64_pair_kernel(DevGame g, const double* __restrict__ gv0, const double* __restrict__ gv1, double* value0,
+                     double* value1, double* partials, unsigned int* counter) {
+  extern __shared__ __align__(16) double smd[];
+  const int NB = g.ld / kSbrHands;
+  const int p = (int)blockIdx.x >= NB ? 1 : 0;
+  const int blk = (int)blockIdx.x - p * NB;
+  unsigned char* raw = reinterpret_cast<unsigned char*>(smd);
+  const TpxTab tt = stage_tpx_tab(g, p, raw);
+  __syncthreads();
+  const double* grz = p ? g.rz64[1] : g.rz64[0];
+  double* part = partials + p * NB;
+  br64_item(g, tt, blk, p ? gv1 : gv0, true, grz, p ? -1.0 : 1.0, part + blk,
+            reinterpret_cast<double*>(raw + tpx_tab_bytes(g, p)));
+  finish_value_n(part, NB, counter + p, p ? value1 : value0);
 }
 
 }  // namespace
@@ -104,6 +144,14 @@ void launch_sbr(const DevGame& g, int player, const SbrArgs& a, cudaStream_t st)
   opt_in_dynamic_smem((const void*)sbr_kernel);
   const int grid = g.ld / kSbrHands;
   sbr_kernel<<<grid, kItemThreads, sbr_smem_bytes(g, player), st>>>(g, player, a);
+}
+
+void launch_br64_pair(const DevGame& g, const double* gv0, const double* gv1, double* value0, double* value1,
+                      double* partials, unsigned int* counter, cudaStream_t st) {
+  opt_in_dynamic_smem((const void*)br64_pair_kernel);
+  const int NB = g.ld / kSbrHands;
+  const size_t smem = std::max(br_smem_bytes(g, 0), br_smem_bytes(g, 1));
+  br64_pair_kernel<<<2 * NB, kItemThreads, smem, st>>>(g, gv0, gv1, value0, value1, partials, counter);
 }
 
 void launch_br64(const DevGame& g, int player, const double* gv, bool contrib, double sign, double* value_dev,
